@@ -1,0 +1,163 @@
+"""CPU oracle for Time Warp Edit Distance -- TEST INFRASTRUCTURE ONLY.
+
+Plain FP64 statement of the TWED dynamic program (paper: section "Time Warp
+Edit Distance", steps 1-6; recurrence restated in ``twed_oracle.c``).  It is
+compiled with gcc from ``twed_oracle.c`` and loaded with ctypes.  Only the
+tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py``
+may import this package; the library in ``paper_2007_16135_gb300`` never
+does, and the two share no code.
+
+Entry points (all values float64; series are ``[len, dim]`` arrays):
+
+* ``twed(a, ta, b, tb, nu, lam, p)`` -- full (n+1)x(m+1) matrix, C order.
+* ``twed_rolling(...)`` -- same operations, two rows of memory (O(m)).
+* ``delete_costs(a, ta, nu, lam, p)`` -- dA(1..n) of one series.
+* ``twed_pairs(setA, setB, pairs, dim, nu, lam, p, nthreads)`` -- rolling
+  oracle over listed pairs of two packed sets, threads over pairs.
+
+Parity pins for these functions live in ``tests/test_oracle_*.py``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "twed_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+# -ffp-contract=off: no FMA contraction (gcc on aarch64 contracts by default),
+# so every operation rounds exactly as written in twed_oracle.c.
+CFLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=c99"]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library with gcc (seconds)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm", "-lpthread"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _declare(lib):
+    d, i64, ci = ctypes.c_double, ctypes.c_int64, ctypes.c_int
+    P = ctypes.c_void_p
+    for name in ("oracle_twed", "oracle_twed_rolling"):
+        f = getattr(lib, name)
+        f.restype = ci
+        f.argtypes = [P, P, i64, P, P, i64, ci, d, d, ci, P]
+    lib.oracle_delete_costs.restype = ci
+    lib.oracle_delete_costs.argtypes = [P, P, i64, ci, d, d, ci, P]
+    lib.oracle_twed_pairs.restype = ci
+    lib.oracle_twed_pairs.argtypes = [P, P, P, P, P, P, P, i64, ci, d, d, ci, ci, P]
+    return lib
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = _declare(ctypes.CDLL(build()))
+    return _lib
+
+
+def build_variant(out_dir: str, defines: dict) -> "callable":
+    """Compile the oracle with extra -D defines into ``out_dir`` and return its
+    full-matrix ``twed`` function.  Used only by the pin-strength test, which
+    plants mistakes (``ORACLE_MUTANT``) and checks that the pins catch them."""
+    tag = "_".join(f"{k}{v}" for k, v in sorted(defines.items()))
+    path = os.path.join(out_dir, f"liboracle_{tag}.so")
+    flags = [f"-D{k}={v}" for k, v in defines.items()]
+    subprocess.check_call(["gcc", *CFLAGS, *flags, "-o", path, _SRC, "-lm", "-lpthread"])
+    lib = _declare(ctypes.CDLL(path))
+    return lambda a, ta, b, tb, nu, lam, p=2: _call(lib.oracle_twed, a, ta, b, tb, nu, lam, p)
+
+
+def _series(a, ta):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.ndim == 1:
+        a = a[:, None]
+    ta = np.ascontiguousarray(ta, dtype=np.float64)
+    if ta.shape != (a.shape[0],):
+        raise ValueError("timestamps must have one entry per point")
+    return a, ta
+
+
+def _ptr(x):
+    return x.ctypes.data_as(ctypes.c_void_p) if x is not None else None
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def _call(fn, a, ta, b, tb, nu, lam, p):
+    a, ta = _series(a, ta)
+    b, tb = _series(b, tb)
+    if a.shape[1] != b.shape[1]:
+        raise ValueError("series dimensions differ")
+    out = np.zeros(1, dtype=np.float64)
+    rc = fn(_ptr(a), _ptr(ta), a.shape[0], _ptr(b), _ptr(tb), b.shape[0], a.shape[1],
+            float(nu), float(lam), int(p), _ptr(out))
+    if rc:
+        raise OracleError(f"oracle rejected its arguments (status {rc})")
+    return float(out[0])
+
+
+def twed(a, ta, b, tb, nu, lam, p=2):
+    """TWED by the full-matrix dynamic program (C order)."""
+    return _call(_load().oracle_twed, a, ta, b, tb, nu, lam, p)
+
+
+def twed_rolling(a, ta, b, tb, nu, lam, p=2):
+    """TWED with two rolling rows; bit-identical to :func:`twed`."""
+    return _call(_load().oracle_twed_rolling, a, ta, b, tb, nu, lam, p)
+
+
+def delete_costs(a, ta, nu, lam, p=2):
+    """dA(i) = d(a_i, a_{i-1}) + nu |t_i - t_{i-1}| + lambda for i = 1..n."""
+    a, ta = _series(a, ta)
+    out = np.zeros(a.shape[0], dtype=np.float64)
+    rc = _load().oracle_delete_costs(_ptr(a), _ptr(ta), a.shape[0], a.shape[1], float(nu),
+                                     float(lam), int(p), _ptr(out))
+    if rc:
+        raise OracleError(f"oracle rejected its arguments (status {rc})")
+    return out
+
+
+def twed_pairs(setA, setB, pairs, nu, lam, p=2, nthreads=None):
+    """Rolling oracle over ``pairs`` ([k, 2] int64 indices into A and B).
+
+    A set is a tuple ``(vals [sum_len, dim], ts [sum_len], offs [n+1])``.
+    """
+    va, ta, oa = setA
+    vb, tb, ob = setB
+    va = np.ascontiguousarray(va, dtype=np.float64)
+    vb = np.ascontiguousarray(vb, dtype=np.float64)
+    if va.ndim == 1:
+        va = va[:, None]
+    if vb.ndim == 1:
+        vb = vb[:, None]
+    ta = np.ascontiguousarray(ta, dtype=np.float64)
+    tb = np.ascontiguousarray(tb, dtype=np.float64)
+    oa = np.ascontiguousarray(oa, dtype=np.int64)
+    ob = np.ascontiguousarray(ob, dtype=np.int64)
+    pairs = np.ascontiguousarray(pairs, dtype=np.int64).reshape(-1, 2)
+    if nthreads is None:
+        nthreads = os.cpu_count() or 1
+    out = np.zeros(pairs.shape[0], dtype=np.float64)
+    rc = _load().oracle_twed_pairs(_ptr(va), _ptr(ta), _ptr(oa), _ptr(vb), _ptr(tb), _ptr(ob),
+                                   _ptr(pairs), pairs.shape[0], va.shape[1], float(nu),
+                                   float(lam), int(p), int(nthreads), _ptr(out))
+    if rc:
+        raise OracleError(f"oracle rejected its arguments (status {rc})")
+    return out
