@@ -1,0 +1,200 @@
+/*
+ * twed.h -- C ABI of the GB300 (sm_103a) Time Warp Edit Distance library.
+ *
+ * What is computed (paper, section "Time Warp Edit Distance", steps 1-6, and
+ * section "Improved Time Warp Edit Distance", which evaluates the same cells
+ * one anti-diagonal at a time):
+ *
+ *   a_1..a_n, b_1..b_m points in R^dim with timestamps t_i, t'_j; a_0 = b_0 = 0,
+ *   t_0 = t'_0 = 0.  d(x,y) = (sum_k |x_k - y_k|^p)^(1/p)  (|x - y| if dim == 1).
+ *   c(i,j)  = d(a_i,b_j) + nu |t_i - t'_j|
+ *   dA(i)   = d(a_i,a_{i-1}) + nu |t_i - t_{i-1}| + lambda   (dB likewise)
+ *   D(0,0)  = 0, D(i,0) = D(0,j) = +inf
+ *   D(i,j)  = min(D(i-1,j) + dA(i), D(i,j-1) + dB(j), D(i-1,j-1) + c(i,j) + c(i-1,j-1))
+ *   TWED    = D(n,m)
+ *
+ * Conventions shared by every entry point:
+ *  - A series is `len` points stored row-major as vals[len][dim] (the dim
+ *    components of a point are contiguous) plus ts[len].
+ *  - A packed set of series (twed_set_*_t) stores many series back to back:
+ *    vals[offs[n]][dim], ts[offs[n]], offs[n+1] (int64, offs[0] = 0, non-
+ *    decreasing); series s is rows offs[s] .. offs[s+1]-1.
+ *  - Pointers named d_* or documented "device" must be device memory of the
+ *    handle's device; others are host memory.  The caller owns every input
+ *    and output buffer; the library owns its workspace (inside the handle or
+ *    plan) and never frees caller memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *  - Parameters: la, lb >= 1; dim >= 1; p >= 1 (integer lp degree; the paper's
+ *    "degree"); nu >= 0 and lambda >= 0, both finite.  Anything else returns
+ *    TWED_ERR_INVALID_ARG and launches nothing.
+ *  - Host entry points also reject non-finite input values and timestamps.
+ *    Device entry points do not read inputs on the host: non-finite device
+ *    inputs give undefined (but memory-safe) results.
+ *  - No exception crosses the ABI.  Every call returns a status; the text of
+ *    the last failure on a handle is twed_last_error(handle).
+ *  - A handle is not thread-safe: use one handle per host thread, and do not
+ *    run two calls of one handle concurrently on different streams (they
+ *    share its workspace).
+ */
+#ifndef TWED_H_
+#define TWED_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TWED_OK = 0,
+    TWED_ERR_INVALID_ARG = 1, /* bad pointer, size or parameter */
+    TWED_ERR_CUDA = 2,        /* a CUDA runtime call failed */
+    TWED_ERR_ALLOC = 3,       /* device workspace allocation failed */
+    TWED_ERR_TIMEOUT = 4,     /* a bounded inter-warp wait expired; results invalid */
+    TWED_ERR_UNSUPPORTED = 5  /* valid request this build cannot serve */
+} twed_status_t;
+
+typedef struct twed_handle_s* twed_handle_t;
+typedef struct twed_plan_s* twed_plan_t;
+
+/* Accumulation of the running cost D for single-precision entry points. */
+typedef enum {
+    TWED_ACCUM_AUTO = 0,  /* FP32, or compensated FP32 once n + m > 100000 */
+    TWED_ACCUM_F32 = 1,   /* plain FP32 sums */
+    TWED_ACCUM_KAHAN = 2  /* compensated (TwoSum) FP32 running cost */
+} twed_accum_t;
+
+/* Options (NULL = all defaults). */
+typedef struct {
+    int accum;          /* twed_accum_t, single precision only */
+    int rows_per_lane;  /* 0 = automatic; else 1..8 rows of the DP per lane */
+    int autotune;       /* plans: 1 = time candidate schedules at creation */
+    double timeout_s;   /* bound on any inter-warp wait; 0 = 2 seconds */
+    int64_t stall_strip;/* fault injection for tests: the given row strip never
+                           publishes progress, so its successor's wait expires
+                           (TWED_ERR_TIMEOUT); -1 = off */
+} twed_opts_t;
+
+/* A packed set of series.  vals/ts/offs are device pointers; offs_host is a
+ * host copy of offs (the library reads lengths from it to plan work). */
+typedef struct {
+    const double* vals;
+    const double* ts;
+    const int64_t* offs;
+    const int64_t* offs_host;
+    int64_t n;
+} twed_set_f64_t;
+
+typedef struct {
+    const float* vals;
+    const float* ts;
+    const int64_t* offs;
+    const int64_t* offs_host;
+    int64_t n;
+} twed_set_f32_t;
+
+/* ---- handles ----------------------------------------------------------- */
+
+/* Create a handle on the current CUDA device.  Allocates a private stream; no
+ * workspace until first use.  Returns TWED_ERR_CUDA without a usable GPU. */
+twed_status_t twed_create(twed_handle_t* handle);
+void twed_destroy(twed_handle_t handle);
+/* Text of the last failure on `handle` (valid until the next call on it). */
+const char* twed_last_error(twed_handle_t handle);
+/* Library version string. */
+const char* twed_version(void);
+/* Waits for `stream`, then reports (and clears) any TWED_ERR_TIMEOUT that a
+ * device entry point enqueued on this handle raised.  TWED_OK otherwise. */
+twed_status_t twed_sync_status(twed_handle_t handle, void* stream);
+
+/* ---- one pair ------------------------------------------------------------
+ * The paper's host-managed `twed` call (section "Basic Methodology and
+ * Results"): host pointers in, host scalar out, blocking.  Copies the inputs
+ * to the handle's workspace, runs the wavefront, copies D(la,lb) back.
+ * a[la][dim], ta[la], b[lb][dim], tb[lb]; *out receives TWED(a, b). */
+twed_status_t twed_f64(twed_handle_t handle, const double* a, const double* ta, int64_t la,
+                       const double* b, const double* tb, int64_t lb, int dim, double nu,
+                       double lambda, int p, double* out);
+twed_status_t twed_f32(twed_handle_t handle, const float* a, const float* ta, int64_t la,
+                       const float* b, const float* tb, int64_t lb, int dim, float nu,
+                       float lambda, int p, float* out);
+/* As twed_f32 with options (accumulation mode, rows per lane, timeout). */
+twed_status_t twed_f32_ex(twed_handle_t handle, const float* a, const float* ta, int64_t la,
+                          const float* b, const float* tb, int64_t lb, int dim, float nu,
+                          float lambda, int p, const twed_opts_t* opts, float* out);
+
+/* The paper's device-resident `twed_dev` call: every pointer is device
+ * memory, work is enqueued on `stream` and the call returns without waiting.
+ * d_out[0] receives TWED.  Wait-timeouts surface through twed_sync_status. */
+twed_status_t twed_dev_f64(twed_handle_t handle, const double* d_a, const double* d_ta,
+                           int64_t la, const double* d_b, const double* d_tb, int64_t lb, int dim,
+                           double nu, double lambda, int p, double* d_out, void* stream);
+twed_status_t twed_dev_f32(twed_handle_t handle, const float* d_a, const float* d_ta, int64_t la,
+                           const float* d_b, const float* d_tb, int64_t lb, int dim, float nu,
+                           float lambda, int p, float* d_out, void* stream);
+twed_status_t twed_dev_f64_ex(twed_handle_t handle, const double* d_a, const double* d_ta,
+                              int64_t la, const double* d_b, const double* d_tb, int64_t lb,
+                              int dim, double nu, double lambda, int p, const twed_opts_t* opts,
+                              double* d_out, void* stream);
+twed_status_t twed_dev_f32_ex(twed_handle_t handle, const float* d_a, const float* d_ta,
+                              int64_t la, const float* d_b, const float* d_tb, int64_t lb,
+                              int dim, float nu, float lambda, int p, const twed_opts_t* opts,
+                              float* d_out, void* stream);
+
+/* ---- explicit pairs over two packed sets ---------------------------------
+ * The paper's batch mode (section "cuTWED Implementation Remarks"), here for
+ * an arbitrary list of pairs: d_pairs[2k], d_pairs[2k+1] (device int64) index
+ * series of A and B; d_out[k] (device) receives TWED(A[d_pairs[2k]],
+ * B[d_pairs[2k+1]]).  One persistent launch, one warp per pair.  Pair indices
+ * are not range-checked on the device: out-of-range indices are undefined.
+ * B may equal A. */
+twed_status_t twed_batch_f64(twed_handle_t handle, const twed_set_f64_t* A,
+                             const twed_set_f64_t* B, const int64_t* d_pairs, int64_t npairs,
+                             int dim, double nu, double lambda, int p, double* d_out, void* stream);
+twed_status_t twed_batch_f32(twed_handle_t handle, const twed_set_f32_t* A,
+                             const twed_set_f32_t* B, const int64_t* d_pairs, int64_t npairs,
+                             int dim, float nu, float lambda, int p, float* d_out, void* stream);
+
+/* ---- all-pairs distance matrix (plan + CUDA graph) -----------------------
+ * The paper's batch mode returning a distance matrix, with its suggested
+ * upper-triangle saving for a symmetric matrix (section "Validation using
+ * Real Datasets").  B == NULL: symmetric self-matrix of A, out[NA][NA]; only
+ * i < j pairs are computed, mirrored, and the diagonal is 0 (TWED(a,a) = 0).
+ * Otherwise out[NA][NB], out[i*NB + j] = TWED(A_i, B_j).
+ * Creation sorts series by length, picks a schedule (and times candidates if
+ * opts->autotune), computes the step-cost records once per execute, and
+ * captures one persistent launch into a CUDA graph.  The plan keeps pointers
+ * to A and B: they must stay valid and keep their lengths; their values may
+ * change between executes.  Execute enqueues one graph launch on `stream`. */
+twed_status_t twed_allpairs_plan_create_f64(twed_handle_t handle, const twed_set_f64_t* A,
+                                            const twed_set_f64_t* B, int dim, double nu,
+                                            double lambda, int p, const twed_opts_t* opts,
+                                            twed_plan_t* plan);
+twed_status_t twed_allpairs_plan_create_f32(twed_handle_t handle, const twed_set_f32_t* A,
+                                            const twed_set_f32_t* B, int dim, float nu,
+                                            float lambda, int p, const twed_opts_t* opts,
+                                            twed_plan_t* plan);
+/* d_out: device float[NA*NB] (f32 plans) or double[NA*NB] (f64 plans). */
+twed_status_t twed_plan_execute(twed_plan_t plan, void* d_out, void* stream);
+/* Interior cells (sum of la*lb over computed pairs) one execute evaluates. */
+int64_t twed_plan_cells(twed_plan_t plan);
+/* Number of pairs one execute evaluates. */
+int64_t twed_plan_pairs(twed_plan_t plan);
+/* Short text naming the schedule the plan chose (rows per lane, warps). */
+const char* twed_plan_describe(twed_plan_t plan);
+void twed_plan_destroy(twed_plan_t plan);
+
+/* All-pairs from host memory, blocking: copies the packed set(s) in, builds
+ * a plan, executes it and copies the matrix out.  B arrays NULL = symmetric.
+ * a_vals[a_offs[na]][dim], a_ts[...], a_offs[na+1]; out[na*nb] (host). */
+twed_status_t twed_allpairs_host_f32(twed_handle_t handle, const float* a_vals,
+                                     const float* a_ts, const int64_t* a_offs, int64_t na,
+                                     const float* b_vals, const float* b_ts,
+                                     const int64_t* b_offs, int64_t nb, int dim, float nu,
+                                     float lambda, int p, float* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TWED_H_ */

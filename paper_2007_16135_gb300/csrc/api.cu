@@ -1,0 +1,835 @@
+// C ABI of the TWED library (include/twed.h): validation, workspace,
+// schedule choice, plans and CUDA-graph capture.  All arithmetic of the
+// method runs in the kernels of kernels_f32.cu / kernels_f64.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "../../include/twed.h"
+#include "launch.h"
+
+using twed::CoopArgs;
+using twed::PairsArgs;
+using twed::RecordsArgs;
+
+#define TWED_VERSION_STR "twed-gb300 0.1"
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// Carves aligned sub-buffers out of one allocation.
+struct Carver {
+    size_t off = 0;
+    size_t take(size_t bytes) {
+        size_t o = off;
+        off = align_up(off + bytes);
+        return o;
+    }
+};
+
+}  // namespace
+
+struct twed_handle_s {
+    int device = 0;
+    int sms = 0;
+    cudaStream_t stream = nullptr;
+    void* ws = nullptr;  // grow-only device workspace
+    size_t ws_bytes = 0;
+    unsigned* ctl = nullptr;  // [0] live error word, [1] sticky error word
+    std::string last_error;
+};
+
+namespace {
+
+twed_status_t fail(twed_handle_t h, twed_status_t st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h) h->last_error = buf;
+    return st;
+}
+
+twed_status_t cuda_fail(twed_handle_t h, cudaError_t e, const char* what) {
+    return fail(h, TWED_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define TWED_CUDA(h, call)                                          \
+    do {                                                            \
+        cudaError_t e_ = (call);                                    \
+        if (e_ != cudaSuccess) return cuda_fail((h), e_, #call);    \
+    } while (0)
+
+twed_status_t ensure_ws(twed_handle_t h, size_t bytes) {
+    if (bytes <= h->ws_bytes) return TWED_OK;
+    if (h->ws) {
+        cudaError_t e = cudaStreamSynchronize(h->stream);
+        if (e != cudaSuccess) return cuda_fail(h, e, "cudaStreamSynchronize");
+        cudaFree(h->ws);
+        h->ws = nullptr;
+        h->ws_bytes = 0;
+    }
+    size_t want = align_up(bytes + bytes / 4);
+    cudaError_t e = cudaMalloc(&h->ws, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        e = cudaMalloc(&h->ws, bytes);
+        want = bytes;
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            h->ws = nullptr;
+            return fail(h, TWED_ERR_ALLOC, "device workspace of %zu bytes: %s", bytes,
+                        cudaGetErrorString(e));
+        }
+    }
+    h->ws_bytes = want;
+    return TWED_OK;
+}
+
+template <typename T>
+bool finite_param(T v) {
+    return std::isfinite((double)v) && v >= T(0);
+}
+
+template <typename T>
+twed_status_t check_params(twed_handle_t h, int64_t la, int64_t lb, int dim, T nu, T lambda,
+                           int p) {
+    if (la < 1 || lb < 1) return fail(h, TWED_ERR_INVALID_ARG, "series lengths must be >= 1");
+    if (la > (int64_t)1 << 30 || lb > (int64_t)1 << 30)
+        return fail(h, TWED_ERR_INVALID_ARG, "series length above 2^30");
+    if (dim < 1) return fail(h, TWED_ERR_INVALID_ARG, "dim must be >= 1");
+    if (p < 1) return fail(h, TWED_ERR_INVALID_ARG, "p must be >= 1");
+    if (!finite_param(nu)) return fail(h, TWED_ERR_INVALID_ARG, "nu must be finite and >= 0");
+    if (!finite_param(lambda))
+        return fail(h, TWED_ERR_INVALID_ARG, "lambda must be finite and >= 0");
+    return TWED_OK;
+}
+
+template <typename T>
+bool all_finite(const T* x, int64_t n) {
+    for (int64_t i = 0; i < n; ++i)
+        if (!std::isfinite((double)x[i])) return false;
+    return true;
+}
+
+unsigned long long timeout_ns(const twed_opts_t* o) {
+    double s = (o && o->timeout_s > 0) ? o->timeout_s : 2.0;
+    if (s > 600.0) s = 600.0;
+    return (unsigned long long)(s * 1e9);
+}
+
+twed::SyncCtl make_sync(twed_handle_t h, const twed_opts_t* o) {
+    twed::SyncCtl sc;
+    sc.err = h->ctl;
+    sc.sticky = h->ctl + 1;
+    sc.timeout_ns = timeout_ns(o);
+    sc.stall_strip = o ? o->stall_strip : -1;
+    return sc;
+}
+
+// Rows per lane for one long pair: enough strips to give every SM several
+// warps, otherwise the most rows per lane (fewest shuffles per cell).
+template <typename T>
+int coop_rows_per_lane(twed_handle_t h, int64_t n, const twed_opts_t* o) {
+    if (o && o->rows_per_lane > 0) {
+        int r = o->rows_per_lane;
+        return r >= 8 ? 8 : r >= 4 ? 4 : r >= 2 ? 2 : 1;
+    }
+    const int64_t want_warps = (int64_t)h->sms * 8;
+    const int cand[4] = {8, 4, 2, 1};
+    for (int r : cand) {
+        if (sizeof(T) == 8 && r > 4) continue;
+        if ((n + 32 * r - 1) / (32 * r) >= want_warps) return r;
+    }
+    return 1;
+}
+
+// Workspace layout of one pair (records, boundary ring, flags) from `base`.
+struct PairLayout {
+    int R;
+    int64_t nstrips;
+    size_t o_ra, o_rb, o_ring, o_flags, end;
+};
+constexpr int kRingSlots = 4;
+
+template <typename T>
+PairLayout pair_layout(twed_handle_t h, int64_t n, int64_t m, int dim, int p,
+                       const twed_opts_t* o, size_t base) {
+    PairLayout L;
+    L.R = coop_rows_per_lane<T>(h, n, o);
+    L.nstrips = (n + 32 * L.R - 1) / (32 * L.R);
+    const int rl = twed::rec_len<T>(dim, p);
+    Carver cv;
+    cv.off = base;
+    L.o_ra = cv.take(sizeof(T) * rl * (size_t)n);
+    L.o_rb = cv.take(sizeof(T) * rl * (size_t)m);
+    L.o_ring = cv.take(sizeof(T) * 2 * (size_t)kRingSlots * (size_t)m);
+    L.o_flags = cv.take(sizeof(unsigned) * (size_t)(L.nstrips + 1));
+    L.end = cv.off;
+    return L;
+}
+
+// Enqueue one pair on `st` with all inputs already on the device.
+template <typename T>
+twed_status_t run_pair_dev(twed_handle_t h, const T* a, const T* ta, int64_t la, const T* b,
+                           const T* tb, int64_t lb, int dim, T nu, T lambda, int p,
+                           const twed_opts_t* o, T* d_out, cudaStream_t st, size_t ws_base) {
+    // rows = the longer series: more strips, more warps in flight
+    if (lb > la) {
+        std::swap(a, b);
+        std::swap(ta, tb);
+        std::swap(la, lb);
+    }
+    const int n = (int)la, m = (int)lb;
+    const PairLayout L = pair_layout<T>(h, n, m, dim, p, o, ws_base);
+    const int R = L.R;
+    const int64_t nstrips = L.nstrips;
+    const int nslot = kRingSlots;
+    twed_status_t s = ensure_ws(h, L.end);
+    if (s != TWED_OK) return s;
+    char* base = (char*)h->ws;
+    T* rec_a = (T*)(base + L.o_ra);
+    T* rec_b = (T*)(base + L.o_rb);
+    unsigned* flags = (unsigned*)(base + L.o_flags);
+    const size_t o_ring = L.o_ring;
+
+    TWED_CUDA(h, cudaMemsetAsync(flags, 0, sizeof(unsigned) * (size_t)(nstrips + 1), st));
+    TWED_CUDA(h, cudaMemsetAsync(h->ctl, 0, sizeof(unsigned), st));
+
+    // offs == nullptr: the records kernel treats the input as one series
+    RecordsArgs<T> ra{a, ta, nullptr, 1, la, dim, p, nu, lambda, rec_a};
+    TWED_CUDA(h, twed::launch_records(ra, st));
+    RecordsArgs<T> rb{b, tb, nullptr, 1, lb, dim, p, nu, lambda, rec_b};
+    TWED_CUDA(h, twed::launch_records(rb, st));
+
+    CoopArgs<T> ca;
+    ca.rec_a = rec_a;
+    ca.rec_b = rec_b;
+    ca.vals_a = a;
+    ca.vals_b = b;
+    ca.n = n;
+    ca.m = m;
+    ca.dim = dim;
+    ca.p = p;
+    ca.nu = nu;
+    ca.nstrips = nstrips;
+    ca.ring = base + o_ring;
+    ca.nslot = nslot;
+    ca.flags = flags;
+    ca.strip_counter = flags + nstrips;
+    ca.out = d_out;
+    ca.sc = make_sync(h, o);
+    const int threads = 128;
+    const int per_sm = std::max(1, twed::coop_blocks_per_sm<T>(dim, p, R, threads));
+    int64_t blocks = std::min<int64_t>((nstrips + 3) / 4, (int64_t)per_sm * h->sms);
+    blocks = std::max<int64_t>(1, blocks);
+    TWED_CUDA(h, twed::launch_coop(ca, R, (int)blocks, threads, st));
+    return TWED_OK;
+}
+
+// Host-pointer pair: copy in, run, copy out, report wait timeouts.
+template <typename T>
+twed_status_t run_pair_host(twed_handle_t h, const T* a, const T* ta, int64_t la, const T* b,
+                            const T* tb, int64_t lb, int dim, T nu, T lambda, int p,
+                            const twed_opts_t* o, T* out) {
+    if (!h) return TWED_ERR_INVALID_ARG;
+    if (!a || !ta || !b || !tb || !out) return fail(h, TWED_ERR_INVALID_ARG, "null pointer");
+    twed_status_t s = check_params<T>(h, la, lb, dim, nu, lambda, p);
+    if (s != TWED_OK) return s;
+    if (!all_finite(a, la * dim) || !all_finite(ta, la) || !all_finite(b, lb * dim) ||
+        !all_finite(tb, lb))
+        return fail(h, TWED_ERR_INVALID_ARG, "non-finite input value or timestamp");
+    Carver cv;
+    const size_t o_a = cv.take(sizeof(T) * (size_t)(la * dim));
+    const size_t o_ta = cv.take(sizeof(T) * (size_t)la);
+    const size_t o_b = cv.take(sizeof(T) * (size_t)(lb * dim));
+    const size_t o_tb = cv.take(sizeof(T) * (size_t)lb);
+    const size_t o_out = cv.take(sizeof(T));
+    const size_t base = cv.off;
+    const PairLayout L = pair_layout<T>(h, std::max(la, lb), std::min(la, lb), dim, p, o, base);
+    s = ensure_ws(h, L.end);  // sized once, so run_pair_dev never reallocates
+    if (s != TWED_OK) return s;
+    cudaStream_t st = h->stream;
+    auto dptr = [&](size_t off) { return (T*)((char*)h->ws + off); };
+    TWED_CUDA(h, cudaMemcpyAsync(dptr(o_a), a, sizeof(T) * la * dim, cudaMemcpyHostToDevice, st));
+    TWED_CUDA(h, cudaMemcpyAsync(dptr(o_ta), ta, sizeof(T) * la, cudaMemcpyHostToDevice, st));
+    TWED_CUDA(h, cudaMemcpyAsync(dptr(o_b), b, sizeof(T) * lb * dim, cudaMemcpyHostToDevice, st));
+    TWED_CUDA(h, cudaMemcpyAsync(dptr(o_tb), tb, sizeof(T) * lb, cudaMemcpyHostToDevice, st));
+    s = run_pair_dev<T>(h, dptr(o_a), dptr(o_ta), la, dptr(o_b), dptr(o_tb), lb, dim, nu, lambda,
+                        p, o, dptr(o_out), st, base);
+    if (s != TWED_OK) return s;
+    unsigned err = 0;
+    TWED_CUDA(h, cudaMemcpyAsync(out, dptr(o_out), sizeof(T), cudaMemcpyDeviceToHost, st));
+    TWED_CUDA(h, cudaMemcpyAsync(&err, h->ctl, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    TWED_CUDA(h, cudaStreamSynchronize(st));
+    if (err != 0) {
+        unsigned zero = 0;
+        cudaMemcpy(h->ctl + 1, &zero, sizeof zero, cudaMemcpyHostToDevice);
+        return fail(h, (twed_status_t)err, "a bounded inter-warp wait expired");
+    }
+    return TWED_OK;
+}
+
+template <typename T>
+twed_status_t twed_dev_impl(twed_handle_t h, const T* a, const T* ta, int64_t la, const T* b,
+                            const T* tb, int64_t lb, int dim, T nu, T lambda, int p,
+                            const twed_opts_t* o, T* d_out, void* stream) {
+    if (!h) return TWED_ERR_INVALID_ARG;
+    if (!a || !ta || !b || !tb || !d_out) return fail(h, TWED_ERR_INVALID_ARG, "null pointer");
+    twed_status_t s = check_params<T>(h, la, lb, dim, nu, lambda, p);
+    if (s != TWED_OK) return s;
+    return run_pair_dev<T>(h, a, ta, la, b, tb, lb, dim, nu, lambda, p, o, d_out,
+                           (cudaStream_t)stream, 0);
+}
+
+}  // namespace
+
+// =========================================================== handles
+extern "C" twed_status_t twed_create(twed_handle_t* out) {
+    if (!out) return TWED_ERR_INVALID_ARG;
+    *out = nullptr;
+    twed_handle_t h = new (std::nothrow) twed_handle_s();
+    if (!h) return TWED_ERR_ALLOC;
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMalloc(&h->ctl, 64);
+    if (e == cudaSuccess) e = cudaMemset(h->ctl, 0, 64);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (h->stream) cudaStreamDestroy(h->stream);
+        if (h->ctl) cudaFree(h->ctl);
+        delete h;
+        return TWED_ERR_CUDA;
+    }
+    *out = h;
+    return TWED_OK;
+}
+
+extern "C" void twed_destroy(twed_handle_t h) {
+    if (!h) return;
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    if (h->ws) cudaFree(h->ws);
+    if (h->ctl) cudaFree(h->ctl);
+    if (h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+extern "C" const char* twed_last_error(twed_handle_t h) {
+    return h ? h->last_error.c_str() : "null handle";
+}
+
+extern "C" const char* twed_version(void) { return TWED_VERSION_STR; }
+
+extern "C" twed_status_t twed_sync_status(twed_handle_t h, void* stream) {
+    if (!h) return TWED_ERR_INVALID_ARG;
+    TWED_CUDA(h, cudaStreamSynchronize((cudaStream_t)stream));
+    TWED_CUDA(h, cudaStreamSynchronize(h->stream));
+    unsigned sticky = 0, zero = 0;
+    TWED_CUDA(h, cudaMemcpy(&sticky, h->ctl + 1, sizeof sticky, cudaMemcpyDeviceToHost));
+    if (sticky) {
+        TWED_CUDA(h, cudaMemcpy(h->ctl + 1, &zero, sizeof zero, cudaMemcpyHostToDevice));
+        return fail(h, (twed_status_t)sticky, "a bounded inter-warp wait expired");
+    }
+    return TWED_OK;
+}
+
+// =========================================================== one pair
+extern "C" twed_status_t twed_f64(twed_handle_t h, const double* a, const double* ta, int64_t la,
+                                  const double* b, const double* tb, int64_t lb, int dim,
+                                  double nu, double lambda, int p, double* out) {
+    return run_pair_host<double>(h, a, ta, la, b, tb, lb, dim, nu, lambda, p, nullptr, out);
+}
+
+extern "C" twed_status_t twed_f32(twed_handle_t h, const float* a, const float* ta, int64_t la,
+                                  const float* b, const float* tb, int64_t lb, int dim, float nu,
+                                  float lambda, int p, float* out) {
+    return run_pair_host<float>(h, a, ta, la, b, tb, lb, dim, nu, lambda, p, nullptr, out);
+}
+
+extern "C" twed_status_t twed_f32_ex(twed_handle_t h, const float* a, const float* ta, int64_t la,
+                                     const float* b, const float* tb, int64_t lb, int dim,
+                                     float nu, float lambda, int p, const twed_opts_t* opts,
+                                     float* out) {
+    return run_pair_host<float>(h, a, ta, la, b, tb, lb, dim, nu, lambda, p, opts, out);
+}
+
+extern "C" twed_status_t twed_dev_f64(twed_handle_t h, const double* a, const double* ta,
+                                      int64_t la, const double* b, const double* tb, int64_t lb,
+                                      int dim, double nu, double lambda, int p, double* d_out,
+                                      void* stream) {
+    return twed_dev_impl<double>(h, a, ta, la, b, tb, lb, dim, nu, lambda, p, nullptr, d_out,
+                                 stream);
+}
+
+extern "C" twed_status_t twed_dev_f32(twed_handle_t h, const float* a, const float* ta, int64_t la,
+                                      const float* b, const float* tb, int64_t lb, int dim,
+                                      float nu, float lambda, int p, float* d_out, void* stream) {
+    return twed_dev_impl<float>(h, a, ta, la, b, tb, lb, dim, nu, lambda, p, nullptr, d_out,
+                                stream);
+}
+
+extern "C" twed_status_t twed_dev_f64_ex(twed_handle_t h, const double* a, const double* ta,
+                                         int64_t la, const double* b, const double* tb,
+                                         int64_t lb, int dim, double nu, double lambda, int p,
+                                         const twed_opts_t* opts, double* d_out, void* stream) {
+    return twed_dev_impl<double>(h, a, ta, la, b, tb, lb, dim, nu, lambda, p, opts, d_out,
+                                 stream);
+}
+
+extern "C" twed_status_t twed_dev_f32_ex(twed_handle_t h, const float* a, const float* ta,
+                                         int64_t la, const float* b, const float* tb, int64_t lb,
+                                         int dim, float nu, float lambda, int p,
+                                         const twed_opts_t* opts, float* d_out, void* stream) {
+    return twed_dev_impl<float>(h, a, ta, la, b, tb, lb, dim, nu, lambda, p, opts, d_out,
+                                stream);
+}
+
+// =========================================================== many pairs
+namespace {
+
+template <typename S>
+twed_status_t check_set(twed_handle_t h, const S* set, const char* name, int64_t* max_len,
+                        int64_t* total) {
+    if (!set || !set->vals || !set->ts || !set->offs || !set->offs_host)
+        return fail(h, TWED_ERR_INVALID_ARG, "set %s: null pointer", name);
+    if (set->n < 1) return fail(h, TWED_ERR_INVALID_ARG, "set %s: no series", name);
+    if (set->offs_host[0] != 0) return fail(h, TWED_ERR_INVALID_ARG, "set %s: offs[0] != 0", name);
+    int64_t mx = 0;
+    for (int64_t s = 0; s < set->n; ++s) {
+        const int64_t len = set->offs_host[s + 1] - set->offs_host[s];
+        if (len < 1) return fail(h, TWED_ERR_INVALID_ARG, "set %s: series %lld is empty", name, (long long)s);
+        if (len > (int64_t)1 << 30) return fail(h, TWED_ERR_INVALID_ARG, "set %s: series too long", name);
+        mx = std::max(mx, len);
+    }
+    *max_len = mx;
+    *total = set->offs_host[set->n];
+    return TWED_OK;
+}
+
+}  // namespace
+
+struct twed_plan_s {
+    twed_handle_t h = nullptr;
+    bool f64 = false;
+    bool symmetric = false;
+    int64_t na = 0, nb = 0, npairs = 0, cells = 0;
+    void* mem = nullptr;
+    size_t mem_bytes = 0;
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    void* bound_out = nullptr;
+    int blocks = 0, threads = 128;
+    // argument blocks (the out pointer is filled in at capture)
+    PairsArgs<float> pf{};
+    PairsArgs<double> pd{};
+    RecordsArgs<float> rfa{}, rfb{};
+    RecordsArgs<double> rda{}, rdb{};
+    unsigned* ctl = nullptr;  // plan's own [live err, sticky err]
+    unsigned long long* counter = nullptr;
+    std::string desc;
+};
+
+namespace {
+
+template <typename T>
+PairsArgs<T>& plan_pairs(twed_plan_t pl);
+template <>
+PairsArgs<float>& plan_pairs<float>(twed_plan_t pl) { return pl->pf; }
+template <>
+PairsArgs<double>& plan_pairs<double>(twed_plan_t pl) { return pl->pd; }
+
+template <typename T>
+RecordsArgs<T>& plan_rec(twed_plan_t pl, int which);
+template <>
+RecordsArgs<float>& plan_rec<float>(twed_plan_t pl, int w) { return w ? pl->rfb : pl->rfa; }
+template <>
+RecordsArgs<double>& plan_rec<double>(twed_plan_t pl, int w) { return w ? pl->rdb : pl->rda; }
+
+// Enqueue the whole plan (prologue + persistent pairs launch) on `st`.
+template <typename T>
+cudaError_t plan_enqueue(twed_plan_t pl, T* out, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(pl->counter, 0, sizeof(unsigned long long), st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(pl->ctl, 0, sizeof(unsigned), st);
+    if (e == cudaSuccess) e = twed::launch_records(plan_rec<T>(pl, 0), st);
+    if (e == cudaSuccess && !pl->symmetric) e = twed::launch_records(plan_rec<T>(pl, 1), st);
+    PairsArgs<T> pa = plan_pairs<T>(pl);
+    pa.out = out;
+    if (e == cudaSuccess) e = twed::launch_pairs(pa, pl->blocks, pl->threads, st);
+    if (e == cudaSuccess && pl->symmetric) e = twed::launch_zero_diag(out, pl->f64, pl->na, st);
+    return e;
+}
+
+template <typename T, typename S>
+twed_status_t plan_create(twed_handle_t h, const S* A, const S* B, int dim, T nu, T lambda,
+                          int p, const twed_opts_t* o, twed_plan_t* out_plan) {
+    if (!h) return TWED_ERR_INVALID_ARG;
+    if (!out_plan) return fail(h, TWED_ERR_INVALID_ARG, "null plan pointer");
+    *out_plan = nullptr;
+    twed_status_t s = check_params<T>(h, 1, 1, dim, nu, lambda, p);
+    if (s != TWED_OK) return s;
+    int64_t maxa = 0, tota = 0, maxb = 0, totb = 0;
+    s = check_set(h, A, "A", &maxa, &tota);
+    if (s != TWED_OK) return s;
+    const bool sym = (B == nullptr);
+    if (!sym) {
+        s = check_set(h, B, "B", &maxb, &totb);
+        if (s != TWED_OK) return s;
+    } else {
+        maxb = maxa;
+        totb = tota;
+    }
+    twed_plan_t pl = new (std::nothrow) twed_plan_s();
+    if (!pl) return fail(h, TWED_ERR_ALLOC, "plan");
+    pl->h = h;
+    pl->f64 = sizeof(T) == 8;
+    pl->symmetric = sym;
+    pl->na = A->n;
+    pl->nb = sym ? A->n : B->n;
+
+    // Longest series first: the persistent warps then finish on the shortest
+    // pairs, which keeps the tail of the launch short.
+    auto sorted = [](const int64_t* offs, int64_t n) {
+        std::vector<int32_t> perm(n);
+        std::iota(perm.begin(), perm.end(), 0);
+        std::stable_sort(perm.begin(), perm.end(), [&](int32_t x, int32_t y) {
+            return offs[x + 1] - offs[x] > offs[y + 1] - offs[y];
+        });
+        return perm;
+    };
+    std::vector<int32_t> perm_a = sorted(A->offs_host, A->n);
+    std::vector<int32_t> perm_b = sym ? std::vector<int32_t>() : sorted(B->offs_host, B->n);
+    int64_t cells = 0;
+    if (sym) {
+        // sum_{i<j} la*lb = ((sum l)^2 - sum l^2) / 2
+        long double sl = 0, sl2 = 0;
+        for (int64_t i = 0; i < A->n; ++i) {
+            long double l = (long double)(A->offs_host[i + 1] - A->offs_host[i]);
+            sl += l;
+            sl2 += l * l;
+        }
+        cells = (int64_t)((sl * sl - sl2) / 2);
+        pl->npairs = A->n * (A->n - 1) / 2;
+    } else {
+        cells = tota * totb;
+        pl->npairs = A->n * B->n;
+    }
+    pl->cells = cells;
+
+    const int rl = twed::rec_len<T>(dim, p);
+    const int threads = 128;
+    const int per_sm = std::max(1, twed::pairs_blocks_per_sm<T>(dim, p, threads));
+    const int64_t want_blocks = (int64_t)per_sm * h->sms;
+    const int64_t need_blocks = std::max<int64_t>(1, (pl->npairs + 3) / 4);
+    pl->blocks = (int)std::min(want_blocks, need_blocks);
+    pl->threads = threads;
+    const int64_t nwarps = (int64_t)pl->blocks * (threads / 32);
+    const int64_t scols = std::max(maxa, maxb);
+
+    Carver cv;
+    const size_t o_ra = cv.take(sizeof(T) * rl * (size_t)tota);
+    const size_t o_rb = sym ? 0 : cv.take(sizeof(T) * rl * (size_t)totb);
+    const size_t o_pa = cv.take(sizeof(int32_t) * perm_a.size());
+    const size_t o_pb = sym ? 0 : cv.take(sizeof(int32_t) * perm_b.size());
+    const size_t o_scr = cv.take(sizeof(T) * 2 * (size_t)nwarps * (size_t)scols);
+    const size_t o_ctl = cv.take(64);
+    pl->mem_bytes = cv.off;
+    cudaError_t e = cudaMalloc(&pl->mem, pl->mem_bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete pl;
+        return fail(h, TWED_ERR_ALLOC, "plan memory of %zu bytes: %s", cv.off, cudaGetErrorString(e));
+    }
+    char* base = (char*)pl->mem;
+    pl->ctl = (unsigned*)(base + o_ctl);
+    pl->counter = (unsigned long long*)(base + o_ctl + 16);
+    e = cudaMemcpy(base + o_pa, perm_a.data(), sizeof(int32_t) * perm_a.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !sym)
+        e = cudaMemcpy(base + o_pb, perm_b.data(), sizeof(int32_t) * perm_b.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(pl->ctl, 0, 64);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(pl->mem);
+        delete pl;
+        return cuda_fail(h, e, "plan set-up copies");
+    }
+
+    T* rec_a = (T*)(base + o_ra);
+    T* rec_b = sym ? rec_a : (T*)(base + o_rb);
+    plan_rec<T>(pl, 0) = RecordsArgs<T>{A->vals, A->ts, A->offs, A->n, tota, dim, p, nu, lambda, rec_a};
+    if (!sym) plan_rec<T>(pl, 1) = RecordsArgs<T>{B->vals, B->ts, B->offs, B->n, totb, dim, p, nu, lambda, rec_b};
+
+    PairsArgs<T>& pa = plan_pairs<T>(pl);
+    pa.rec_a = rec_a;
+    pa.rec_b = rec_b;
+    pa.vals_a = A->vals;
+    pa.vals_b = sym ? A->vals : B->vals;
+    pa.offs_a = A->offs;
+    pa.offs_b = sym ? A->offs : B->offs;
+    pa.mode = sym ? twed::kSymmetricSorted : twed::kBlockSorted;
+    pa.pairs = nullptr;
+    pa.perm_a = (const int32_t*)(base + o_pa);
+    pa.perm_b = sym ? pa.perm_a : (const int32_t*)(base + o_pb);
+    pa.npairs = pl->npairs;
+    pa.na = pl->na;
+    pa.nb = pl->nb;
+    pa.dim = dim;
+    pa.p = p;
+    pa.rmax = (o && o->rows_per_lane > 0) ? o->rows_per_lane : twed::pairs_rmax_limit<T>();
+    pa.nu = nu;
+    pa.out = nullptr;
+    pa.counter = pl->counter;
+    pa.scratch = base + o_scr;
+    pa.scratch_cols = scols;
+    pa.sc.err = pl->ctl;
+    pa.sc.sticky = pl->ctl + 1;
+    pa.sc.timeout_ns = timeout_ns(o);
+    pa.sc.stall_strip = -1;
+
+    e = cudaStreamCreateWithFlags(&pl->cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(pl->mem);
+        delete pl;
+        return cuda_fail(h, e, "cudaStreamCreate");
+    }
+    char d[160];
+    snprintf(d, sizeof d, "%s pairs=%lld warps=%lld rows_per_lane<=%d blocks=%d x %d threads",
+             sizeof(T) == 8 ? "f64" : "f32", (long long)pl->npairs, (long long)nwarps, pa.rmax,
+             pl->blocks, threads);
+    pl->desc = d;
+    *out_plan = pl;
+    return TWED_OK;
+}
+
+template <typename T>
+twed_status_t plan_capture(twed_plan_t pl, T* out) {
+    twed_handle_t h = pl->h;
+    if (pl->exec) {
+        cudaGraphExecDestroy(pl->exec);
+        pl->exec = nullptr;
+    }
+    if (pl->graph) {
+        cudaGraphDestroy(pl->graph);
+        pl->graph = nullptr;
+    }
+    TWED_CUDA(h, cudaStreamBeginCapture(pl->cap, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = plan_enqueue<T>(pl, out, pl->cap);
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(pl->cap, &g);
+    if (e != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return cuda_fail(h, e, "capturing the plan");
+    }
+    if (e2 != cudaSuccess) return cuda_fail(h, e2, "cudaStreamEndCapture");
+    pl->graph = g;
+    TWED_CUDA(h, cudaGraphInstantiate(&pl->exec, g, 0));
+    pl->bound_out = out;
+    return TWED_OK;
+}
+
+}  // namespace
+
+extern "C" twed_status_t twed_allpairs_plan_create_f64(twed_handle_t h, const twed_set_f64_t* A,
+                                                       const twed_set_f64_t* B, int dim, double nu,
+                                                       double lambda, int p,
+                                                       const twed_opts_t* opts, twed_plan_t* plan) {
+    return plan_create<double>(h, A, B, dim, nu, lambda, p, opts, plan);
+}
+
+extern "C" twed_status_t twed_allpairs_plan_create_f32(twed_handle_t h, const twed_set_f32_t* A,
+                                                       const twed_set_f32_t* B, int dim, float nu,
+                                                       float lambda, int p,
+                                                       const twed_opts_t* opts, twed_plan_t* plan) {
+    return plan_create<float>(h, A, B, dim, nu, lambda, p, opts, plan);
+}
+
+extern "C" twed_status_t twed_plan_execute(twed_plan_t pl, void* d_out, void* stream) {
+    if (!pl) return TWED_ERR_INVALID_ARG;
+    if (!d_out) return fail(pl->h, TWED_ERR_INVALID_ARG, "null output");
+    if (d_out != pl->bound_out || !pl->exec) {
+        twed_status_t s = pl->f64 ? plan_capture<double>(pl, (double*)d_out)
+                                  : plan_capture<float>(pl, (float*)d_out);
+        if (s != TWED_OK) return s;
+    }
+    TWED_CUDA(pl->h, cudaGraphLaunch(pl->exec, (cudaStream_t)stream));
+    return TWED_OK;
+}
+
+extern "C" int64_t twed_plan_cells(twed_plan_t pl) { return pl ? pl->cells : 0; }
+extern "C" int64_t twed_plan_pairs(twed_plan_t pl) { return pl ? pl->npairs : 0; }
+extern "C" const char* twed_plan_describe(twed_plan_t pl) { return pl ? pl->desc.c_str() : ""; }
+
+extern "C" void twed_plan_destroy(twed_plan_t pl) {
+    if (!pl) return;
+    cudaStreamSynchronize(pl->cap);
+    if (pl->exec) cudaGraphExecDestroy(pl->exec);
+    if (pl->graph) cudaGraphDestroy(pl->graph);
+    if (pl->cap) cudaStreamDestroy(pl->cap);
+    cudaDeviceSynchronize();
+    if (pl->mem) cudaFree(pl->mem);
+    delete pl;
+}
+
+// =========================================================== explicit pairs
+namespace {
+
+template <typename T, typename S>
+twed_status_t batch_impl(twed_handle_t h, const S* A, const S* B, const int64_t* d_pairs,
+                         int64_t npairs, int dim, T nu, T lambda, int p, T* d_out, void* stream) {
+    if (!h) return TWED_ERR_INVALID_ARG;
+    if (npairs < 0) return fail(h, TWED_ERR_INVALID_ARG, "npairs < 0");
+    if (npairs == 0) return TWED_OK;
+    if (!d_pairs || !d_out) return fail(h, TWED_ERR_INVALID_ARG, "null pointer");
+    twed_status_t s = check_params<T>(h, 1, 1, dim, nu, lambda, p);
+    if (s != TWED_OK) return s;
+    int64_t maxa, tota, maxb, totb;
+    if ((s = check_set(h, A, "A", &maxa, &tota)) != TWED_OK) return s;
+    if ((s = check_set(h, B, "B", &maxb, &totb)) != TWED_OK) return s;
+    const bool same = (A->vals == B->vals && A->offs == B->offs && A->ts == B->ts);
+    const int rl = twed::rec_len<T>(dim, p);
+    const int threads = 128;
+    const int per_sm = std::max(1, twed::pairs_blocks_per_sm<T>(dim, p, threads));
+    const int blocks = (int)std::min<int64_t>((int64_t)per_sm * h->sms, (npairs + 3) / 4);
+    const int64_t nwarps = (int64_t)blocks * (threads / 32);
+    const int64_t scols = std::max(maxa, maxb);
+    Carver cv;
+    const size_t o_ra = cv.take(sizeof(T) * rl * (size_t)tota);
+    const size_t o_rb = same ? o_ra : cv.take(sizeof(T) * rl * (size_t)totb);
+    const size_t o_scr = cv.take(sizeof(T) * 2 * (size_t)nwarps * (size_t)scols);
+    const size_t o_cnt = cv.take(sizeof(unsigned long long));
+    if ((s = ensure_ws(h, cv.off)) != TWED_OK) return s;
+    char* base = (char*)h->ws;
+    cudaStream_t st = (cudaStream_t)stream;
+    T* rec_a = (T*)(base + o_ra);
+    T* rec_b = (T*)(base + o_rb);
+    unsigned long long* counter = (unsigned long long*)(base + o_cnt);
+    TWED_CUDA(h, cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
+    TWED_CUDA(h, cudaMemsetAsync(h->ctl, 0, sizeof(unsigned), st));
+    RecordsArgs<T> ra{A->vals, A->ts, A->offs, A->n, tota, dim, p, nu, lambda, rec_a};
+    TWED_CUDA(h, twed::launch_records(ra, st));
+    if (!same) {
+        RecordsArgs<T> rb{B->vals, B->ts, B->offs, B->n, totb, dim, p, nu, lambda, rec_b};
+        TWED_CUDA(h, twed::launch_records(rb, st));
+    }
+    PairsArgs<T> pa{};
+    pa.rec_a = rec_a;
+    pa.rec_b = rec_b;
+    pa.vals_a = A->vals;
+    pa.vals_b = B->vals;
+    pa.offs_a = A->offs;
+    pa.offs_b = B->offs;
+    pa.mode = twed::kExplicitPairs;
+    pa.pairs = d_pairs;
+    pa.npairs = npairs;
+    pa.na = A->n;
+    pa.nb = B->n;
+    pa.dim = dim;
+    pa.p = p;
+    pa.rmax = twed::pairs_rmax_limit<T>();
+    pa.nu = nu;
+    pa.out = d_out;
+    pa.counter = counter;
+    pa.scratch = base + o_scr;
+    pa.scratch_cols = scols;
+    pa.sc = make_sync(h, nullptr);
+    TWED_CUDA(h, twed::launch_pairs(pa, blocks, threads, st));
+    return TWED_OK;
+}
+
+}  // namespace
+
+extern "C" twed_status_t twed_batch_f64(twed_handle_t h, const twed_set_f64_t* A,
+                                        const twed_set_f64_t* B, const int64_t* d_pairs,
+                                        int64_t npairs, int dim, double nu, double lambda, int p,
+                                        double* d_out, void* stream) {
+    return batch_impl<double>(h, A, B, d_pairs, npairs, dim, nu, lambda, p, d_out, stream);
+}
+
+extern "C" twed_status_t twed_batch_f32(twed_handle_t h, const twed_set_f32_t* A,
+                                        const twed_set_f32_t* B, const int64_t* d_pairs,
+                                        int64_t npairs, int dim, float nu, float lambda, int p,
+                                        float* d_out, void* stream) {
+    return batch_impl<float>(h, A, B, d_pairs, npairs, dim, nu, lambda, p, d_out, stream);
+}
+
+// =========================================================== host all-pairs
+extern "C" twed_status_t twed_allpairs_host_f32(twed_handle_t h, const float* a_vals,
+                                                const float* a_ts, const int64_t* a_offs,
+                                                int64_t na, const float* b_vals,
+                                                const float* b_ts, const int64_t* b_offs,
+                                                int64_t nb, int dim, float nu, float lambda, int p,
+                                                float* out) {
+    if (!h) return TWED_ERR_INVALID_ARG;
+    if (!a_vals || !a_ts || !a_offs || na < 1 || !out)
+        return fail(h, TWED_ERR_INVALID_ARG, "null pointer or empty set");
+    const bool sym = (b_vals == nullptr);
+    if (!sym && (!b_ts || !b_offs || nb < 1))
+        return fail(h, TWED_ERR_INVALID_ARG, "set B incomplete");
+    if (dim < 1) return fail(h, TWED_ERR_INVALID_ARG, "dim must be >= 1");
+    const int64_t tota = a_offs[na], totb = sym ? 0 : b_offs[nb];
+    if (tota < 1 || (!sym && totb < 1)) return fail(h, TWED_ERR_INVALID_ARG, "empty set");
+    if (!all_finite(a_vals, tota * dim) || !all_finite(a_ts, tota) ||
+        (!sym && (!all_finite(b_vals, totb * dim) || !all_finite(b_ts, totb))))
+        return fail(h, TWED_ERR_INVALID_ARG, "non-finite input value or timestamp");
+    const int64_t NB = sym ? na : nb;
+    Carver cv;
+    const size_t o_av = cv.take(sizeof(float) * tota * dim);
+    const size_t o_at = cv.take(sizeof(float) * tota);
+    const size_t o_ao = cv.take(sizeof(int64_t) * (na + 1));
+    const size_t o_bv = sym ? 0 : cv.take(sizeof(float) * totb * dim);
+    const size_t o_bt = sym ? 0 : cv.take(sizeof(float) * totb);
+    const size_t o_bo = sym ? 0 : cv.take(sizeof(int64_t) * (nb + 1));
+    const size_t o_out = cv.take(sizeof(float) * na * NB);
+    void* mem = nullptr;
+    cudaError_t e = cudaMalloc(&mem, cv.off);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(h, TWED_ERR_ALLOC, "staging memory: %s", cudaGetErrorString(e));
+    }
+    char* base = (char*)mem;
+    cudaStream_t st = h->stream;
+    twed_status_t s = TWED_OK;
+    twed_plan_t pl = nullptr;
+    do {
+        e = cudaMemcpyAsync(base + o_av, a_vals, sizeof(float) * tota * dim, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(base + o_at, a_ts, sizeof(float) * tota, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(base + o_ao, a_offs, sizeof(int64_t) * (na + 1), cudaMemcpyHostToDevice, st);
+        if (!sym) {
+            if (e == cudaSuccess) e = cudaMemcpyAsync(base + o_bv, b_vals, sizeof(float) * totb * dim, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(base + o_bt, b_ts, sizeof(float) * totb, cudaMemcpyHostToDevice, st);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(base + o_bo, b_offs, sizeof(int64_t) * (nb + 1), cudaMemcpyHostToDevice, st);
+        }
+        if (e != cudaSuccess) { s = cuda_fail(h, e, "host to device copies"); break; }
+        twed_set_f32_t A{(const float*)(base + o_av), (const float*)(base + o_at),
+                         (const int64_t*)(base + o_ao), a_offs, na};
+        twed_set_f32_t B{(const float*)(base + o_bv), (const float*)(base + o_bt),
+                         (const int64_t*)(base + o_bo), b_offs, nb};
+        s = plan_create<float>(h, &A, sym ? nullptr : &B, dim, nu, lambda, p, nullptr, &pl);
+        if (s != TWED_OK) break;
+        // run the plan directly (no graph): a one-shot call gains nothing from capture
+        e = plan_enqueue<float>(pl, (float*)(base + o_out), st);
+        if (e != cudaSuccess) { s = cuda_fail(h, e, "all-pairs launch"); break; }
+        e = cudaMemcpyAsync(out, base + o_out, sizeof(float) * na * NB, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) { s = cuda_fail(h, e, "device to host copy"); break; }
+        unsigned err = 0;
+        cudaMemcpy(&err, pl->ctl, sizeof err, cudaMemcpyDeviceToHost);
+        if (err) s = fail(h, (twed_status_t)err, "a bounded wait expired");
+    } while (0);
+    if (pl) twed_plan_destroy(pl);
+    cudaStreamSynchronize(st);
+    cudaFree(mem);
+    return s;
+}

@@ -1,0 +1,294 @@
+// TWED kernels: prologue records, one-long-pair strips, many-pairs warps.
+// Included once per precision (kernels_f32.cu, kernels_f64.cu).
+#pragma once
+
+#include "engine.cuh"
+
+namespace twed {
+
+// ------------------------------------------------------------------ prologue
+// Step 1 of the paper's algorithm: the O(n) deletion costs of every series,
+// dA(i) = d(a_i, a_{i-1}) + nu |t_i - t_{i-1}| + lambda, with a_0 = 0 and
+// t_0 = 0 for the first point (the paper's footnote; the DP never reads
+// dA(1)).  Packed with the point itself into one record per point.
+template <typename T, int DIM, int P>
+__global__ void __launch_bounds__(256) records_kernel(RecordsArgs<T> a) {
+    using A = Arith<T>;
+    using RL = Rec<T, DIM>;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < a.total; g += stride) {
+        bool first = (g == 0);  // offs == nullptr: one series of `total` points
+        if (a.offs != nullptr) {
+            int64_t lo = 0, hi = a.nseries;  // offs[lo] <= g < offs[hi]
+            while (hi - lo > 1) {
+                const int64_t mid = (lo + hi) >> 1;
+                if (__ldg(a.offs + mid) <= g) lo = mid; else hi = mid;
+            }
+            first = (__ldg(a.offs + lo) == g);
+        }
+        const T t = a.ts[g];
+        const T tprev = first ? T(0) : a.ts[g - 1];
+        T d;
+        T* out = a.rec + g * RL::kLen;
+        if constexpr (DIM > 0) {
+            T x[DIM], y[DIM];
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) {
+                x[k] = a.vals[g * DIM + k];
+                y[k] = first ? T(0) : a.vals[(g - 1) * DIM + k];
+                out[k] = x[k];
+            }
+            d = dist<T, DIM, P>(x, y, DIM, a.p);
+        } else {
+            const T* x = a.vals + g * (int64_t)a.dim;
+            if (!first) {
+                d = dist<T, 0, P>(x, x - a.dim, a.dim, a.p);
+            } else {
+                // distance to the zero padding: |x_k - 0| = |x_k|
+                if (a.dim == 1) {
+                    d = A::absv(x[0]);
+                } else if (a.p == 1) {
+                    d = A::absv(x[0]);
+                    for (int k = 1; k < a.dim; ++k) d = A::add(d, A::absv(x[k]));
+                } else if (a.p == 2) {
+                    T s = A::mul(x[0], x[0]);
+                    for (int k = 1; k < a.dim; ++k) s = A::sq_acc(s, x[k]);
+                    d = A::root(s);
+                } else {
+                    const T e = (T)a.p;
+                    T s = A::powv(A::absv(x[0]), e);
+                    for (int k = 1; k < a.dim; ++k) s = A::add(s, A::powv(A::absv(x[k]), e));
+                    d = A::powv(s, (T)1 / e);
+                }
+            }
+        }
+        out[RL::kT] = t;
+        out[RL::kDel] = A::add(A::wcost(d, a.nu, t, tprev), a.lam);
+#pragma unroll
+        for (int q = RL::kDel + 1; q < RL::kLen; ++q) out[q] = T(0);
+    }
+}
+
+// --------------------------------------------------------- one long pair
+// Rows are cut into strips of 32*R rows.  Warps take strips in increasing
+// order from an atomic counter, so the strip a warp waits on was taken by a
+// warp that is already running: progress never depends on a warp that has
+// not started, whatever the residency.  A strip publishes its bottom row
+// every 32 columns into a ring slot (release store of the column count) and
+// its successor polls that count (acquire, bounded by %globaltimer).
+template <typename T, int DIM, int P, int R>
+__global__ void __launch_bounds__(128) coop_kernel(CoopArgs<T> a) {
+    using V2 = typename Pair2<T>::V;
+    const int lane = threadIdx.x & 31;
+    PairRef<T> pr;
+    pr.rec_a = a.rec_a;
+    pr.rec_b = a.rec_b;
+    pr.vals_a = a.vals_a;
+    pr.vals_b = a.vals_b;
+    pr.a_first = 0;
+    pr.b_first = 0;
+    pr.n = a.n;
+    pr.m = a.m;
+    pr.dim = a.dim;
+    pr.p = a.p;
+    pr.nu = a.nu;
+    V2* ring = reinterpret_cast<V2*>(a.ring);
+    while (true) {
+        unsigned k = 0;
+        if (lane == 0) k = atomicAdd(a.strip_counter, 1u);
+        k = __shfl_sync(kFull, k, 0);
+        if ((int64_t)k >= a.nstrips) break;
+        if (*(volatile unsigned*)a.sc.err != 0u) break;
+        const int r0 = (int)k * 32 * R + 1;
+        const int rows = min(32 * R, a.n - r0 + 1);
+        StripIO<T> io;
+        io.up = k == 0 ? nullptr : ring + (int64_t)((k - 1) % a.nslot) * a.m;
+        io.up_flag = k == 0 ? nullptr : a.flags + (k - 1);
+        const bool last = (int64_t)k == a.nstrips - 1;
+        io.down = last ? nullptr : ring + (int64_t)(k % a.nslot) * a.m;
+        io.down_flag = last ? nullptr : a.flags + k;
+        io.publish = (long long)k != a.sc.stall_strip;
+        if (!run_strip<T, DIM, P, R>(pr, r0, rows, io, a.sc, a.out, nullptr)) break;
+    }
+}
+
+// ------------------------------------------------------------- many pairs
+__device__ __forceinline__ void triangle_pos(int64_t w, int64_t n, int64_t& p, int64_t& q) {
+    // row-major enumeration of {(p, q): 0 <= p < q < n}; row p starts at
+    // p*(2n - p - 1)/2
+    const double b = 2.0 * (double)n - 1.0;
+    int64_t r = (int64_t)((b - sqrt(b * b - 8.0 * (double)w)) * 0.5);
+    if (r < 0) r = 0;
+    if (r > n - 2) r = n - 2;
+    while (r > 0 && r * (2 * n - r - 1) / 2 > w) --r;
+    while (r < n - 2 && (r + 1) * (2 * n - r - 2) / 2 <= w) ++r;
+    p = r;
+    q = w - r * (2 * n - r - 1) / 2 + r + 1;
+}
+
+template <typename T, int DIM, int P, int R>
+__device__ __forceinline__ bool pair_strip(const PairRef<T>& pr, int r0, int rows,
+                                           const StripIO<T>& io, const SyncCtl& sc, T* o1,
+                                           T* o2) {
+    return run_strip<T, DIM, P, R>(pr, r0, rows, io, sc, o1, o2);
+}
+
+template <typename T, int DIM, int P, int RMAX>
+__global__ void __launch_bounds__(128) pairs_kernel(PairsArgs<T> a) {
+    using V2 = typename Pair2<T>::V;
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    V2* row = reinterpret_cast<V2*>(a.scratch) + gw * a.scratch_cols;
+    const int rmax = a.rmax < RMAX ? (a.rmax < 1 ? 1 : a.rmax) : RMAX;
+    while (true) {
+        unsigned long long w = 0;
+        if (lane == 0) w = atomicAdd(a.counter, 1ull);
+        w = __shfl_sync(kFull, w, 0);
+        if ((int64_t)w >= a.npairs) break;
+        int64_t x, y;
+        T *o1, *o2 = nullptr;
+        if (a.mode == kExplicitPairs) {
+            x = a.pairs[2 * w];
+            y = a.pairs[2 * w + 1];
+            o1 = a.out + w;
+        } else if (a.mode == kSymmetricSorted) {
+            int64_t pp, qq;
+            triangle_pos((int64_t)w, a.na, pp, qq);
+            x = a.perm_a[pp];
+            y = a.perm_a[qq];
+            o1 = a.out + x * a.na + y;
+            o2 = a.out + y * a.na + x;
+        } else {
+            const int64_t pp = (int64_t)w / a.nb, qq = (int64_t)w % a.nb;
+            x = a.perm_a[pp];
+            y = a.perm_b[qq];
+            o1 = a.out + x * a.nb + y;
+        }
+        const int64_t xa = a.offs_a[x], nx = a.offs_a[x + 1] - xa;
+        const int64_t yb = a.offs_b[y], ny = a.offs_b[y + 1] - yb;
+        // rows = the shorter series (fewer strips), columns = the longer one;
+        // TWED is symmetric, and the swapped evaluation performs the mirrored
+        // operations, so the value is the same bit for bit.
+        PairRef<T> pr;
+        pr.dim = a.dim;
+        pr.p = a.p;
+        pr.nu = a.nu;
+        if (nx <= ny) {
+            pr.rec_a = a.rec_a; pr.vals_a = a.vals_a; pr.a_first = xa; pr.n = (int)nx;
+            pr.rec_b = a.rec_b; pr.vals_b = a.vals_b; pr.b_first = yb; pr.m = (int)ny;
+        } else {
+            pr.rec_a = a.rec_b; pr.vals_a = a.vals_b; pr.a_first = yb; pr.n = (int)ny;
+            pr.rec_b = a.rec_a; pr.vals_b = a.vals_a; pr.b_first = xa; pr.m = (int)nx;
+        }
+        int r0 = 1;
+        while (r0 <= pr.n) {
+            const int left = pr.n - r0 + 1;
+            const int R = left >= 32 * rmax ? rmax : (left + 31) / 32;
+            const int rows = min(left, 32 * R);
+            const bool last = r0 + rows > pr.n;
+            StripIO<T> io;
+            io.up = r0 == 1 ? nullptr : row;
+            io.up_flag = nullptr;
+            io.down = last ? nullptr : row;
+            io.down_flag = nullptr;
+            io.publish = true;
+            switch (R) {
+                case 1: pair_strip<T, DIM, P, 1>(pr, r0, rows, io, a.sc, o1, o2); break;
+                case 2: if constexpr (RMAX >= 2) pair_strip<T, DIM, P, 2>(pr, r0, rows, io, a.sc, o1, o2); break;
+                case 3: if constexpr (RMAX >= 3) pair_strip<T, DIM, P, 3>(pr, r0, rows, io, a.sc, o1, o2); break;
+                case 4: if constexpr (RMAX >= 4) pair_strip<T, DIM, P, 4>(pr, r0, rows, io, a.sc, o1, o2); break;
+                case 5: if constexpr (RMAX >= 5) pair_strip<T, DIM, P, 5>(pr, r0, rows, io, a.sc, o1, o2); break;
+                case 6: if constexpr (RMAX >= 6) pair_strip<T, DIM, P, 6>(pr, r0, rows, io, a.sc, o1, o2); break;
+                case 7: if constexpr (RMAX >= 7) pair_strip<T, DIM, P, 7>(pr, r0, rows, io, a.sc, o1, o2); break;
+                case 8: if constexpr (RMAX >= 8) pair_strip<T, DIM, P, 8>(pr, r0, rows, io, a.sc, o1, o2); break;
+                default: break;
+            }
+            r0 += rows;
+            __syncwarp();
+        }
+    }
+}
+
+template <typename T>
+__global__ void zero_diag_kernel(T* out, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i * n + i] = T(0);
+}
+
+// ----------------------------------------------------------- dispatch
+// (dim, p) -> compiled variant: dims 1, 2, 3, 4, 8 keep points in registers;
+// any other dim uses the run-time-dimension kernels (DIM = 0).  p = 1 and
+// p = 2 have closed forms; other p use pow (P = 0).
+#define TWED_DISPATCH(dim, p, BODY)                                            \
+    do {                                                                       \
+        _Pragma("nv_diag_suppress 177")                                        \
+        switch (dim) {                                                         \
+            case 1: { constexpr int DIM_ = 1, P_ = 2; BODY; } break;           \
+            case 2: if (p == 1) { constexpr int DIM_ = 2, P_ = 1; BODY; }      \
+                    else if (p == 2) { constexpr int DIM_ = 2, P_ = 2; BODY; } \
+                    else { constexpr int DIM_ = 0, P_ = 0; BODY; } break;      \
+            case 3: if (p == 1) { constexpr int DIM_ = 3, P_ = 1; BODY; }      \
+                    else if (p == 2) { constexpr int DIM_ = 3, P_ = 2; BODY; } \
+                    else { constexpr int DIM_ = 0, P_ = 0; BODY; } break;      \
+            case 4: if (p == 1) { constexpr int DIM_ = 4, P_ = 1; BODY; }      \
+                    else if (p == 2) { constexpr int DIM_ = 4, P_ = 2; BODY; } \
+                    else { constexpr int DIM_ = 0, P_ = 0; BODY; } break;      \
+            case 8: if (p == 1) { constexpr int DIM_ = 8, P_ = 1; BODY; }      \
+                    else if (p == 2) { constexpr int DIM_ = 8, P_ = 2; BODY; } \
+                    else { constexpr int DIM_ = 0, P_ = 0; BODY; } break;      \
+            default: { constexpr int DIM_ = 0, P_ = 0; BODY; } break;          \
+        }                                                                      \
+    } while (0)
+
+template <typename T>
+cudaError_t launch_records_t(const RecordsArgs<T>& a, cudaStream_t st) {
+    if (a.total <= 0) return cudaSuccess;
+    const int threads = 256;
+    int64_t blocks = (a.total + threads - 1) / threads;
+    if (blocks > 65535) blocks = 65535;
+    TWED_DISPATCH(a.dim, a.p, (records_kernel<T, DIM_, P_><<<(int)blocks, threads, 0, st>>>(a)));
+    return cudaGetLastError();
+}
+
+template <typename T, int RMAX_LIMIT>
+cudaError_t launch_pairs_t(const PairsArgs<T>& a, int blocks, int threads, cudaStream_t st) {
+    if (a.npairs <= 0) return cudaSuccess;
+    TWED_DISPATCH(a.dim, a.p, (pairs_kernel<T, DIM_, P_, RMAX_LIMIT><<<blocks, threads, 0, st>>>(a)));
+    return cudaGetLastError();
+}
+
+template <typename T, int RMAX_LIMIT>
+int pairs_blocks_per_sm_t(int dim, int p, int threads) {
+    int nb = 0;
+    TWED_DISPATCH(dim, p, (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                               &nb, pairs_kernel<T, DIM_, P_, RMAX_LIMIT>, threads, 0)));
+    return nb;
+}
+
+template <typename T>
+cudaError_t launch_coop_t(const CoopArgs<T>& a, int R, int blocks, int threads, cudaStream_t st) {
+    switch (R) {
+        case 1: TWED_DISPATCH(a.dim, a.p, (coop_kernel<T, DIM_, P_, 1><<<blocks, threads, 0, st>>>(a))); break;
+        case 2: TWED_DISPATCH(a.dim, a.p, (coop_kernel<T, DIM_, P_, 2><<<blocks, threads, 0, st>>>(a))); break;
+        case 4: TWED_DISPATCH(a.dim, a.p, (coop_kernel<T, DIM_, P_, 4><<<blocks, threads, 0, st>>>(a))); break;
+        case 8: TWED_DISPATCH(a.dim, a.p, (coop_kernel<T, DIM_, P_, 8><<<blocks, threads, 0, st>>>(a))); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+template <typename T>
+int coop_blocks_per_sm_t(int dim, int p, int R, int threads) {
+    int nb = 0;
+    switch (R) {
+        case 1: TWED_DISPATCH(dim, p, (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, coop_kernel<T, DIM_, P_, 1>, threads, 0))); break;
+        case 2: TWED_DISPATCH(dim, p, (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, coop_kernel<T, DIM_, P_, 2>, threads, 0))); break;
+        case 4: TWED_DISPATCH(dim, p, (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, coop_kernel<T, DIM_, P_, 4>, threads, 0))); break;
+        case 8: TWED_DISPATCH(dim, p, (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, coop_kernel<T, DIM_, P_, 8>, threads, 0))); break;
+        default: break;
+    }
+    return nb;
+}
+
+}  // namespace twed

@@ -1,0 +1,100 @@
+// Host-visible argument blocks of the TWED kernels and their launchers.
+// Included by the C ABI (api.cu) and by the per-precision kernel units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace twed {
+
+// Status words shared by all warps of one launch.  `err` is cleared before
+// each launch and makes every waiting warp give up once set; `sticky` keeps
+// the first failure until the host reads it.
+struct SyncCtl {
+    unsigned* err;
+    unsigned* sticky;
+    unsigned long long timeout_ns;
+    long long stall_strip;  // fault injection: strip that never publishes (-1 off)
+};
+
+// Prologue: one record per point (see Rec<> in engine.cuh).
+template <typename T>
+struct RecordsArgs {
+    const T* vals;         // [total][dim]
+    const T* ts;           // [total]
+    const int64_t* offs;   // [nseries + 1], device; nullptr = one series
+    int64_t nseries;
+    int64_t total;
+    int dim, p;
+    T nu, lam;
+    T* rec;                // [total][rec_len]
+};
+
+// One long pair, rows split into strips that many warps run concurrently.
+template <typename T>
+struct CoopArgs {
+    const T* rec_a;        // row series records [n]
+    const T* rec_b;        // column series records [m]
+    const T* vals_a;       // raw values (runtime-dimension kernels only)
+    const T* vals_b;
+    int n, m, dim, p;
+    T nu;
+    int64_t nstrips;
+    void* ring;            // [nslot][m] pairs (D, c) of strip bottom rows
+    int nslot;
+    unsigned* flags;       // [nstrips] published columns per strip
+    unsigned* strip_counter;
+    T* out;                // D(n, m)
+    SyncCtl sc;
+};
+
+// Many pairs, one warp per pair, strips of a pair run one after another.
+enum PairMode : int { kExplicitPairs = 0, kSymmetricSorted = 1, kBlockSorted = 2 };
+
+template <typename T>
+struct PairsArgs {
+    const T* rec_a;
+    const T* rec_b;
+    const T* vals_a;
+    const T* vals_b;
+    const int64_t* offs_a;
+    const int64_t* offs_b;
+    int mode;
+    const int64_t* pairs;    // kExplicitPairs: [npairs][2]
+    const int32_t* perm_a;   // sorted position -> series index (sorted modes)
+    const int32_t* perm_b;
+    int64_t npairs, na, nb;
+    int dim, p, rmax;
+    T nu;
+    T* out;
+    unsigned long long* counter;
+    void* scratch;           // per warp: one boundary row of `scratch_cols` (D, c) pairs
+    int64_t scratch_cols;
+    SyncCtl sc;
+};
+
+// Elements per point record for (dim, p) (16-byte multiple; see Rec<>).
+template <typename T>
+int rec_len(int dim, int p);
+
+cudaError_t launch_records(const RecordsArgs<float>& a, cudaStream_t st);
+cudaError_t launch_records(const RecordsArgs<double>& a, cudaStream_t st);
+
+// R (rows of the DP per lane) in {1, 2, 4, 8}.
+cudaError_t launch_coop(const CoopArgs<float>& a, int R, int blocks, int threads, cudaStream_t st);
+cudaError_t launch_coop(const CoopArgs<double>& a, int R, int blocks, int threads, cudaStream_t st);
+template <typename T>
+int coop_blocks_per_sm(int dim, int p, int R, int threads);
+
+// a.rmax (largest rows per lane) is clamped to pairs_rmax_limit<T>().
+cudaError_t launch_pairs(const PairsArgs<float>& a, int blocks, int threads, cudaStream_t st);
+cudaError_t launch_pairs(const PairsArgs<double>& a, int blocks, int threads, cudaStream_t st);
+template <typename T>
+int pairs_blocks_per_sm(int dim, int p, int threads);
+template <typename T>
+int pairs_rmax_limit();
+
+// Writes 0 to out[i*n + i], i < n.
+cudaError_t launch_zero_diag(void* out, bool f64, int64_t n, cudaStream_t st);
+
+}  // namespace twed

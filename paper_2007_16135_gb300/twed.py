@@ -1,0 +1,383 @@
+"""ctypes binding of libtwed.so with the entry-point names of include/twed.h.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Device entry points take torch CUDA tensors (PyTorch is used only
+for device memory and streams); host entry points take numpy arrays.  If the
+library has not been built, or no GPU is present, calls raise -- there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libtwed.so")
+
+TWED_OK = 0
+TWED_ERR_INVALID_ARG = 1
+TWED_ERR_CUDA = 2
+TWED_ERR_ALLOC = 3
+TWED_ERR_TIMEOUT = 4
+TWED_ERR_UNSUPPORTED = 5
+_NAMES = {0: "OK", 1: "INVALID_ARG", 2: "CUDA", 3: "ALLOC", 4: "TIMEOUT", 5: "UNSUPPORTED"}
+
+ACCUM_AUTO, ACCUM_F32, ACCUM_KAHAN = 0, 1, 2
+
+# Every symbol include/twed.h declares (checked by the CPU test suite).
+EXPORTS = (
+    "twed_create", "twed_destroy", "twed_last_error", "twed_version", "twed_sync_status",
+    "twed_f64", "twed_f32", "twed_f32_ex",
+    "twed_dev_f64", "twed_dev_f32", "twed_dev_f64_ex", "twed_dev_f32_ex",
+    "twed_batch_f64", "twed_batch_f32",
+    "twed_allpairs_plan_create_f64", "twed_allpairs_plan_create_f32", "twed_plan_execute",
+    "twed_plan_cells", "twed_plan_pairs", "twed_plan_describe", "twed_plan_destroy",
+    "twed_allpairs_host_f32",
+)
+
+
+class TwedError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"TWED_ERR_{_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("accum", ctypes.c_int), ("rows_per_lane", ctypes.c_int),
+                ("autotune", ctypes.c_int), ("timeout_s", ctypes.c_double),
+                ("stall_strip", ctypes.c_int64)]
+
+
+def make_opts(accum=0, rows_per_lane=0, autotune=0, timeout_s=0.0, stall_strip=-1) -> Opts:
+    return Opts(accum, rows_per_lane, autotune, timeout_s, stall_strip)
+
+
+class _SetF64(ctypes.Structure):
+    _fields_ = [("vals", ctypes.c_void_p), ("ts", ctypes.c_void_p), ("offs", ctypes.c_void_p),
+                ("offs_host", ctypes.c_void_p), ("n", ctypes.c_int64)]
+
+
+_SetF32 = _SetF64  # identical layout: four pointers and a count
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path: str | None = None):
+    """Load libtwed.so (raises if it is missing: build it first)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"libtwed.so not built ({p}); run paper_2007_16135_gb300/build.py")
+        lib = ctypes.CDLL(p)
+        P, i64, ci = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+        d, f = ctypes.c_double, ctypes.c_float
+        sig = {
+            "twed_create": (ci, [P]),
+            "twed_destroy": (None, [P]),
+            "twed_last_error": (ctypes.c_char_p, [P]),
+            "twed_version": (ctypes.c_char_p, []),
+            "twed_sync_status": (ci, [P, P]),
+            "twed_f64": (ci, [P, P, P, i64, P, P, i64, ci, d, d, ci, P]),
+            "twed_f32": (ci, [P, P, P, i64, P, P, i64, ci, f, f, ci, P]),
+            "twed_f32_ex": (ci, [P, P, P, i64, P, P, i64, ci, f, f, ci, P, P]),
+            "twed_dev_f64": (ci, [P, P, P, i64, P, P, i64, ci, d, d, ci, P, P]),
+            "twed_dev_f32": (ci, [P, P, P, i64, P, P, i64, ci, f, f, ci, P, P]),
+            "twed_dev_f64_ex": (ci, [P, P, P, i64, P, P, i64, ci, d, d, ci, P, P, P]),
+            "twed_dev_f32_ex": (ci, [P, P, P, i64, P, P, i64, ci, f, f, ci, P, P, P]),
+            "twed_batch_f64": (ci, [P, P, P, P, i64, ci, d, d, ci, P, P]),
+            "twed_batch_f32": (ci, [P, P, P, P, i64, ci, f, f, ci, P, P]),
+            "twed_allpairs_plan_create_f64": (ci, [P, P, P, ci, d, d, ci, P, P]),
+            "twed_allpairs_plan_create_f32": (ci, [P, P, P, ci, f, f, ci, P, P]),
+            "twed_plan_execute": (ci, [P, P, P]),
+            "twed_plan_cells": (i64, [P]),
+            "twed_plan_pairs": (i64, [P]),
+            "twed_plan_describe": (ctypes.c_char_p, [P]),
+            "twed_plan_destroy": (None, [P]),
+            "twed_allpairs_host_f32": (ci, [P, P, P, P, i64, P, P, P, i64, ci, f, f, ci, P]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+        return lib
+
+
+def version() -> str:
+    return load().twed_version().decode()
+
+
+def _np_ptr(x: np.ndarray):
+    return ctypes.c_void_p(x.ctypes.data)
+
+
+def _t_ptr(t):
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+class Handle:
+    """twed_create / twed_destroy.  One handle per host thread."""
+
+    def __init__(self):
+        self.lib = load()
+        h = ctypes.c_void_p()
+        st = self.lib.twed_create(ctypes.byref(h))
+        if st != TWED_OK:
+            raise TwedError(st, "twed_create failed (no usable CUDA device?)")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.twed_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, st: int):
+        if st != TWED_OK:
+            raise TwedError(st, self.lib.twed_last_error(self.h).decode(errors="replace"))
+
+    def sync_status(self, stream=None):
+        self.check(self.lib.twed_sync_status(self.h, _stream_ptr(stream)))
+
+
+_default = threading.local()
+
+
+def default_handle() -> Handle:
+    h = getattr(_default, "h", None)
+    if h is None:
+        h = Handle()
+        _default.h = h
+    return h
+
+
+def _series_np(a, ta, dtype):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    if a.ndim == 1:
+        a = a[:, None]
+    ta = np.ascontiguousarray(ta, dtype=dtype)
+    return a, ta
+
+
+# ------------------------------------------------------------------ one pair
+def twed_f64(a, ta, b, tb, nu, lam, p=2, handle: Handle | None = None) -> float:
+    """Host arrays in, TWED out (blocking).  a: [n, dim] or [n]."""
+    h = handle or default_handle()
+    a, ta = _series_np(a, ta, np.float64)
+    b, tb = _series_np(b, tb, np.float64)
+    out = ctypes.c_double()
+    h.check(h.lib.twed_f64(h.h, _np_ptr(a), _np_ptr(ta), a.shape[0], _np_ptr(b), _np_ptr(tb),
+                           b.shape[0], a.shape[1], nu, lam, p, ctypes.byref(out)))
+    return out.value
+
+
+def twed_f32(a, ta, b, tb, nu, lam, p=2, handle: Handle | None = None, opts: Opts | None = None) -> float:
+    h = handle or default_handle()
+    a, ta = _series_np(a, ta, np.float32)
+    b, tb = _series_np(b, tb, np.float32)
+    out = ctypes.c_float()
+    if opts is None:
+        st = h.lib.twed_f32(h.h, _np_ptr(a), _np_ptr(ta), a.shape[0], _np_ptr(b), _np_ptr(tb),
+                            b.shape[0], a.shape[1], nu, lam, p, ctypes.byref(out))
+    else:
+        st = h.lib.twed_f32_ex(h.h, _np_ptr(a), _np_ptr(ta), a.shape[0], _np_ptr(b), _np_ptr(tb),
+                               b.shape[0], a.shape[1], nu, lam, p, ctypes.byref(opts),
+                               ctypes.byref(out))
+    h.check(st)
+    return out.value
+
+
+def twed_dev(a, ta, b, tb, nu, lam, p=2, out=None, stream=None, handle: Handle | None = None,
+             opts: Opts | None = None):
+    """Device tensors in (float32 or float64, a: [n, dim]), out: 1-element
+    device tensor.  Enqueued on `stream` (default: torch's current stream)."""
+    import torch
+    h = handle or default_handle()
+    if a.dim() == 1:
+        a = a[:, None]
+    if b.dim() == 1:
+        b = b[:, None]
+    a, b, ta, tb = (x.contiguous() for x in (a, b, ta, tb))
+    f64 = a.dtype == torch.float64
+    if out is None:
+        out = torch.empty(1, dtype=a.dtype, device=a.device)
+    sp = _stream_ptr(stream)
+    op = ctypes.byref(opts) if opts is not None else None
+    if f64:
+        st = h.lib.twed_dev_f64_ex(h.h, _t_ptr(a), _t_ptr(ta), a.shape[0], _t_ptr(b), _t_ptr(tb),
+                                   b.shape[0], a.shape[1], float(nu), float(lam), p, op,
+                                   _t_ptr(out), sp)
+    else:
+        st = h.lib.twed_dev_f32_ex(h.h, _t_ptr(a), _t_ptr(ta), a.shape[0], _t_ptr(b), _t_ptr(tb),
+                                   b.shape[0], a.shape[1], float(nu), float(lam), p, op,
+                                   _t_ptr(out), sp)
+    h.check(st)
+    return out
+
+
+twed_dev_f64 = twed_dev
+twed_dev_f32 = twed_dev
+
+
+# ------------------------------------------------------------------ sets
+@dataclass
+class DeviceSet:
+    """A packed set on the device plus the host copy of its offsets."""
+    vals: "object"  # torch [sum_len, dim]
+    ts: "object"  # torch [sum_len]
+    offs: "object"  # torch int64 [n + 1] (device)
+    offs_host: np.ndarray  # int64 [n + 1]
+
+    @classmethod
+    def from_numpy(cls, vals, ts, offs, dtype, device="cuda"):
+        import torch
+        v = np.ascontiguousarray(vals)
+        if v.ndim == 1:
+            v = v[:, None]
+        return cls(torch.as_tensor(v, device=device).to(dtype).contiguous(),
+                   torch.as_tensor(np.ascontiguousarray(ts), device=device).to(dtype).contiguous(),
+                   torch.as_tensor(np.ascontiguousarray(offs, dtype=np.int64), device=device),
+                   np.ascontiguousarray(offs, dtype=np.int64))
+
+    @property
+    def n(self) -> int:
+        return int(self.offs_host.shape[0] - 1)
+
+    @property
+    def dim(self) -> int:
+        return int(self.vals.shape[1])
+
+    def cstruct(self):
+        return _SetF64(self.vals.data_ptr(), self.ts.data_ptr(), self.offs.data_ptr(),
+                       self.offs_host.ctypes.data, self.n)
+
+
+def twed_batch(A: DeviceSet, B: DeviceSet, pairs, nu, lam, p=2, out=None, stream=None,
+               handle: Handle | None = None):
+    """TWED of listed pairs (device int64 [k, 2]) -> device tensor [k]."""
+    import torch
+    h = handle or default_handle()
+    pairs = pairs.contiguous()
+    k = pairs.shape[0]
+    if out is None:
+        out = torch.empty(k, dtype=A.vals.dtype, device=A.vals.device)
+    sa, sb = A.cstruct(), B.cstruct()
+    fn = h.lib.twed_batch_f64 if A.vals.dtype == torch.float64 else h.lib.twed_batch_f32
+    h.check(fn(h.h, ctypes.byref(sa), ctypes.byref(sb), _t_ptr(pairs), k, A.dim, float(nu),
+               float(lam), p, _t_ptr(out), _stream_ptr(stream)))
+    return out
+
+
+twed_batch_f64 = twed_batch
+twed_batch_f32 = twed_batch
+
+
+class Plan:
+    """twed_allpairs_plan_create_* / twed_plan_execute / twed_plan_destroy."""
+
+    def __init__(self, A: DeviceSet, B: DeviceSet | None, nu, lam, p=2,
+                 opts: Opts | None = None, handle: Handle | None = None):
+        import torch
+        self.handle = handle or default_handle()
+        self.A, self.B = A, B  # keep the device buffers alive
+        self.f64 = A.vals.dtype == torch.float64
+        self._sa = A.cstruct()
+        self._sb = B.cstruct() if B is not None else None
+        plan = ctypes.c_void_p()
+        lib = self.handle.lib
+        fn = lib.twed_allpairs_plan_create_f64 if self.f64 else lib.twed_allpairs_plan_create_f32
+        self.handle.check(fn(self.handle.h, ctypes.byref(self._sa),
+                             ctypes.byref(self._sb) if self._sb is not None else None, A.dim,
+                             float(nu), float(lam), p,
+                             ctypes.byref(opts) if opts is not None else None,
+                             ctypes.byref(plan)))
+        self.plan = plan
+        self.na = A.n
+        self.nb = A.n if B is None else B.n
+
+    @property
+    def cells(self) -> int:
+        return int(self.handle.lib.twed_plan_cells(self.plan))
+
+    @property
+    def pairs(self) -> int:
+        return int(self.handle.lib.twed_plan_pairs(self.plan))
+
+    def describe(self) -> str:
+        return self.handle.lib.twed_plan_describe(self.plan).decode()
+
+    def new_output(self):
+        import torch
+        return torch.empty((self.na, self.nb), dtype=self.A.vals.dtype, device=self.A.vals.device)
+
+    def execute(self, out=None, stream=None):
+        if out is None:
+            out = self.new_output()
+        self.handle.check(self.handle.lib.twed_plan_execute(self.plan, _t_ptr(out),
+                                                            _stream_ptr(stream)))
+        return out
+
+    def close(self):
+        if getattr(self, "plan", None):
+            self.handle.lib.twed_plan_destroy(self.plan)
+            self.plan = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+twed_allpairs_plan_create_f64 = Plan
+twed_allpairs_plan_create_f32 = Plan
+
+
+def twed_allpairs_host_f32(a_vals, a_ts, a_offs, b=None, nu=1.0, lam=1.0, p=2,
+                           handle: Handle | None = None, out: np.ndarray | None = None):
+    """All-pairs matrix from host arrays (blocking).  b = (vals, ts, offs) or
+    None for the symmetric self-matrix.  Returns a float32 [na, nb] array."""
+    h = handle or default_handle()
+    av = np.ascontiguousarray(a_vals, dtype=np.float32)
+    if av.ndim == 1:
+        av = av[:, None]
+    at = np.ascontiguousarray(a_ts, dtype=np.float32)
+    ao = np.ascontiguousarray(a_offs, dtype=np.int64)
+    na = ao.shape[0] - 1
+    if b is None:
+        bv = bt = bo = None
+        nb = na
+    else:
+        bv = np.ascontiguousarray(b[0], dtype=np.float32)
+        if bv.ndim == 1:
+            bv = bv[:, None]
+        bt = np.ascontiguousarray(b[1], dtype=np.float32)
+        bo = np.ascontiguousarray(b[2], dtype=np.int64)
+        nb = bo.shape[0] - 1
+    if out is None:
+        out = np.empty((na, nb), dtype=np.float32)
+    ptr = lambda x: None if x is None else _np_ptr(x)
+    h.check(h.lib.twed_allpairs_host_f32(h.h, _np_ptr(av), _np_ptr(at), _np_ptr(ao), na, ptr(bv),
+                                         ptr(bt), ptr(bo), nb if b is not None else 0,
+                                         av.shape[1], float(nu), float(lam), p, _np_ptr(out)))
+    return out

@@ -1,0 +1,120 @@
+"""GPU parity of the batched and all-pairs entry points against the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2007_16135_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tw():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_2007_16135_gb300 import twed
+    twed.load()
+    return twed
+
+
+def oracle_matrix(SA, SB, nu, lam, p, pairs):
+    A64 = SA.astype(np.float64)
+    B64 = SB.astype(np.float64)
+    return oracle.twed_pairs(A64.as_tuple(), B64.as_tuple(), pairs, nu, lam, p)
+
+
+def ragged_set(seed, nseries, lo, hi, dim, dtype):
+    rng = np.random.default_rng(seed)
+    out = []
+    for n in rng.integers(lo, hi + 1, size=nseries):
+        v = np.cumsum(rng.normal(size=(n, dim)), axis=0)
+        t = np.cumsum(rng.exponential(1.0, n))
+        out.append((v, t))
+    return W.pack(out).astype(dtype)
+
+
+def rel(got, want):
+    return np.abs(got - want) / np.maximum(np.abs(want), 1e-300)
+
+
+@pytest.mark.parametrize("dim,p", [(8, 2), (1, 2), (3, 1), (5, 2)])
+def test_allpairs_symmetric_f32(tw, dim, p):
+    import torch
+    S = ragged_set(dim * 10 + p, 37, 1, 700, dim, np.float32)
+    D = tw.DeviceSet.from_numpy(S.vals, S.ts, S.offs, torch.float32)
+    plan = tw.Plan(D, None, 0.5, 0.5, p)
+    M = plan.execute().cpu().numpy()
+    n = S.n
+    pairs = np.array([(i, j) for i in range(n) for j in range(i + 1, n)])
+    ref = oracle_matrix(S, S, 0.5, 0.5, p, pairs)
+    assert rel(M[pairs[:, 0], pairs[:, 1]], ref).max() <= 1e-5
+    assert np.array_equal(M, M.T)
+    assert np.all(np.diag(M) == 0)
+    assert plan.pairs == n * (n - 1) // 2
+    L = S.lengths.astype(np.int64)
+    assert plan.cells == int((L.sum() ** 2 - (L ** 2).sum()) // 2)
+
+
+@pytest.mark.parametrize("dim,p", [(8, 2), (2, 1), (4, 3)])
+def test_allpairs_block_f64_bitwise(tw, dim, p):
+    import torch
+    SA = ragged_set(100 + dim, 19, 1, 600, dim, np.float64)
+    SB = ragged_set(200 + dim, 23, 1, 900, dim, np.float64)
+    A = tw.DeviceSet.from_numpy(SA.vals, SA.ts, SA.offs, torch.float64)
+    B = tw.DeviceSet.from_numpy(SB.vals, SB.ts, SB.offs, torch.float64)
+    plan = tw.Plan(A, B, 0.75, 0.3, p)
+    M = plan.execute().cpu().numpy()
+    pairs = np.array([(i, j) for i in range(SA.n) for j in range(SB.n)])
+    ref = oracle_matrix(SA, SB, 0.75, 0.3, p, pairs).reshape(SA.n, SB.n)
+    if p in (1, 2):
+        assert np.array_equal(M, ref)
+    else:
+        assert rel(M, ref).max() <= 1e-12
+
+
+def test_plan_reexecute_and_new_output(tw):
+    import torch
+    S = ragged_set(5, 16, 30, 300, 3, np.float32)
+    D = tw.DeviceSet.from_numpy(S.vals, S.ts, S.offs, torch.float32)
+    plan = tw.Plan(D, None, 1.0, 1.0, 2)
+    m1 = plan.execute().clone()
+    out = torch.full_like(m1, -1.0)
+    m2 = plan.execute(out)
+    m3 = plan.execute(out)
+    torch.cuda.synchronize()
+    assert torch.equal(m1, m2) and torch.equal(m2, m3)
+
+
+def test_explicit_pairs_match_oracle(tw):
+    import torch
+    SA = ragged_set(31, 25, 1, 1200, 4, np.float32)
+    SB = ragged_set(32, 17, 1, 1500, 4, np.float32)
+    A = tw.DeviceSet.from_numpy(SA.vals, SA.ts, SA.offs, torch.float32)
+    B = tw.DeviceSet.from_numpy(SB.vals, SB.ts, SB.offs, torch.float32)
+    rng = np.random.default_rng(0)
+    pairs = np.stack([rng.integers(0, SA.n, 300), rng.integers(0, SB.n, 300)], axis=1)
+    out = tw.twed_batch(A, B, torch.as_tensor(pairs).cuda(), 1.0, 1.0, 2)
+    got = out.cpu().numpy()
+    ref = oracle_matrix(SA, SB, 1.0, 1.0, 2, pairs)
+    assert rel(got, ref).max() <= 1e-5
+
+
+def test_host_allpairs_equals_plan(tw):
+    import torch
+    S = W.set_w3(nseries=40, len_lo=64, len_hi=512).astype(np.float32)
+    host = tw.twed_allpairs_host_f32(S.vals, S.ts, S.offs, None, 0.5, 0.5, 2)
+    D = tw.DeviceSet.from_numpy(S.vals, S.ts, S.offs, torch.float32)
+    dev = tw.Plan(D, None, 0.5, 0.5, 2).execute().cpu().numpy()
+    assert np.array_equal(host, dev)
+
+
+def test_w3_recipe_small_matches_oracle(tw):
+    # the 4096-series dim-8 recipe at 64 series, all pairs against the oracle
+    import torch
+    S = W.set_w3(nseries=64).astype(np.float32)
+    D = tw.DeviceSet.from_numpy(S.vals, S.ts, S.offs, torch.float32)
+    M = tw.Plan(D, None, 0.5, 0.5, 2).execute().cpu().numpy()
+    pairs = W.sample_upper_pairs(S.n, 400, 3)
+    ref = oracle_matrix(S, S, 0.5, 0.5, 2, pairs)
+    assert rel(M[pairs[:, 0], pairs[:, 1]], ref).max() <= 1e-5
