@@ -1,0 +1,435 @@
+#!/usr/bin/env python3
+"""TWED throughput benchmark (GCUPS = interior DP cells per second / 1e9).
+
+Default workload: all i<j pairs of 4096 dim-8 series with lengths U[64, 2048]
+(three-sinusoid mixtures plus noise, t_i = i, nu = lambda = 0.5, p = 2, FP32),
+8,386,560 pairs per step, one plan execute (one CUDA-graph launch) per step.
+Other workloads: --workload w2 (one 3-D pair, n = m = 1e6 FP32, or 1e5 FP64
+with --dtype f64), w1 (one 1-D FP64 pair, n = m = 1000).
+
+`python bench.py --gpus N --steps K --warmup W` prints one JSON line.  Under
+torchrun each rank runs its own instance of the workload (independent
+problems, no data-path collective: weak scaling); timing is the max over
+ranks.  `--impl reference` times the CPU oracle (the reference arm) instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "TWED GCUPS on 1 GB300; k-NN queries/s at recall@10>=0.99 vs exact batched"
+UNIT = "GCUPS"
+FALLBACK_SM_MAX_MHZ = 2070.0
+FP32_LANES_PER_SM = 128  # FADD/FMUL/FFMA lanes per SM per clock
+KERNEL_SOURCES = ["engine.cuh", "kernels.cuh", "kernels_f32.cu", "kernels_f64.cu", "launch.h"]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["w3", "w2", "w1"], default="w3")
+    ap.add_argument("--dtype", choices=["f32", "f64"], default=None)
+    ap.add_argument("--n", type=int, default=None, help="series length override (w1/w2)")
+    ap.add_argument("--nseries", type=int, default=4096, help="w3 set size (profiling runs)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- helpers
+def kernel_src_hash() -> str:
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2007_16135_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.dev), "-lms", "200", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        rows = []
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    parts = [x.strip() for x in line.split(",")]
+                    if len(parts) >= 9:
+                        rows.append(parts)
+        except OSError:
+            pass
+        finally:
+            if self.path and os.path.exists(self.path):
+                os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no nvidia-smi samples"]}
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return float("nan")
+
+        sm = np.array([num(r[1]) for r in rows])
+        smax = np.array([num(r[2]) for r in rows])
+        pw = np.array([num(r[3]) for r in rows])
+        load = pw >= np.nanmax(pw) * 0.5 if np.isfinite(pw).any() else np.ones_like(sm, bool)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = [n for k, n in enumerate(names) if any(r[5 + k] == "Active" for r in rows)]
+        return {"sm_mhz": float(np.nanmedian(sm[load])), "sm_max_mhz": float(np.nanmax(smax)),
+                "reasons": reasons, "samples": int(len(rows)), "samples_under_load": int(load.sum())}
+
+
+def ops_per_cell(dim: int, p: int) -> int:
+    """FP32-pipe operations (FADD/FMUL/FFMA) the recurrence needs per cell:
+    dim subtractions and dim multiply-adds for d (p = 2), the time term
+    (1 FADD + 1 FFMA), the match sum (2 FADD) and both deletions (2 FADD).
+    The two mins (ALU pipe) and the square root (MUFU) are not counted."""
+    if dim == 1:
+        return 1 + 6
+    return 2 * dim + 6
+
+
+# ---------------------------------------------------------------- workloads
+def w3_set(rank: int, nseries: int = 4096):
+    from paper_2007_16135_gb300 import workloads as W
+    # rank 0 uses the seeded set A stream; other ranks draw their own instance
+    return W.set_w3(nseries=nseries, stream=0 if rank == 0 else 10 + rank).astype(np.float32)
+
+
+def run_cpu_baseline(S, pairs, seconds: float, nu, lam, p):
+    """Time the oracle on a bounded, seeded sample of pairs of the workload."""
+    import oracle
+    cores = os.cpu_count() or 1
+    S64 = S.astype(np.float64)
+    L = S.lengths.astype(np.int64)
+    done, cells, vals, t0 = 0, 0, [], time.perf_counter()
+    chunk = max(cores, 8)
+    while done < len(pairs) and time.perf_counter() - t0 < seconds:
+        pc = pairs[done:done + chunk]
+        vals.append(oracle.twed_pairs(S64.as_tuple(), S64.as_tuple(), pc, nu, lam, p, nthreads=cores))
+        cells += int((L[pc[:, 0]] * L[pc[:, 1]]).sum())
+        done += len(pc)
+    el = time.perf_counter() - t0
+    return {"value": cells / el / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{done} seeded uniform i<j pairs of the workload ({cells:.3e} cells, "
+                      f"{el:.1f} s, FP64 rolling-row oracle, threads over pairs)"}, pairs[:done], np.concatenate(vals)
+
+
+# ---------------------------------------------------------------- our arm
+def bench_w3(args, rank, world, dev):
+    import torch
+
+    from paper_2007_16135_gb300 import twed
+    from paper_2007_16135_gb300 import workloads as W
+
+    nu, lam, p = 0.5, 0.5, 2
+    S = w3_set(rank, args.nseries)
+    D = twed.DeviceSet.from_numpy(S.vals, S.ts, S.offs, torch.float32, device=dev)
+    plan = twed.Plan(D, None, nu, lam, p)
+    out = plan.new_output()
+    cells = plan.cells
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        plan.execute(out, stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    kern_ms = []
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        torch.cuda.synchronize()
+        barrier(world)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            plan.execute(out, stream)
+            # the plan's graph records events around its pairs launch; reading
+            # them needs the step to finish (a ~10 us host wait per step)
+            stream.synchronize()
+            kern_ms.append(plan.kernel_ms())
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+    total_ms = ev0.elapsed_time(ev1)
+    total_ms = max_over_ranks(total_ms, world, dev)
+    ms_step = total_ms / args.steps
+    value = cells * world / (ms_step / 1e3) / 1e9
+
+    res = {"cells_per_step": cells, "pairs_per_step": plan.pairs, "plan": plan.describe(),
+           "ms_per_step": ms_step, "value": value, "clocks": clk.summary(),
+           "kernel_ms": float(np.mean(kern_ms))}
+
+    # roofline of the dominant kernel (pairs launch), ALU-bound (FP32 pipe)
+    props = torch.cuda.get_device_properties(dev)
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", FALLBACK_SM_MAX_MHZ))
+    peak_ops = props.multi_processor_count * FP32_LANES_PER_SM * sm_max * 1e6
+    opc = ops_per_cell(8, p)
+    achieved = cells * opc / (res["kernel_ms"] / 1e3)
+    traffic = None
+    tp = os.path.join(ROOT, "profiles", "pairs_kernel_w3_traffic.json")
+    if os.path.exists(tp):
+        with open(tp) as f:
+            tj = json.load(f)
+        if tj.get("src_hash") == kernel_src_hash():
+            traffic = tj.get("dram_bytes_per_launch")
+    res["roofline"] = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
+                       "unit": "Top/s", "frac": achieved / peak_ops, "traffic": traffic,
+                       "ops_per_cell": opc, "peak_basis":
+                           f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
+                           f"{sm_max:.0f} MHz (max SM clock)",
+                       "kernel": "pairs_kernel<float,8,2,8>"}
+
+    # end to end through the public host API (pinned host buffers)
+    if not args.no_e2e:
+        pv = torch.from_numpy(np.ascontiguousarray(S.vals)).pin_memory().numpy()
+        pt = torch.from_numpy(np.ascontiguousarray(S.ts)).pin_memory().numpy()
+        po = np.ascontiguousarray(S.offs)
+        pout = torch.empty((S.n, S.n), dtype=torch.float32).pin_memory().numpy()
+        twed.twed_allpairs_host_f32(pv, pt, po, None, nu, lam, p, out=pout)  # warm-up
+        e2e_steps = max(1, min(args.steps, 2))
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            twed.twed_allpairs_host_f32(pv, pt, po, None, nu, lam, p, out=pout)
+        el = max_over_ranks((time.perf_counter() - t0) * 1e3, world, dev) / e2e_steps
+        res["e2e"] = {"value": cells * world / (el / 1e3) / 1e9, "unit": UNIT,
+                      "h2d_bytes_per_step": int(pv.nbytes + pt.nbytes + po.nbytes),
+                      "d2h_bytes_per_step": int(pout.nbytes), "ms_per_step": el,
+                      "api": "twed_allpairs_host_f32"}
+    res["gpu_launches"] = 3 * args.steps  # records + pairs + zero-diagonal per step
+
+    # oracle on a bounded sample: CPU baseline and the error of our output
+    if rank == 0 and not args.no_cpu:
+        M = out.cpu().numpy()
+        pairs = W.sample_upper_pairs(S.n, min(20000, S.n * (S.n - 1) // 2), 3)
+        cpu, done_pairs, ref = run_cpu_baseline(S, pairs, args.cpu_seconds, nu, lam, p)
+        got = M[done_pairs[:, 0], done_pairs[:, 1]].astype(np.float64)
+        relerr = np.abs(got - ref) / np.maximum(np.abs(ref), 1e-300)
+        res["cpu_baseline"] = cpu
+        res["error_vs_oracle"] = {"max_rel": float(relerr.max()), "mean_rel": float(relerr.mean()),
+                                  "pairs": int(len(done_pairs)), "bound": 1e-5}
+    res["config"] = {"workload": f"w3 all-pairs: {S.n} series, dim 8, len U[64,2048], sinusoid "
+                                 "mixtures + N(0,0.1), t_i=i, nu=lambda=0.5, p=2, FP32",
+                     "pairs": plan.pairs, "cells": cells, "series": S.n, "dim": 8,
+                     "l2": "inputs larger than L2 (point records 208 MB > 126 MB L2)",
+                     "parallelism": f"{world} independent replica(s)"}
+    res["dtype"] = "f32"
+    return res
+
+
+def bench_pair(args, rank, world, dev, workload):
+    """One long pair through twed_dev (the one-pair kernel)."""
+    import torch
+
+    from paper_2007_16135_gb300 import twed
+    from paper_2007_16135_gb300 import workloads as W
+
+    dtype = args.dtype or ("f32" if workload == "w2" else "f64")
+    td = torch.float32 if dtype == "f32" else torch.float64
+    if workload == "w2":
+        n = args.n or (1_000_000 if dtype == "f32" else 100_000)
+        a, ta, b, tb = W.pair_w2(n)
+        nu, lam, p, dim = 0.001, 1.0, 2, 3
+    else:
+        n = args.n or 1000
+        a, ta, b, tb = W.pair_w1(n, n)
+        nu, lam, p, dim = 1.0, 1.0, 2, 1
+    dv = lambda x: torch.as_tensor(np.ascontiguousarray(x)).to(td).to(dev)
+    A, TA, B, TB = dv(a), dv(ta), dv(b), dv(tb)
+    out = torch.empty(1, dtype=td, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        twed.twed_dev(A, TA, B, TB, nu, lam, p, out=out, stream=stream)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        barrier(world)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            twed.twed_dev(A, TA, B, TB, nu, lam, p, out=out, stream=stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+    twed.default_handle().sync_status(stream)
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world, dev) / args.steps
+    cells = len(a) * len(b)
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = float(measured_peaks().get("sm_max_mhz", FALLBACK_SM_MAX_MHZ))
+    res = {"ms_per_step": ms, "value": cells * world / (ms / 1e3) / 1e9, "clocks": clk.summary(),
+           "cells_per_step": cells, "dtype": dtype, "gpu_launches": 3 * args.steps,
+           "result": float(out.item())}
+    if dtype == "f32":
+        peak = props.multi_processor_count * FP32_LANES_PER_SM * sm_max * 1e6
+        opc = ops_per_cell(dim, p)
+        res["roofline"] = {"bound": "alu", "achieved": cells * opc / (ms / 1e3) / 1e12,
+                           "peak": peak / 1e12, "unit": "Top/s",
+                           "frac": cells * opc / (ms / 1e3) / peak, "traffic": None,
+                           "ops_per_cell": opc, "kernel": f"coop_kernel<float,{dim},2,R>"}
+    res["config"] = {"workload": f"{workload} one pair n=m={n}, dim {dim}, {dtype}", "n": n,
+                     "l2": "one pair per step; records stream through L2"}
+    return res
+
+
+# ---------------------------------------------------------------- reference arm
+def bench_reference(args, rank, world):
+    """The reference arm is the CPU oracle, timed on this host's cores."""
+    from paper_2007_16135_gb300 import workloads as W
+    import oracle
+    if rank != 0:
+        return None
+    nu, lam, p = 0.5, 0.5, 2
+    S = w3_set(0)
+    S64 = S.astype(np.float64)
+    L = S.lengths.astype(np.int64)
+    cores = os.cpu_count() or 1
+    pairs = W.sample_upper_pairs(S.n, 200000, 3)
+    # size one step to about args.cpu_seconds / 2 of CPU time from a calibration slice
+    t0 = time.perf_counter()
+    oracle.twed_pairs(S64.as_tuple(), S64.as_tuple(), pairs[:cores], nu, lam, p, nthreads=cores)
+    per = (time.perf_counter() - t0) / cores
+    k = int(max(cores, min(len(pairs), (args.cpu_seconds / 2) / max(per, 1e-6) * cores)))
+    step_pairs = pairs[:k]
+    cells = int((L[step_pairs[:, 0]] * L[step_pairs[:, 1]]).sum())
+    for _ in range(args.warmup):
+        oracle.twed_pairs(S64.as_tuple(), S64.as_tuple(), step_pairs[:cores], nu, lam, p, nthreads=cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.twed_pairs(S64.as_tuple(), S64.as_tuple(), step_pairs, nu, lam, p, nthreads=cores)
+    el = (time.perf_counter() - t0) / args.steps
+    value = cells / el / 1e9
+    sample = (f"{k} seeded uniform i<j pairs of the w3 workload per step ({cells:.3e} cells), "
+              f"FP64 rolling-row oracle, threads over pairs")
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": el * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "w3 all-pairs: 4096 series, dim 8, len U[64,2048] (sampled "
+                                   "pairs)", "parallelism": "host cores"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "gpu_launches": 0}
+
+
+# ---------------------------------------------------------------- distributed
+_pg = None
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def dist_init(world, local, use_gpu):
+    global _pg
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl" if use_gpu else "gloo")
+        _pg = dist
+
+
+def barrier(world):
+    if world > 1 and _pg is not None:
+        _pg.barrier()
+
+
+def max_over_ranks(x: float, world, dev):
+    if world > 1 and _pg is not None:
+        import torch
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        _pg.all_reduce(t, op=_pg.ReduceOp.MAX)
+        return float(t.item())
+    return x
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_setup()
+    if args.impl == "reference":
+        res = bench_reference(args, rank, world)
+        if res is not None:
+            print(json.dumps(res), flush=True)
+        return
+    import torch
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist_init(world, local, True)
+    from paper_2007_16135_gb300 import twed
+    twed.load()
+    if args.workload == "w3":
+        res = bench_w3(args, rank, world, dev)
+    else:
+        res = bench_pair(args, rank, world, dev, args.workload)
+    if rank == 0:
+        line = {"metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_per_step"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": res.get("dtype", "f32"), "data": "synthetic (seeded generators)",
+                "config": res["config"]}
+        for k in ("roofline", "cpu_baseline", "e2e", "gpu_launches", "clocks", "error_vs_oracle",
+                  "kernel_ms", "plan", "cells_per_step", "result"):
+            if k in res:
+                line[k] = res[k]
+        print(json.dumps(line), flush=True)
+    if world > 1 and _pg is not None:
+        _pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

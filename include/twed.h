@@ -180,6 +180,10 @@ twed_status_t twed_plan_execute(twed_plan_t plan, void* d_out, void* stream);
 int64_t twed_plan_cells(twed_plan_t plan);
 /* Number of pairs one execute evaluates. */
 int64_t twed_plan_pairs(twed_plan_t plan);
+/* Device time, in milliseconds, of the persistent pairs launch of the last
+ * completed execute (CUDA events recorded inside the plan's graph around that
+ * launch).  Call after the execute's stream has been synchronized. */
+twed_status_t twed_plan_kernel_ms(twed_plan_t plan, float* ms);
 /* Short text naming the schedule the plan chose (rows per lane, warps). */
 const char* twed_plan_describe(twed_plan_t plan);
 void twed_plan_destroy(twed_plan_t plan);

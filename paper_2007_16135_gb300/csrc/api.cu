@@ -438,6 +438,7 @@ struct twed_plan_s {
     RecordsArgs<double> rda{}, rdb{};
     unsigned* ctl = nullptr;  // plan's own [live err, sticky err]
     unsigned long long* counter = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around the pairs launch
     std::string desc;
 };
 
@@ -466,7 +467,13 @@ cudaError_t plan_enqueue(twed_plan_t pl, T* out, cudaStream_t st) {
     if (e == cudaSuccess && !pl->symmetric) e = twed::launch_records(plan_rec<T>(pl, 1), st);
     PairsArgs<T> pa = plan_pairs<T>(pl);
     pa.out = out;
+    // inside a capture the records become graph event-record nodes
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (e == cudaSuccess) e = cudaStreamIsCapturing(st, &cs);
+    const unsigned evflag = cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u;
+    if (e == cudaSuccess) e = cudaEventRecordWithFlags(pl->ev0, st, evflag);
     if (e == cudaSuccess) e = twed::launch_pairs(pa, pl->blocks, pl->threads, st);
+    if (e == cudaSuccess) e = cudaEventRecordWithFlags(pl->ev1, st, evflag);
     if (e == cudaSuccess && pl->symmetric) e = twed::launch_zero_diag(out, pl->f64, pl->na, st);
     return e;
 }
@@ -598,6 +605,8 @@ twed_status_t plan_create(twed_handle_t h, const S* A, const S* B, int dim, T nu
     pa.sc.stall_strip = -1;
 
     e = cudaStreamCreateWithFlags(&pl->cap, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&pl->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&pl->ev1);
     if (e != cudaSuccess) {
         cudaGetLastError();
         cudaFree(pl->mem);
@@ -667,6 +676,12 @@ extern "C" twed_status_t twed_plan_execute(twed_plan_t pl, void* d_out, void* st
     return TWED_OK;
 }
 
+extern "C" twed_status_t twed_plan_kernel_ms(twed_plan_t pl, float* ms) {
+    if (!pl || !ms) return TWED_ERR_INVALID_ARG;
+    TWED_CUDA(pl->h, cudaEventElapsedTime(ms, pl->ev0, pl->ev1));
+    return TWED_OK;
+}
+
 extern "C" int64_t twed_plan_cells(twed_plan_t pl) { return pl ? pl->cells : 0; }
 extern "C" int64_t twed_plan_pairs(twed_plan_t pl) { return pl ? pl->npairs : 0; }
 extern "C" const char* twed_plan_describe(twed_plan_t pl) { return pl ? pl->desc.c_str() : ""; }
@@ -677,6 +692,8 @@ extern "C" void twed_plan_destroy(twed_plan_t pl) {
     if (pl->exec) cudaGraphExecDestroy(pl->exec);
     if (pl->graph) cudaGraphDestroy(pl->graph);
     if (pl->cap) cudaStreamDestroy(pl->cap);
+    if (pl->ev0) cudaEventDestroy(pl->ev0);
+    if (pl->ev1) cudaEventDestroy(pl->ev1);
     cudaDeviceSynchronize();
     if (pl->mem) cudaFree(pl->mem);
     delete pl;

@@ -35,7 +35,8 @@ EXPORTS = (
     "twed_dev_f64", "twed_dev_f32", "twed_dev_f64_ex", "twed_dev_f32_ex",
     "twed_batch_f64", "twed_batch_f32",
     "twed_allpairs_plan_create_f64", "twed_allpairs_plan_create_f32", "twed_plan_execute",
-    "twed_plan_cells", "twed_plan_pairs", "twed_plan_describe", "twed_plan_destroy",
+    "twed_plan_cells", "twed_plan_pairs", "twed_plan_kernel_ms", "twed_plan_describe",
+    "twed_plan_destroy",
     "twed_allpairs_host_f32",
 )
 
@@ -99,6 +100,7 @@ def load(path: str | None = None):
             "twed_plan_execute": (ci, [P, P, P]),
             "twed_plan_cells": (i64, [P]),
             "twed_plan_pairs": (i64, [P]),
+            "twed_plan_kernel_ms": (ci, [P, P]),
             "twed_plan_describe": (ctypes.c_char_p, [P]),
             "twed_plan_destroy": (None, [P]),
             "twed_allpairs_host_f32": (ci, [P, P, P, P, i64, P, P, P, i64, ci, f, f, ci, P]),
@@ -322,6 +324,12 @@ class Plan:
     @property
     def pairs(self) -> int:
         return int(self.handle.lib.twed_plan_pairs(self.plan))
+
+    def kernel_ms(self) -> float:
+        """Device time of the pairs launch in the last completed execute."""
+        ms = ctypes.c_float()
+        self.handle.check(self.handle.lib.twed_plan_kernel_ms(self.plan, ctypes.byref(ms)))
+        return ms.value
 
     def describe(self) -> str:
         return self.handle.lib.twed_plan_describe(self.plan).decode()
