@@ -155,6 +155,32 @@ twed_status_t twed_batch_f32(twed_handle_t handle, const twed_set_f32_t* A,
                              const twed_set_f32_t* B, const int64_t* d_pairs, int64_t npairs,
                              int dim, float nu, float lambda, int p, float* d_out, void* stream);
 
+/* ---- explicit pairs without any allocation -------------------------------
+ * The paper has no counterpart to this entry point.  It exists for callers
+ * that must not allocate device memory: code that runs while another thread
+ * captures a CUDA graph in global mode (cudaMalloc is illegal there), loops
+ * where a cudaMalloc/cudaFree would synchronize the device, and plug-ins
+ * whose host framework hands them a fixed memory budget.  Everything above
+ * allocates (twed_create, workspace growth, plans); this call does not.
+ *
+ * Same arguments and result as twed_batch_f32, minus the handle.  Its
+ * working memory is one static device array of TWED_NOALLOC_SCRATCH_BYTES
+ * inside the library, which every GPU that loads the library keeps until
+ * the process exits.  The caller still passes (and owns) all inputs and
+ * outputs.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls share the one array and it keeps
+ * the last call's contents (the call clears what must start at zero): two
+ * calls whose work overlaps on the GPU -- on different streams, or from
+ * different threads -- race and give undefined results.  Requests whose
+ * per-point records plus one boundary row need more than the array return
+ * TWED_ERR_UNSUPPORTED before enqueuing anything.  No error text is kept
+ * (there is no handle); the status code is the whole report. */
+#define TWED_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
+twed_status_t twed_batch_f32_noalloc(const twed_set_f32_t* A, const twed_set_f32_t* B,
+                                     const int64_t* d_pairs, int64_t npairs, int dim, float nu,
+                                     float lambda, int p, float* d_out, void* stream);
+
 /* ---- all-pairs distance matrix (plan + CUDA graph) -----------------------
  * The paper's batch mode returning a distance matrix, with its suggested
  * upper-triangle saving for a symmetric matrix (section "Validation using

@@ -1,0 +1,139 @@
+// twed_batch_f32_noalloc: explicit pairs with no device allocation.
+//
+// For callers that must not call cudaMalloc (see include/twed.h): the
+// records, boundary rows and control words of the many-pairs kernel live in
+// one static device array instead of a handle's workspace.  The kernels are
+// the ones twed_batch_f32 uses; only where their scratch lives differs.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <mutex>
+
+#include "../../include/twed.h"
+#include "launch.h"
+
+namespace {
+
+constexpr size_t kScratchBytes = TWED_NOALLOC_SCRATCH_BYTES;
+constexpr size_t kAlign = 256;
+constexpr int kThreads = 128;
+constexpr int kWarpsPerBlock = kThreads / 32;
+constexpr int kMaxDevices = 64;
+
+// The library's only static device buffer.  In host code this name is a
+// stand-in, not a device address: host code uses the address that
+// cudaGetSymbolAddress returns for the current device.
+static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
+
+std::mutex g_mu;
+void* g_scratch_addr[kMaxDevices] = {};
+
+size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+// Device address of g_scratch on device `dev` (looked up once per device,
+// with that device current).
+cudaError_t scratch_address(int dev, unsigned char** out) {
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (g_scratch_addr[dev] == nullptr) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+        if (e != cudaSuccess) return e;
+        g_scratch_addr[dev] = p;
+    }
+    *out = static_cast<unsigned char*>(g_scratch_addr[dev]);
+    return cudaSuccess;
+}
+
+bool good_set(const twed_set_f32_t* s, int64_t* max_len, int64_t* total) {
+    if (!s || !s->vals || !s->ts || !s->offs || !s->offs_host || s->n < 1) return false;
+    if (s->offs_host[0] != 0) return false;
+    int64_t mx = 0;
+    for (int64_t i = 0; i < s->n; ++i) {
+        const int64_t len = s->offs_host[i + 1] - s->offs_host[i];
+        if (len < 1 || len > ((int64_t)1 << 30)) return false;
+        mx = std::max(mx, len);
+    }
+    *max_len = mx;
+    *total = s->offs_host[s->n];
+    return true;
+}
+
+}  // namespace
+
+extern "C" twed_status_t twed_batch_f32_noalloc(const twed_set_f32_t* A, const twed_set_f32_t* B,
+                                                const int64_t* d_pairs, int64_t npairs, int dim,
+                                                float nu, float lambda, int p, float* d_out,
+                                                void* stream) {
+    if (npairs < 0) return TWED_ERR_INVALID_ARG;
+    if (npairs == 0) return TWED_OK;
+    if (!d_pairs || !d_out || dim < 1 || p < 1) return TWED_ERR_INVALID_ARG;
+    if (!std::isfinite(nu) || nu < 0.f || !std::isfinite(lambda) || lambda < 0.f)
+        return TWED_ERR_INVALID_ARG;
+    int64_t maxa = 0, tota = 0, maxb = 0, totb = 0;
+    if (!good_set(A, &maxa, &tota) || !good_set(B, &maxb, &totb)) return TWED_ERR_INVALID_ARG;
+
+    // layout inside the static array: control words, records, boundary rows
+    const bool same = (A->vals == B->vals && A->ts == B->ts && A->offs == B->offs);
+    const size_t rl = (size_t)twed::rec_len<float>(dim, p);
+    const size_t o_ctl = 0;  // [0] err, [1] sticky, [4..5] pair counter
+    const size_t o_ra = align_up(o_ctl + 64);
+    const size_t o_rb = same ? o_ra : align_up(o_ra + sizeof(float) * rl * (size_t)tota);
+    const size_t o_rows = align_up(o_rb + sizeof(float) * rl * (size_t)totb);
+    const int64_t scols = std::max(maxa, maxb);
+    const size_t row_bytes = sizeof(float) * 2 * (size_t)scols;
+    if (o_rows > kScratchBytes) return TWED_ERR_UNSUPPORTED;
+    const int64_t fit_warps = (int64_t)((kScratchBytes - o_rows) / row_bytes);
+    if (fit_warps < kWarpsPerBlock) return TWED_ERR_UNSUPPORTED;
+
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return TWED_ERR_CUDA;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return TWED_ERR_CUDA;
+    unsigned char* base = nullptr;
+    if (scratch_address(dev, &base) != cudaSuccess) return TWED_ERR_CUDA;
+
+    const int per_sm = std::max(1, twed::pairs_blocks_per_sm<float>(dim, p, kThreads));
+    int64_t blocks = std::min<int64_t>((int64_t)per_sm * sms, (npairs + kWarpsPerBlock - 1) / kWarpsPerBlock);
+    blocks = std::min<int64_t>(blocks, fit_warps / kWarpsPerBlock);
+    blocks = std::max<int64_t>(blocks, 1);
+
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned* ctl = reinterpret_cast<unsigned*>(base + o_ctl);
+    // the array keeps the previous call's contents: zero the control words
+    if (cudaMemsetAsync(ctl, 0, 64, st) != cudaSuccess) return TWED_ERR_CUDA;
+    float* rec_a = reinterpret_cast<float*>(base + o_ra);
+    float* rec_b = reinterpret_cast<float*>(base + o_rb);
+    twed::RecordsArgs<float> ra{A->vals, A->ts, A->offs, A->n, tota, dim, p, nu, lambda, rec_a};
+    if (twed::launch_records(ra, st) != cudaSuccess) return TWED_ERR_CUDA;
+    if (!same) {
+        twed::RecordsArgs<float> rb{B->vals, B->ts, B->offs, B->n, totb, dim, p, nu, lambda, rec_b};
+        if (twed::launch_records(rb, st) != cudaSuccess) return TWED_ERR_CUDA;
+    }
+    twed::PairsArgs<float> pa{};
+    pa.rec_a = rec_a;
+    pa.rec_b = rec_b;
+    pa.vals_a = A->vals;
+    pa.vals_b = B->vals;
+    pa.offs_a = A->offs;
+    pa.offs_b = B->offs;
+    pa.mode = twed::kExplicitPairs;
+    pa.pairs = d_pairs;
+    pa.npairs = npairs;
+    pa.na = A->n;
+    pa.nb = B->n;
+    pa.dim = dim;
+    pa.p = p;
+    pa.rmax = twed::pairs_rmax_limit<float>();
+    pa.nu = nu;
+    pa.out = d_out;
+    pa.counter = reinterpret_cast<unsigned long long*>(ctl + 4);
+    pa.scratch = base + o_rows;
+    pa.scratch_cols = scols;
+    pa.sc.err = ctl;
+    pa.sc.sticky = ctl + 1;
+    pa.sc.timeout_ns = 2000000000ull;
+    pa.sc.stall_strip = -1;
+    if (twed::launch_pairs(pa, (int)blocks, kThreads, st) != cudaSuccess) return TWED_ERR_CUDA;
+    return TWED_OK;
+}

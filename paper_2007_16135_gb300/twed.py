@@ -33,7 +33,7 @@ EXPORTS = (
     "twed_create", "twed_destroy", "twed_last_error", "twed_version", "twed_sync_status",
     "twed_f64", "twed_f32", "twed_f32_ex",
     "twed_dev_f64", "twed_dev_f32", "twed_dev_f64_ex", "twed_dev_f32_ex",
-    "twed_batch_f64", "twed_batch_f32",
+    "twed_batch_f64", "twed_batch_f32", "twed_batch_f32_noalloc",
     "twed_allpairs_plan_create_f64", "twed_allpairs_plan_create_f32", "twed_plan_execute",
     "twed_plan_cells", "twed_plan_pairs", "twed_plan_kernel_ms", "twed_plan_describe",
     "twed_plan_destroy",
@@ -95,6 +95,7 @@ def load(path: str | None = None):
             "twed_dev_f32_ex": (ci, [P, P, P, i64, P, P, i64, ci, f, f, ci, P, P, P]),
             "twed_batch_f64": (ci, [P, P, P, P, i64, ci, d, d, ci, P, P]),
             "twed_batch_f32": (ci, [P, P, P, P, i64, ci, f, f, ci, P, P]),
+            "twed_batch_f32_noalloc": (ci, [P, P, P, i64, ci, f, f, ci, P, P]),
             "twed_allpairs_plan_create_f64": (ci, [P, P, P, ci, d, d, ci, P, P]),
             "twed_allpairs_plan_create_f32": (ci, [P, P, P, ci, f, f, ci, P, P]),
             "twed_plan_execute": (ci, [P, P, P]),
@@ -292,6 +293,25 @@ def twed_batch(A: DeviceSet, B: DeviceSet, pairs, nu, lam, p=2, out=None, stream
 
 twed_batch_f64 = twed_batch
 twed_batch_f32 = twed_batch
+
+
+def twed_batch_f32_noalloc(A: DeviceSet, B: DeviceSet, pairs, nu, lam, p=2, out=None,
+                           stream=None):
+    """As twed_batch for float32 sets, for callers that cannot allocate: the
+    library works in its one static device array (no handle, no cudaMalloc).
+    `out` (float32 device [k]) is allocated here only if not given."""
+    import torch
+    lib = load()
+    pairs = pairs.contiguous()
+    k = pairs.shape[0]
+    if out is None:
+        out = torch.empty(k, dtype=torch.float32, device=A.vals.device)
+    sa, sb = A.cstruct(), B.cstruct()
+    st = lib.twed_batch_f32_noalloc(ctypes.byref(sa), ctypes.byref(sb), _t_ptr(pairs), k, A.dim,
+                                    float(nu), float(lam), p, _t_ptr(out), _stream_ptr(stream))
+    if st != TWED_OK:
+        raise TwedError(st, "twed_batch_f32_noalloc failed")
+    return out
 
 
 class Plan:
