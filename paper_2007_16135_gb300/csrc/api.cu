@@ -158,6 +158,7 @@ int coop_rows_per_lane(twed_handle_t h, int64_t n, const twed_opts_t* o) {
 struct PairLayout {
     int R;
     int64_t nstrips;
+    int64_t ring_stride;
     size_t o_ra, o_rb, o_ring, o_flags, end;
 };
 constexpr int kRingSlots = 4;
@@ -173,7 +174,8 @@ PairLayout pair_layout(twed_handle_t h, int64_t n, int64_t m, int dim, int p,
     cv.off = base;
     L.o_ra = cv.take(sizeof(T) * rl * (size_t)n);
     L.o_rb = cv.take(sizeof(T) * rl * (size_t)m);
-    L.o_ring = cv.take(sizeof(T) * 2 * (size_t)kRingSlots * (size_t)m);
+    L.ring_stride = (m + 2) & ~(int64_t)1;  // >= m + 1, even
+    L.o_ring = cv.take(sizeof(T) * 2 * (size_t)kRingSlots * (size_t)L.ring_stride);
     L.o_flags = cv.take(sizeof(unsigned) * (size_t)(L.nstrips + 1));
     L.end = cv.off;
     return L;
@@ -225,6 +227,7 @@ twed_status_t run_pair_dev(twed_handle_t h, const T* a, const T* ta, int64_t la,
     ca.nstrips = nstrips;
     ca.ring = base + o_ring;
     ca.nslot = nslot;
+    ca.ring_stride = L.ring_stride;
     ca.flags = flags;
     ca.strip_counter = flags + nstrips;
     ca.out = d_out;
@@ -542,7 +545,7 @@ twed_status_t plan_create(twed_handle_t h, const S* A, const S* B, int dim, T nu
     pl->blocks = (int)std::min(want_blocks, need_blocks);
     pl->threads = threads;
     const int64_t nwarps = (int64_t)pl->blocks * (threads / 32);
-    const int64_t scols = std::max(maxa, maxb);
+    const int64_t scols = (std::max(maxa, maxb) + 2) & ~(int64_t)1;  // >= longest + 1, even
 
     Carver cv;
     const size_t o_ra = cv.take(sizeof(T) * rl * (size_t)tota);
@@ -720,7 +723,7 @@ twed_status_t batch_impl(twed_handle_t h, const S* A, const S* B, const int64_t*
     const int per_sm = std::max(1, twed::pairs_blocks_per_sm<T>(dim, p, threads));
     const int blocks = (int)std::min<int64_t>((int64_t)per_sm * h->sms, (npairs + 3) / 4);
     const int64_t nwarps = (int64_t)blocks * (threads / 32);
-    const int64_t scols = std::max(maxa, maxb);
+    const int64_t scols = (std::max(maxa, maxb) + 2) & ~(int64_t)1;  // >= longest + 1, even
     Carver cv;
     const size_t o_ra = cv.take(sizeof(T) * rl * (size_t)tota);
     const size_t o_rb = same ? o_ra : cv.take(sizeof(T) * rl * (size_t)totb);

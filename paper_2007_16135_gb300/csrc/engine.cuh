@@ -91,14 +91,18 @@ struct Arith<float> {
 
 // ------------------------------------------------------------- point records
 // The prologue packs every point into one 16-byte aligned record:
-//   [v_0 .. v_{DIM-1}, t, delete-cost, padding]
-// so that a lane fetches a whole column of B with DIM/4 + 1 vector loads.
+//   FP64:  [v_0 .. v_{DIM-1}, t, delete-cost, padding]
+//   FP32:  [v_0, v_0, v_1, v_1, .., v_{DIM-1}, v_{DIM-1}, t, delete-cost, padding]
+// so that a lane fetches a whole column of B with a few vector loads.  FP32
+// stores every component twice: a 64-bit load then yields the (b_k, b_k)
+// operand that the packed f32x2 instructions subtract from two rows at once.
 // DIM == 0 means "dimension known only at run time": the record then holds
 // only [t, delete-cost] and values are read from the caller's array.
 template <typename T, int DIM>
 struct Rec {
     static constexpr int kPer16 = 16 / (int)sizeof(T);
-    static constexpr int kVals = DIM > 0 ? DIM : 0;
+    static constexpr int kVS = (sizeof(T) == 4 && DIM > 0) ? 2 : 1;  // stride between components
+    static constexpr int kVals = DIM > 0 ? DIM * kVS : 0;
     static constexpr int kLen = (kVals + 2 + kPer16 - 1) / kPer16 * kPer16;
     static constexpr int kQ = kLen / kPer16;
     static constexpr int kT = kVals;

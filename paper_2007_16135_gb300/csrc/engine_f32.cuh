@@ -1,0 +1,274 @@
+// FP32 wavefront engine with staged columns and packed row pairs.
+//
+// Same strip/lane/step mapping and boundary-row protocol as run_strip in
+// engine.cuh (see there for the correspondence with the paper's
+// anti-diagonals), with three changes that cut the instructions per cell:
+//
+//  * Column records are staged per warp in a shared-memory ring of 128
+//    columns.  Every 32 steps each lane issues cp.async copies of one column
+//    (32 columns ahead of lane 0), so a step reads its column with a few
+//    shared-memory vector loads and no prefetch registers.  The boundary row
+//    above the strip is staged the same way (16 lanes copy two columns each).
+//  * For p = 2 two rows share one packed f32x2 subtract / multiply-add per
+//    component: the record stores each component twice, so a 64-bit load is
+//    the (b_k, b_k) operand.
+//  * The three-way minimum is one three-input min instruction.
+#pragma once
+
+#include "engine.cuh"
+
+namespace twed {
+
+// ---------------------------------------------------------------- f32x2
+__device__ __forceinline__ unsigned long long f2_sub(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long f2_mul(unsigned long long a, unsigned long long b) {
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
+                                                     unsigned long long c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ unsigned long long f2_pack(float lo, float hi) {
+    unsigned long long d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+    return d;
+}
+__device__ __forceinline__ void f2_unpack(unsigned long long x, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(x));
+}
+__device__ __forceinline__ float min3f(float a, float b, float c) {
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
+// ---------------------------------------------------------------- cp.async
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+constexpr int kRingCols = 128;  // staged columns per warp (power of two)
+
+// Shared memory one warp needs for DIM (bytes).
+template <int DIM>
+__host__ __device__ constexpr int staged_bytes_per_warp() {
+    return kRingCols * (Rec<float, DIM>::kLen * 4 + 8);
+}
+
+// One strip (rows r0 .. r0+rows-1, rows <= 32*R) of an FP32 pair with the
+// dimension known at compile time.  `ring` / `bring` are this warp's staging
+// areas (kRingCols records, kRingCols (D, c) pairs).  Boundary rows `io.up`
+// must have at least m+1 readable (D, c) pairs (the copy of the last column
+// pair may read one past m).
+template <int DIM, int P, int R>
+__device__ __forceinline__ bool run_strip_staged(const PairRef<float>& pr, int r0, int rows,
+                                                 const StripIO<float>& io, const SyncCtl& sc,
+                                                 float* result_a, float* result_b, float* ring,
+                                                 float2* bring) {
+    static_assert(DIM > 0, "staged engine needs a compile-time dimension");
+    using RL = Rec<float, DIM>;
+    constexpr int LEN = RL::kLen;
+    constexpr bool PACK = (P == 2 && DIM >= 2 && (R % 2) == 0);
+    const int lane = threadIdx.x & 31;
+    const float INF = __int_as_float(0x7f800000);
+    const int m = pr.m;
+    const bool first = (io.up == nullptr);
+    const int lanes_used = (rows + R - 1) / R;
+    const float* gcol = pr.rec_b + pr.b_first * LEN;  // column j at gcol + (j-1)*LEN
+
+    // ---- rows: points (packed in pairs for p = 2), times, deletion costs
+    constexpr int NPR = PACK ? R / 2 : 1;
+    constexpr int NSC = PACK ? 1 : R;
+    unsigned long long A2[NPR][DIM];
+    float ra[NSC][DIM];
+    float rt[R], rdel[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        int i = r0 + lane * R + r;
+        i = i < pr.n ? i : pr.n;  // rows past n repeat row n; never used
+        const float4* p = reinterpret_cast<const float4*>(pr.rec_a + (pr.a_first + i - 1) * LEN);
+        float rec[LEN];
+#pragma unroll
+        for (int q = 0; q < LEN / 4; ++q) {
+            const float4 v = __ldg(p + q);
+            rec[4 * q] = v.x;
+            rec[4 * q + 1] = v.y;
+            rec[4 * q + 2] = v.z;
+            rec[4 * q + 3] = v.w;
+        }
+        rt[r] = rec[RL::kT];
+        rdel[r] = rec[RL::kDel];
+        if constexpr (PACK) {
+            if (r & 1) {
+#pragma unroll
+                for (int k = 0; k < DIM; ++k) {
+                    float lo, hi;
+                    f2_unpack(A2[r / 2][k], lo, hi);
+                    A2[r / 2][k] = f2_pack(lo, rec[2 * k]);
+                }
+            } else {
+#pragma unroll
+                for (int k = 0; k < DIM; ++k) A2[r / 2][k] = f2_pack(rec[2 * k], 0.f);
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) ra[r][k] = rec[2 * k];
+        }
+    }
+    float Dl[R], cp[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        Dl[r] = INF;  // D(i, 0)
+        cp[r] = 0.f;
+    }
+    float diagD = (r0 == 1 && lane == 0) ? 0.f : INF;
+    float diagC = 0.f;
+    float botD = INF, botC = 0.f;
+
+    // ---- staging of 32-column chunks (chunk c = columns 32c+1 .. 32c+32)
+    auto issue = [&](int c) {
+        const int j = 32 * c + 1 + lane;
+        if (j <= m) {
+            const float* src = gcol + (int64_t)(j - 1) * LEN;
+            float* dst = ring + ((j - 1) & (kRingCols - 1)) * LEN;
+#pragma unroll
+            for (int q = 0; q < LEN / 4; ++q) cp_async16(dst + 4 * q, src + 4 * q);
+        }
+        if (!first && lane < 16) {
+            const int jj = 32 * c + 1 + 2 * lane;  // columns jj, jj+1 (jj-1 even: 16-B aligned)
+            if (jj <= m) cp_async16(bring + ((jj - 1) & (kRingCols - 1)), io.up + (jj - 1));
+        }
+        cp_async_commit();
+    };
+    if (!first && io.up_flag != nullptr) {
+        const bool w = wait_progress(io.up_flag, (unsigned)min(32, m), sc);
+        if (!__all_sync(kFull, w)) return false;
+    }
+    issue(0);
+
+    const int steps = m + lanes_used - 1;
+    int j = 1 - lane;
+    for (int s = 0; s < steps; ++s, ++j) {
+        if ((s & 31) == 0) {
+            // chunk s/32 (issued 32 steps ago) must have landed; then stage the next one
+            cp_async_wait_all();
+            __syncwarp();
+            const int c = (s >> 5) + 1;
+            if (32 * c + 1 <= m) {
+                if (!first && io.up_flag != nullptr) {
+                    const bool w = wait_progress(io.up_flag, (unsigned)min(32 * c + 32, m), sc);
+                    if (__any_sync(kFull, !w)) {
+                        cp_async_wait_all();
+                        return false;
+                    }
+                }
+                issue(c);
+            }
+        }
+        float upD = __shfl_up_sync(kFull, botD, 1);
+        float upC = __shfl_up_sync(kFull, botC, 1);
+        if (j >= 1 && j <= m) {
+            const int slot = (j - 1) & (kRingCols - 1);
+            const float4* rp = reinterpret_cast<const float4*>(ring + slot * LEN);
+            float rec[LEN];
+#pragma unroll
+            for (int q = 0; q < LEN / 4; ++q) {
+                const float4 v = rp[q];
+                rec[4 * q] = v.x;
+                rec[4 * q + 1] = v.y;
+                rec[4 * q + 2] = v.z;
+                rec[4 * q + 3] = v.w;
+            }
+            const float2 bnd = bring[slot];
+            if (lane == 0) {
+                upD = first ? INF : bnd.x;  // D(r0-1, j)
+                upC = first ? 0.f : bnd.y;  // c(r0-1, j)
+            }
+            const float tb = rec[RL::kT];
+            const float delb = rec[RL::kDel];
+            float d_up = upD, d_dg = diagD, c_dg = diagC;
+            if constexpr (PACK) {
+                unsigned long long B2[DIM];
+#pragma unroll
+                for (int k = 0; k < DIM; ++k) B2[k] = f2_pack(rec[2 * k], rec[2 * k + 1]);
+#pragma unroll
+                for (int q = 0; q < R / 2; ++q) {
+                    unsigned long long d2 = f2_sub(A2[q][0], B2[0]);
+                    unsigned long long s2 = f2_mul(d2, d2);
+#pragma unroll
+                    for (int k = 1; k < DIM; ++k) {
+                        d2 = f2_sub(A2[q][k], B2[k]);
+                        s2 = f2_fma(d2, d2, s2);
+                    }
+                    float s0, s1;
+                    f2_unpack(s2, s0, s1);
+                    const int r = 2 * q;
+                    const float c0 = fmaf(pr.nu, fabsf(rt[r] - tb), Arith<float>::root(s0));
+                    const float c1 = fmaf(pr.nu, fabsf(rt[r + 1] - tb), Arith<float>::root(s1));
+                    const float oD0 = Dl[r], oC0 = cp[r], oD1 = Dl[r + 1], oC1 = cp[r + 1];
+                    const float v0 = min3f(d_up + rdel[r], oD0 + delb, (d_dg + c0) + c_dg);
+                    const float v1 = min3f(v0 + rdel[r + 1], oD1 + delb, (oD0 + c1) + oC0);
+                    Dl[r] = v0;
+                    cp[r] = c0;
+                    Dl[r + 1] = v1;
+                    cp[r + 1] = c1;
+                    d_up = v1;
+                    d_dg = oD1;
+                    c_dg = oC1;
+                }
+            } else {
+                float bv[DIM];
+#pragma unroll
+                for (int k = 0; k < DIM; ++k) bv[k] = rec[2 * k];
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const float dd = dist<float, DIM, P>(ra[r], bv, DIM, pr.p);
+                    const float c = fmaf(pr.nu, fabsf(rt[r] - tb), dd);
+                    const float oD = Dl[r], oC = cp[r];
+                    const float v = min3f(d_up + rdel[r], oD + delb, (d_dg + c) + c_dg);
+                    Dl[r] = v;
+                    cp[r] = c;
+                    d_up = v;
+                    d_dg = oD;
+                    c_dg = oC;
+                }
+            }
+            diagD = upD;
+            diagC = upC;
+            botD = Dl[R - 1];
+            botC = cp[R - 1];
+            if (io.down != nullptr && lane == 31) {
+                __stcg(io.down + (j - 1), make_float2(botD, botC));
+                if (io.down_flag != nullptr && io.publish && (((j & 31) == 0) || j == m))
+                    st_release(io.down_flag, (unsigned)j);
+            }
+            if (j == m) {
+                const int rr = pr.n - r0 - lane * R;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    if (r == rr) {
+                        if (result_a) *result_a = Dl[r];
+                        if (result_b) *result_b = Dl[r];
+                    }
+                }
+            }
+        }
+        __syncwarp();
+    }
+    cp_async_wait_all();
+    __syncwarp();
+    return true;
+}
+
+}  // namespace twed

@@ -3,8 +3,34 @@
 #pragma once
 
 #include "engine.cuh"
+#include "engine_f32.cuh"
 
 namespace twed {
+
+// FP32 with a compile-time dimension runs the staged engine (engine_f32.cuh);
+// FP64 and run-time dimensions run run_strip (engine.cuh).
+template <typename T, int DIM>
+constexpr bool kStaged = (sizeof(T) == 4 && DIM > 0);
+
+template <typename T, int DIM>
+__host__ __device__ constexpr int smem_per_warp() {
+    if constexpr (kStaged<T, DIM>) return staged_bytes_per_warp<DIM>();
+    else return 0;
+}
+
+template <typename T, int DIM, int P, int R>
+__device__ __forceinline__ bool strip_call(const PairRef<T>& pr, int r0, int rows,
+                                           const StripIO<T>& io, const SyncCtl& sc, T* o1, T* o2,
+                                           unsigned char* wsmem) {
+    if constexpr (kStaged<T, DIM>) {
+        float* ring = reinterpret_cast<float*>(wsmem);
+        float2* bring = reinterpret_cast<float2*>(wsmem + kRingCols * Rec<float, DIM>::kLen * 4);
+        return run_strip_staged<DIM, P, R>(pr, r0, rows, io, sc, o1, o2, ring, bring);
+    } else {
+        (void)wsmem;
+        return run_strip<T, DIM, P, R>(pr, r0, rows, io, sc, o1, o2);
+    }
+}
 
 // ------------------------------------------------------------------ prologue
 // Step 1 of the paper's algorithm: the O(n) deletion costs of every series,
@@ -36,7 +62,8 @@ __global__ void __launch_bounds__(256) records_kernel(RecordsArgs<T> a) {
             for (int k = 0; k < DIM; ++k) {
                 x[k] = a.vals[g * DIM + k];
                 y[k] = first ? T(0) : a.vals[(g - 1) * DIM + k];
-                out[k] = x[k];
+#pragma unroll
+                for (int u = 0; u < RL::kVS; ++u) out[k * RL::kVS + u] = x[k];
             }
             d = dist<T, DIM, P>(x, y, DIM, a.p);
         } else {
@@ -79,6 +106,8 @@ __global__ void __launch_bounds__(256) records_kernel(RecordsArgs<T> a) {
 template <typename T, int DIM, int P, int R>
 __global__ void __launch_bounds__(128) coop_kernel(CoopArgs<T> a) {
     using V2 = typename Pair2<T>::V;
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    unsigned char* wsmem = dyn_smem + (threadIdx.x >> 5) * smem_per_warp<T, DIM>();
     const int lane = threadIdx.x & 31;
     PairRef<T> pr;
     pr.rec_a = a.rec_a;
@@ -102,13 +131,13 @@ __global__ void __launch_bounds__(128) coop_kernel(CoopArgs<T> a) {
         const int r0 = (int)k * 32 * R + 1;
         const int rows = min(32 * R, a.n - r0 + 1);
         StripIO<T> io;
-        io.up = k == 0 ? nullptr : ring + (int64_t)((k - 1) % a.nslot) * a.m;
+        io.up = k == 0 ? nullptr : ring + (int64_t)((k - 1) % a.nslot) * a.ring_stride;
         io.up_flag = k == 0 ? nullptr : a.flags + (k - 1);
         const bool last = (int64_t)k == a.nstrips - 1;
-        io.down = last ? nullptr : ring + (int64_t)(k % a.nslot) * a.m;
+        io.down = last ? nullptr : ring + (int64_t)(k % a.nslot) * a.ring_stride;
         io.down_flag = last ? nullptr : a.flags + k;
         io.publish = (long long)k != a.sc.stall_strip;
-        if (!run_strip<T, DIM, P, R>(pr, r0, rows, io, a.sc, a.out, nullptr)) break;
+        if (!strip_call<T, DIM, P, R>(pr, r0, rows, io, a.sc, a.out, nullptr, wsmem)) break;
     }
 }
 
@@ -126,16 +155,13 @@ __device__ __forceinline__ void triangle_pos(int64_t w, int64_t n, int64_t& p, i
     q = w - r * (2 * n - r - 1) / 2 + r + 1;
 }
 
-template <typename T, int DIM, int P, int R>
-__device__ __forceinline__ bool pair_strip(const PairRef<T>& pr, int r0, int rows,
-                                           const StripIO<T>& io, const SyncCtl& sc, T* o1,
-                                           T* o2) {
-    return run_strip<T, DIM, P, R>(pr, r0, rows, io, sc, o1, o2);
-}
-
 template <typename T, int DIM, int P, int RMAX>
 __global__ void __launch_bounds__(128) pairs_kernel(PairsArgs<T> a) {
     using V2 = typename Pair2<T>::V;
+    // packed row pairs need an even number of rows per lane
+    constexpr bool kEven = kStaged<T, DIM> && P == 2 && DIM >= 2;
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    unsigned char* wsmem = dyn_smem + (threadIdx.x >> 5) * smem_per_warp<T, DIM>();
     const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     V2* row = reinterpret_cast<V2*>(a.scratch) + gw * a.scratch_cols;
@@ -183,7 +209,8 @@ __global__ void __launch_bounds__(128) pairs_kernel(PairsArgs<T> a) {
         int r0 = 1;
         while (r0 <= pr.n) {
             const int left = pr.n - r0 + 1;
-            const int R = left >= 32 * rmax ? rmax : (left + 31) / 32;
+            int R = left >= 32 * rmax ? rmax : (left + 31) / 32;
+            if (kEven) R = min((R + 1) & ~1, rmax);
             const int rows = min(left, 32 * R);
             const bool last = r0 + rows > pr.n;
             StripIO<T> io;
@@ -193,14 +220,14 @@ __global__ void __launch_bounds__(128) pairs_kernel(PairsArgs<T> a) {
             io.down_flag = nullptr;
             io.publish = true;
             switch (R) {
-                case 1: pair_strip<T, DIM, P, 1>(pr, r0, rows, io, a.sc, o1, o2); break;
-                case 2: if constexpr (RMAX >= 2) pair_strip<T, DIM, P, 2>(pr, r0, rows, io, a.sc, o1, o2); break;
-                case 3: if constexpr (RMAX >= 3) pair_strip<T, DIM, P, 3>(pr, r0, rows, io, a.sc, o1, o2); break;
-                case 4: if constexpr (RMAX >= 4) pair_strip<T, DIM, P, 4>(pr, r0, rows, io, a.sc, o1, o2); break;
-                case 5: if constexpr (RMAX >= 5) pair_strip<T, DIM, P, 5>(pr, r0, rows, io, a.sc, o1, o2); break;
-                case 6: if constexpr (RMAX >= 6) pair_strip<T, DIM, P, 6>(pr, r0, rows, io, a.sc, o1, o2); break;
-                case 7: if constexpr (RMAX >= 7) pair_strip<T, DIM, P, 7>(pr, r0, rows, io, a.sc, o1, o2); break;
-                case 8: if constexpr (RMAX >= 8) pair_strip<T, DIM, P, 8>(pr, r0, rows, io, a.sc, o1, o2); break;
+                case 1: if constexpr (!kEven) strip_call<T, DIM, P, 1>(pr, r0, rows, io, a.sc, o1, o2, wsmem); break;
+                case 2: if constexpr (RMAX >= 2) strip_call<T, DIM, P, 2>(pr, r0, rows, io, a.sc, o1, o2, wsmem); break;
+                case 3: if constexpr (RMAX >= 3 && !kEven) strip_call<T, DIM, P, 3>(pr, r0, rows, io, a.sc, o1, o2, wsmem); break;
+                case 4: if constexpr (RMAX >= 4) strip_call<T, DIM, P, 4>(pr, r0, rows, io, a.sc, o1, o2, wsmem); break;
+                case 5: if constexpr (RMAX >= 5 && !kEven) strip_call<T, DIM, P, 5>(pr, r0, rows, io, a.sc, o1, o2, wsmem); break;
+                case 6: if constexpr (RMAX >= 6) strip_call<T, DIM, P, 6>(pr, r0, rows, io, a.sc, o1, o2, wsmem); break;
+                case 7: if constexpr (RMAX >= 7 && !kEven) strip_call<T, DIM, P, 7>(pr, r0, rows, io, a.sc, o1, o2, wsmem); break;
+                case 8: if constexpr (RMAX >= 8) strip_call<T, DIM, P, 8>(pr, r0, rows, io, a.sc, o1, o2, wsmem); break;
                 default: break;
             }
             r0 += rows;
@@ -251,41 +278,71 @@ cudaError_t launch_records_t(const RecordsArgs<T>& a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// Launch (or size) a kernel with `threads` threads and its per-warp dynamic
+// shared memory; the opt-in above 48 KB is set on every call (cheap).
+template <typename K>
+cudaError_t prepare_smem(K kernel, int smem) {
+    if (smem <= 48 * 1024) return cudaSuccess;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
+template <typename K, typename A>
+cudaError_t launch_with_smem(K kernel, int smem_warp, int blocks, int threads, cudaStream_t st,
+                             const A& a) {
+    const int smem = smem_warp * (threads / 32);
+    cudaError_t e = prepare_smem(kernel, smem);
+    if (e != cudaSuccess) return e;
+    kernel<<<blocks, threads, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename K>
+int blocks_per_sm(K kernel, int smem_warp, int threads) {
+    const int smem = smem_warp * (threads / 32);
+    if (prepare_smem(kernel, smem) != cudaSuccess) return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, smem) != cudaSuccess) return 0;
+    return nb;
+}
+
 template <typename T, int RMAX_LIMIT>
 cudaError_t launch_pairs_t(const PairsArgs<T>& a, int blocks, int threads, cudaStream_t st) {
     if (a.npairs <= 0) return cudaSuccess;
-    TWED_DISPATCH(a.dim, a.p, (pairs_kernel<T, DIM_, P_, RMAX_LIMIT><<<blocks, threads, 0, st>>>(a)));
-    return cudaGetLastError();
+    cudaError_t e = cudaSuccess;
+    TWED_DISPATCH(a.dim, a.p, (e = launch_with_smem(pairs_kernel<T, DIM_, P_, RMAX_LIMIT>,
+                                                    smem_per_warp<T, DIM_>(), blocks, threads, st, a)));
+    return e;
 }
 
 template <typename T, int RMAX_LIMIT>
 int pairs_blocks_per_sm_t(int dim, int p, int threads) {
     int nb = 0;
-    TWED_DISPATCH(dim, p, (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-                               &nb, pairs_kernel<T, DIM_, P_, RMAX_LIMIT>, threads, 0)));
+    TWED_DISPATCH(dim, p, (nb = blocks_per_sm(pairs_kernel<T, DIM_, P_, RMAX_LIMIT>,
+                                              smem_per_warp<T, DIM_>(), threads)));
     return nb;
 }
 
 template <typename T>
 cudaError_t launch_coop_t(const CoopArgs<T>& a, int R, int blocks, int threads, cudaStream_t st) {
+    cudaError_t e = cudaSuccess;
     switch (R) {
-        case 1: TWED_DISPATCH(a.dim, a.p, (coop_kernel<T, DIM_, P_, 1><<<blocks, threads, 0, st>>>(a))); break;
-        case 2: TWED_DISPATCH(a.dim, a.p, (coop_kernel<T, DIM_, P_, 2><<<blocks, threads, 0, st>>>(a))); break;
-        case 4: TWED_DISPATCH(a.dim, a.p, (coop_kernel<T, DIM_, P_, 4><<<blocks, threads, 0, st>>>(a))); break;
-        case 8: TWED_DISPATCH(a.dim, a.p, (coop_kernel<T, DIM_, P_, 8><<<blocks, threads, 0, st>>>(a))); break;
+        case 1: TWED_DISPATCH(a.dim, a.p, (e = launch_with_smem(coop_kernel<T, DIM_, P_, 1>, smem_per_warp<T, DIM_>(), blocks, threads, st, a))); break;
+        case 2: TWED_DISPATCH(a.dim, a.p, (e = launch_with_smem(coop_kernel<T, DIM_, P_, 2>, smem_per_warp<T, DIM_>(), blocks, threads, st, a))); break;
+        case 4: TWED_DISPATCH(a.dim, a.p, (e = launch_with_smem(coop_kernel<T, DIM_, P_, 4>, smem_per_warp<T, DIM_>(), blocks, threads, st, a))); break;
+        case 8: TWED_DISPATCH(a.dim, a.p, (e = launch_with_smem(coop_kernel<T, DIM_, P_, 8>, smem_per_warp<T, DIM_>(), blocks, threads, st, a))); break;
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
+    return e;
 }
 
 template <typename T>
 int coop_blocks_per_sm_t(int dim, int p, int R, int threads) {
     int nb = 0;
     switch (R) {
-        case 1: TWED_DISPATCH(dim, p, (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, coop_kernel<T, DIM_, P_, 1>, threads, 0))); break;
-        case 2: TWED_DISPATCH(dim, p, (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, coop_kernel<T, DIM_, P_, 2>, threads, 0))); break;
-        case 4: TWED_DISPATCH(dim, p, (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, coop_kernel<T, DIM_, P_, 4>, threads, 0))); break;
-        case 8: TWED_DISPATCH(dim, p, (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, coop_kernel<T, DIM_, P_, 8>, threads, 0))); break;
+        case 1: TWED_DISPATCH(dim, p, (nb = blocks_per_sm(coop_kernel<T, DIM_, P_, 1>, smem_per_warp<T, DIM_>(), threads))); break;
+        case 2: TWED_DISPATCH(dim, p, (nb = blocks_per_sm(coop_kernel<T, DIM_, P_, 2>, smem_per_warp<T, DIM_>(), threads))); break;
+        case 4: TWED_DISPATCH(dim, p, (nb = blocks_per_sm(coop_kernel<T, DIM_, P_, 4>, smem_per_warp<T, DIM_>(), threads))); break;
+        case 8: TWED_DISPATCH(dim, p, (nb = blocks_per_sm(coop_kernel<T, DIM_, P_, 8>, smem_per_warp<T, DIM_>(), threads))); break;
         default: break;
     }
     return nb;

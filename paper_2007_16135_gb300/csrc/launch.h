@@ -40,8 +40,9 @@ struct CoopArgs {
     int n, m, dim, p;
     T nu;
     int64_t nstrips;
-    void* ring;            // [nslot][m] pairs (D, c) of strip bottom rows
+    void* ring;            // [nslot][ring_stride] pairs (D, c) of strip bottom rows
     int nslot;
+    int64_t ring_stride;   // >= m + 1, even (a staged copy may read one pair past m)
     unsigned* flags;       // [nstrips] published columns per strip
     unsigned* strip_counter;
     T* out;                // D(n, m)
@@ -69,7 +70,7 @@ struct PairsArgs {
     T* out;
     unsigned long long* counter;
     void* scratch;           // per warp: one boundary row of `scratch_cols` (D, c) pairs
-    int64_t scratch_cols;
+    int64_t scratch_cols;    // >= longest series + 1, even
     SyncCtl sc;
 };
 

@@ -80,7 +80,7 @@ extern "C" twed_status_t twed_batch_f32_noalloc(const twed_set_f32_t* A, const t
     const size_t o_ra = align_up(o_ctl + 64);
     const size_t o_rb = same ? o_ra : align_up(o_ra + sizeof(float) * rl * (size_t)tota);
     const size_t o_rows = align_up(o_rb + sizeof(float) * rl * (size_t)totb);
-    const int64_t scols = std::max(maxa, maxb);
+    const int64_t scols = (std::max(maxa, maxb) + 2) & ~(int64_t)1;  // >= longest + 1, even
     const size_t row_bytes = sizeof(float) * 2 * (size_t)scols;
     if (o_rows > kScratchBytes) return TWED_ERR_UNSUPPORTED;
     const int64_t fit_warps = (int64_t)((kScratchBytes - o_rows) / row_bytes);
