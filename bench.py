@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--dtype", choices=["f32", "f64"], default=None)
     ap.add_argument("--n", type=int, default=None, help="series length override (w1/w2)")
     ap.add_argument("--nseries", type=int, default=4096, help="w3 set size (profiling runs)")
+    ap.add_argument("--accum", choices=["auto", "f32", "kahan"], default="auto",
+                    help="w2 FP32 running-cost accumulation")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -291,15 +293,18 @@ def bench_pair(args, rank, world, dev, workload):
     A, TA, B, TB = dv(a), dv(ta), dv(b), dv(tb)
     out = torch.empty(1, dtype=td, device=dev)
     stream = torch.cuda.current_stream()
+    accum = {"auto": twed.ACCUM_AUTO, "f32": twed.ACCUM_F32, "kahan": twed.ACCUM_KAHAN}[args.accum]
+    opts = twed.make_opts(accum=accum)
+    kahan = dtype == "f32" and (args.accum == "kahan" or (args.accum == "auto" and 2 * n > 100000))
     for _ in range(args.warmup):
-        twed.twed_dev(A, TA, B, TB, nu, lam, p, out=out, stream=stream)
+        twed.twed_dev(A, TA, B, TB, nu, lam, p, out=out, stream=stream, opts=opts)
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(torch.cuda.current_device()) as clk:
         barrier(world)
         ev0.record(stream)
         for _ in range(args.steps):
-            twed.twed_dev(A, TA, B, TB, nu, lam, p, out=out, stream=stream)
+            twed.twed_dev(A, TA, B, TB, nu, lam, p, out=out, stream=stream, opts=opts)
         ev1.record(stream)
         torch.cuda.synchronize()
         barrier(world)
@@ -318,7 +323,9 @@ def bench_pair(args, rank, world, dev, workload):
                            "peak": peak / 1e12, "unit": "Top/s",
                            "frac": cells * opc / (ms / 1e3) / peak, "traffic": None,
                            "ops_per_cell": opc, "kernel": f"coop_kernel<float,{dim},2,R>"}
-    res["config"] = {"workload": f"{workload} one pair n=m={n}, dim {dim}, {dtype}", "n": n,
+    res["config"] = {"workload": f"{workload} one pair n=m={n}, dim {dim}, {dtype}"
+                                 + (", compensated (TwoSum) FP32 running cost" if kahan else ""),
+                     "n": n, "accumulation": "kahan" if kahan else dtype,
                      "l2": "one pair per step; records stream through L2"}
     return res
 

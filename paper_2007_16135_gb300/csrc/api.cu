@@ -154,20 +154,72 @@ int coop_rows_per_lane(twed_handle_t h, int64_t n, const twed_opts_t* o) {
     return 1;
 }
 
+// Band schedule (FP32, compiled point layouts): strips of 32*R rows, bands of
+// kBandWarps strips per block.  R is picked with a small cost model: a step
+// costs the larger of one warp's dependency chain and the SM's issue slots
+// shared by its active warps; consecutive strips start ~40 steps apart; bands
+// beyond the resident blocks run in further rounds.
+constexpr int kBandWarps = 8;
+
+int band_rows_per_lane(twed_handle_t h, int64_t n, int64_t m, int dim, int p, bool kahan,
+                       const twed_opts_t* o) {
+    if (o && o->rows_per_lane > 0) {
+        int r = o->rows_per_lane;
+        return r >= 8 ? 8 : r >= 4 ? 4 : r >= 2 ? 2 : 1;
+    }
+    const double c_row = (dim > 1 ? dim : 2) + 9.0 + (kahan ? 35.0 : 0.0);  // instructions per row
+    const double c_step = 24.0;                                          // per step, per warp
+    const double lat_row = kahan ? 40.0 : 8.0;                           // chain cycles per row
+    int best = 1;
+    double best_t = 1e300;
+    for (int R : {8, 4, 2, 1}) {
+        const int per_sm = twed::band_blocks_per_sm(dim, p, R, kahan, kBandWarps);
+        if (per_sm < 1) continue;
+        const double nstrips = std::ceil((double)n / (32.0 * R));
+        const double nbands = std::ceil(nstrips / kBandWarps);
+        const double conc = (double)per_sm * h->sms;
+        const double rounds = std::ceil(nbands / conc);
+        const double active = std::min(nbands, conc);
+        const double warps_sm = active * kBandWarps / h->sms;
+        const double t_step = std::max(60.0 + lat_row * R, (c_row * R + c_step) * warps_sm / 4.0);
+        const double t = rounds * ((double)m + active * kBandWarps * 40.0) * t_step;
+        if (t < best_t) {
+            best_t = t;
+            best = R;
+        }
+    }
+    return best;
+}
+
 // Workspace layout of one pair (records, boundary ring, flags) from `base`.
 struct PairLayout {
     int R;
+    bool kahan;
+    bool band;  // block-cooperative FP32 schedule
     int64_t nstrips;
     int64_t ring_stride;
     size_t o_ra, o_rb, o_ring, o_flags, end;
 };
 constexpr int kRingSlots = 4;
 
+// Compensated FP32 running cost: requested, or automatic above 1e5 points
+// per pair (where plain FP32 sums along ~n+m steps start to drift).
+template <typename T>
+bool use_kahan(int64_t n, int64_t m, int dim, int p, const twed_opts_t* o) {
+    if (sizeof(T) != 4 || !twed::compiled_layout(dim, p)) return false;
+    const int acc = o ? o->accum : TWED_ACCUM_AUTO;
+    if (acc == TWED_ACCUM_KAHAN) return true;
+    if (acc == TWED_ACCUM_F32) return false;
+    return n + m > 100000;
+}
+
 template <typename T>
 PairLayout pair_layout(twed_handle_t h, int64_t n, int64_t m, int dim, int p,
                        const twed_opts_t* o, size_t base) {
     PairLayout L;
-    L.R = coop_rows_per_lane<T>(h, n, o);
+    L.kahan = use_kahan<T>(n, m, dim, p, o);
+    L.band = sizeof(T) == 4 && twed::compiled_layout(dim, p);
+    L.R = L.band ? band_rows_per_lane(h, n, m, dim, p, L.kahan, o) : coop_rows_per_lane<T>(h, n, o);
     L.nstrips = (n + 32 * L.R - 1) / (32 * L.R);
     const int rl = twed::rec_len<T>(dim, p);
     Carver cv;
@@ -175,7 +227,8 @@ PairLayout pair_layout(twed_handle_t h, int64_t n, int64_t m, int dim, int p,
     L.o_ra = cv.take(sizeof(T) * rl * (size_t)n);
     L.o_rb = cv.take(sizeof(T) * rl * (size_t)m);
     L.ring_stride = (m + 2) & ~(int64_t)1;  // >= m + 1, even
-    L.o_ring = cv.take(sizeof(T) * 2 * (size_t)kRingSlots * (size_t)L.ring_stride);
+    const size_t entry = L.kahan ? 16 : sizeof(T) * 2;
+    L.o_ring = cv.take(entry * (size_t)kRingSlots * (size_t)L.ring_stride);
     L.o_flags = cv.take(sizeof(unsigned) * (size_t)(L.nstrips + 1));
     L.end = cv.off;
     return L;
@@ -186,6 +239,11 @@ template <typename T>
 twed_status_t run_pair_dev(twed_handle_t h, const T* a, const T* ta, int64_t la, const T* b,
                            const T* tb, int64_t lb, int dim, T nu, T lambda, int p,
                            const twed_opts_t* o, T* d_out, cudaStream_t st, size_t ws_base) {
+    if (o && (o->accum < TWED_ACCUM_AUTO || o->accum > TWED_ACCUM_KAHAN))
+        return fail(h, TWED_ERR_INVALID_ARG, "unknown accumulation mode %d", o->accum);
+    if (o && o->accum == TWED_ACCUM_KAHAN && sizeof(T) == 4 && !twed::compiled_layout(dim, p))
+        return fail(h, TWED_ERR_UNSUPPORTED,
+                    "compensated FP32 needs dim in {1,2,3,4,8} and p in {1,2} (dim 1: any p)");
     // rows = the longer series: more strips, more warps in flight
     if (lb > la) {
         std::swap(a, b);
@@ -232,11 +290,23 @@ twed_status_t run_pair_dev(twed_handle_t h, const T* a, const T* ta, int64_t la,
     ca.strip_counter = flags + nstrips;
     ca.out = d_out;
     ca.sc = make_sync(h, o);
+    if constexpr (sizeof(T) == 4) {
+        if (L.band) {
+            const int per_sm = std::max(1, twed::band_blocks_per_sm(dim, p, R, L.kahan, kBandWarps));
+            const int64_t nbands = (nstrips + kBandWarps - 1) / kBandWarps;
+            const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(nbands, (int64_t)per_sm * h->sms));
+            const cudaError_t e = twed::launch_band(ca, R, L.kahan, (int)blocks, kBandWarps, st);
+            if (e != cudaSuccess)
+                return fail(h, TWED_ERR_CUDA, "band launch (dim %d, p %d, R %d, kahan %d, blocks %lld, per_sm %d): %s",
+                            dim, p, R, (int)L.kahan, (long long)blocks, per_sm, cudaGetErrorString(e));
+            return TWED_OK;
+        }
+    }
     const int threads = 128;
-    const int per_sm = std::max(1, twed::coop_blocks_per_sm<T>(dim, p, R, threads));
+    const int per_sm = std::max(1, twed::coop_blocks_per_sm<T>(dim, p, R, L.kahan, threads));
     int64_t blocks = std::min<int64_t>((nstrips + 3) / 4, (int64_t)per_sm * h->sms);
     blocks = std::max<int64_t>(1, blocks);
-    TWED_CUDA(h, twed::launch_coop(ca, R, (int)blocks, threads, st));
+    TWED_CUDA(h, twed::launch_coop(ca, R, L.kahan, (int)blocks, threads, st));
     return TWED_OK;
 }
 

@@ -251,12 +251,65 @@ __device__ __forceinline__ bool wait_progress(const unsigned* flag, unsigned tar
 template <typename T>
 struct StripIO {
     using V2 = typename Pair2<T>::V;
-    const V2* up;            // bottom row of the strip above (D, c) per column; unused if first
+    const V2* up;            // bottom row of the strip above (D, c) per column, global
     const unsigned* up_flag; // columns of `up` already published; nullptr = all ready
-    V2* down;                // this strip's bottom row; nullptr = nobody needs it
+    V2* down;                // this strip's bottom row, global; nullptr = nobody needs it
     unsigned* down_flag;     // progress of `down`; nullptr = no publication
     bool publish;            // false: skip publication (fault injection)
+    // Block-local hand-off (staged FP32 engine only): the warp above writes
+    // the row above straight into this warp's shared-memory boundary ring.
+    bool up_local;           // the row above arrives in this warp's ring
+    volatile int* up_prog;   // columns the warp above has written into it
+    volatile int* my_cons;   // columns of it this warp has consumed (back-pressure)
+    void* down_local;        // the warp below's boundary ring; nullptr = none
+    volatile int* down_prog; // its progress word
+    volatile int* down_cons; // its consumption word
 };
+
+template <typename T>
+__device__ __forceinline__ StripIO<T> strip_io_global(const typename Pair2<T>::V* up,
+                                                      const unsigned* up_flag,
+                                                      typename Pair2<T>::V* down,
+                                                      unsigned* down_flag, bool publish) {
+    StripIO<T> io;
+    io.up = up;
+    io.up_flag = up_flag;
+    io.down = down;
+    io.down_flag = down_flag;
+    io.publish = publish;
+    io.up_local = false;
+    io.up_prog = nullptr;
+    io.my_cons = nullptr;
+    io.down_local = nullptr;
+    io.down_prog = nullptr;
+    io.down_cons = nullptr;
+    return io;
+}
+
+// Bounded wait (whole warp) until *word >= target on a shared-memory word
+// written by another warp of the block.  Gives up, like wait_progress, on
+// the launch's error word or after timeout_ns.
+__device__ __forceinline__ bool wait_local(volatile int* word, int target, const SyncCtl& sc) {
+    if (*word >= target) {
+        __threadfence_block();
+        return true;
+    }
+    const unsigned long long t0 = globaltimer();
+    unsigned spins = 0;
+    while (*word < target) {
+        if ((++spins & 63u) == 0) {
+            if (*(volatile unsigned*)sc.err != 0u) return false;
+            if (globaltimer() - t0 > sc.timeout_ns) {
+                atomicCAS(sc.err, 0u, 4u /* TWED_ERR_TIMEOUT */);
+                atomicCAS(sc.sticky, 0u, 4u);
+                return false;
+            }
+        }
+        __nanosleep(32);
+    }
+    __threadfence_block();
+    return true;
+}
 
 // The series a strip works on.  Row i (1-based) of the DP is point
 // a_first + i - 1 of the row set; column j is point b_first + j - 1.

@@ -60,32 +60,75 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 
 constexpr int kRingCols = 128;  // staged columns per warp (power of two)
 
-// Shared memory one warp needs for DIM (bytes).
-template <int DIM>
+// Shared memory one warp needs for DIM (bytes).  The compensated variant
+// (KH) stages (D_hi, D_lo, c, 0) per boundary column instead of (D, c).
+template <int DIM, bool KH = false>
 __host__ __device__ constexpr int staged_bytes_per_warp() {
-    return kRingCols * (Rec<float, DIM>::kLen * 4 + 8);
+    return kRingCols * (Rec<float, DIM>::kLen * 4 + (KH ? 16 : 8));
+}
+
+// ---------------------------------------------------------------- TwoSum
+// s + e == a + b exactly (Knuth's TwoSum, no ordering assumption).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// Compensated running cost: D is carried as hi + lo.  Every candidate adds
+// FP32 costs with TwoSum and folds the rounding error into lo; the minimum is
+// taken on hi + lo.  An error-free border needs a finite sentinel (inf - inf
+// would poison TwoSum): kBig is far above any reachable cost.
+constexpr float kBig = 1.2676506e30f;  // 2^100
+
+__device__ __forceinline__ void kahan_cell(float uh, float ul, float lh, float ll, float dh,
+                                           float dl, float del_a, float del_b, float c,
+                                           float c_dg, float& oh, float& ol) {
+    float s1, e1, s2, e2, s3, e3, s4, e4;
+    two_sum(uh, del_a, s1, e1);
+    const float l1 = ul + e1;
+    const float v1 = s1 + l1;
+    two_sum(lh, del_b, s2, e2);
+    const float l2 = ll + e2;
+    const float v2 = s2 + l2;
+    two_sum(dh, c, s3, e3);
+    two_sum(s3, c_dg, s4, e4);
+    const float l3 = (dl + e3) + e4;
+    const float v3 = s4 + l3;
+    float h = s1, l = l1, v = v1;
+    if (v2 < v) { h = s2; l = l2; v = v2; }
+    if (v3 < v) { h = s4; l = l3; }
+    oh = h;
+    ol = l;
 }
 
 // One strip (rows r0 .. r0+rows-1, rows <= 32*R) of an FP32 pair with the
 // dimension known at compile time.  `ring` / `bring` are this warp's staging
-// areas (kRingCols records, kRingCols (D, c) pairs).  Boundary rows `io.up`
-// must have at least m+1 readable (D, c) pairs (the copy of the last column
-// pair may read one past m).
-template <int DIM, int P, int R>
+// areas (kRingCols records, kRingCols boundary entries).  Boundary rows hold
+// (D, c) float2 per column, or (D_hi, D_lo, c, 0) float4 when KH; `io.up`
+// must have at least m+1 readable entries (a staged copy may read one past m).
+template <int DIM, int P, int R, bool KH = false>
 __device__ __forceinline__ bool run_strip_staged(const PairRef<float>& pr, int r0, int rows,
                                                  const StripIO<float>& io, const SyncCtl& sc,
                                                  float* result_a, float* result_b, float* ring,
-                                                 float2* bring) {
+                                                 void* bring_v) {
     static_assert(DIM > 0, "staged engine needs a compile-time dimension");
     using RL = Rec<float, DIM>;
     constexpr int LEN = RL::kLen;
     constexpr bool PACK = (P == 2 && DIM >= 2 && (R % 2) == 0);
     const int lane = threadIdx.x & 31;
-    const float INF = __int_as_float(0x7f800000);
+    const float INF = KH ? kBig : __int_as_float(0x7f800000);
     const int m = pr.m;
-    const bool first = (io.up == nullptr);
+    const bool first = (io.up == nullptr && !io.up_local);
+    const bool up_global = (io.up != nullptr);
     const int lanes_used = (rows + R - 1) / R;
     const float* gcol = pr.rec_b + pr.b_first * LEN;  // column j at gcol + (j-1)*LEN
+    float2* bring2 = reinterpret_cast<float2*>(bring_v);
+    float4* bring4 = reinterpret_cast<float4*>(bring_v);
+    const float4* up4 = reinterpret_cast<const float4*>(io.up);
+    float4* down4 = reinterpret_cast<float4*>(io.down);
+    float2* dloc2 = reinterpret_cast<float2*>(io.down_local);  // the next warp's ring
+    float4* dloc4 = reinterpret_cast<float4*>(io.down_local);
 
     // ---- rows: points (packed in pairs for p = 2), times, deletion costs
     constexpr int NPR = PACK ? R / 2 : 1;
@@ -126,15 +169,16 @@ __device__ __forceinline__ bool run_strip_staged(const PairRef<float>& pr, int r
             for (int k = 0; k < DIM; ++k) ra[r][k] = rec[2 * k];
         }
     }
-    float Dl[R], cp[R];
+    float Dl[R], Dlo[KH ? R : 1], cp[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         Dl[r] = INF;  // D(i, 0)
+        if constexpr (KH) Dlo[r] = 0.f;
         cp[r] = 0.f;
     }
     float diagD = (r0 == 1 && lane == 0) ? 0.f : INF;
-    float diagC = 0.f;
-    float botD = INF, botC = 0.f;
+    float diagL = 0.f, diagC = 0.f;
+    float botD = INF, botL = 0.f, botC = 0.f;
 
     // ---- staging of 32-column chunks (chunk c = columns 32c+1 .. 32c+32)
     auto issue = [&](int c) {
@@ -145,13 +189,17 @@ __device__ __forceinline__ bool run_strip_staged(const PairRef<float>& pr, int r
 #pragma unroll
             for (int q = 0; q < LEN / 4; ++q) cp_async16(dst + 4 * q, src + 4 * q);
         }
-        if (!first && lane < 16) {
-            const int jj = 32 * c + 1 + 2 * lane;  // columns jj, jj+1 (jj-1 even: 16-B aligned)
-            if (jj <= m) cp_async16(bring + ((jj - 1) & (kRingCols - 1)), io.up + (jj - 1));
+        if (up_global) {
+            if constexpr (KH) {
+                if (j <= m) cp_async16(bring4 + ((j - 1) & (kRingCols - 1)), up4 + (j - 1));
+            } else if (lane < 16) {
+                const int jj = 32 * c + 1 + 2 * lane;  // columns jj, jj+1 (jj-1 even: 16-B aligned)
+                if (jj <= m) cp_async16(bring2 + ((jj - 1) & (kRingCols - 1)), io.up + (jj - 1));
+            }
         }
         cp_async_commit();
     };
-    if (!first && io.up_flag != nullptr) {
+    if (up_global && io.up_flag != nullptr) {
         const bool w = wait_progress(io.up_flag, (unsigned)min(32, m), sc);
         if (!__all_sync(kFull, w)) return false;
     }
@@ -166,7 +214,7 @@ __device__ __forceinline__ bool run_strip_staged(const PairRef<float>& pr, int r
             __syncwarp();
             const int c = (s >> 5) + 1;
             if (32 * c + 1 <= m) {
-                if (!first && io.up_flag != nullptr) {
+                if (up_global && io.up_flag != nullptr) {
                     const bool w = wait_progress(io.up_flag, (unsigned)min(32 * c + 32, m), sc);
                     if (__any_sync(kFull, !w)) {
                         cp_async_wait_all();
@@ -176,8 +224,29 @@ __device__ __forceinline__ bool run_strip_staged(const PairRef<float>& pr, int r
                 issue(c);
             }
         }
+        if ((s & 7) == 0 && (io.up_local || io.down_local != nullptr)) {
+            // block-local hand-off, 8 columns at a time: the row above must be
+            // written for lane 0's next 8 columns, and the warp below must have
+            // consumed what lane 31's next 8 writes overwrite (ring of 128)
+            bool w = true;
+            if (io.up_local) {
+                if (lane == 0) {
+                    __threadfence_block();
+                    *io.my_cons = s;  // columns 1..s of the ring are consumed
+                }
+                if (s < m) w = wait_local(io.up_prog, min(s + 8, m), sc);
+            }
+            if (w && io.down_local != nullptr && s - 151 >= 1)
+                w = wait_local(io.down_cons, s - 151, sc);
+            if (__any_sync(kFull, !w)) {
+                cp_async_wait_all();
+                return false;
+            }
+        }
         float upD = __shfl_up_sync(kFull, botD, 1);
         float upC = __shfl_up_sync(kFull, botC, 1);
+        float upL = 0.f;
+        if constexpr (KH) upL = __shfl_up_sync(kFull, botL, 1);
         if (j >= 1 && j <= m) {
             const int slot = (j - 1) & (kRingCols - 1);
             const float4* rp = reinterpret_cast<const float4*>(ring + slot * LEN);
@@ -190,14 +259,45 @@ __device__ __forceinline__ bool run_strip_staged(const PairRef<float>& pr, int r
                 rec[4 * q + 2] = v.z;
                 rec[4 * q + 3] = v.w;
             }
-            const float2 bnd = bring[slot];
-            if (lane == 0) {
-                upD = first ? INF : bnd.x;  // D(r0-1, j)
-                upC = first ? 0.f : bnd.y;  // c(r0-1, j)
+            if constexpr (KH) {
+                const float4 bnd = bring4[slot];
+                if (lane == 0) {
+                    upD = first ? INF : bnd.x;  // D(r0-1, j), hi and lo
+                    upL = first ? 0.f : bnd.y;
+                    upC = first ? 0.f : bnd.z;  // c(r0-1, j)
+                }
+            } else {
+                const float2 bnd = bring2[slot];
+                if (lane == 0) {
+                    upD = first ? INF : bnd.x;  // D(r0-1, j)
+                    upC = first ? 0.f : bnd.y;  // c(r0-1, j)
+                }
             }
             const float tb = rec[RL::kT];
             const float delb = rec[RL::kDel];
             float d_up = upD, d_dg = diagD, c_dg = diagC;
+            float l_up = upL, l_dg = diagL;
+            // one DP cell: plain or compensated
+            auto update = [&](int r, float c) {
+                const float oD = Dl[r], oC = cp[r];
+                if constexpr (KH) {
+                    const float oL = Dlo[r];
+                    float h, l;
+                    kahan_cell(d_up, l_up, oD, oL, d_dg, l_dg, rdel[r], delb, c, c_dg, h, l);
+                    Dl[r] = h;
+                    Dlo[r] = l;
+                    d_up = h;
+                    l_up = l;
+                    l_dg = oL;
+                } else {
+                    const float v = min3f(d_up + rdel[r], oD + delb, (d_dg + c) + c_dg);
+                    Dl[r] = v;
+                    d_up = v;
+                }
+                cp[r] = c;
+                d_dg = oD;
+                c_dg = oC;
+            };
             if constexpr (PACK) {
                 unsigned long long B2[DIM];
 #pragma unroll
@@ -216,16 +316,8 @@ __device__ __forceinline__ bool run_strip_staged(const PairRef<float>& pr, int r
                     const int r = 2 * q;
                     const float c0 = fmaf(pr.nu, fabsf(rt[r] - tb), Arith<float>::root(s0));
                     const float c1 = fmaf(pr.nu, fabsf(rt[r + 1] - tb), Arith<float>::root(s1));
-                    const float oD0 = Dl[r], oC0 = cp[r], oD1 = Dl[r + 1], oC1 = cp[r + 1];
-                    const float v0 = min3f(d_up + rdel[r], oD0 + delb, (d_dg + c0) + c_dg);
-                    const float v1 = min3f(v0 + rdel[r + 1], oD1 + delb, (oD0 + c1) + oC0);
-                    Dl[r] = v0;
-                    cp[r] = c0;
-                    Dl[r + 1] = v1;
-                    cp[r + 1] = c1;
-                    d_up = v1;
-                    d_dg = oD1;
-                    c_dg = oC1;
+                    update(r, c0);
+                    update(r + 1, c1);
                 }
             } else {
                 float bv[DIM];
@@ -234,32 +326,40 @@ __device__ __forceinline__ bool run_strip_staged(const PairRef<float>& pr, int r
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     const float dd = dist<float, DIM, P>(ra[r], bv, DIM, pr.p);
-                    const float c = fmaf(pr.nu, fabsf(rt[r] - tb), dd);
-                    const float oD = Dl[r], oC = cp[r];
-                    const float v = min3f(d_up + rdel[r], oD + delb, (d_dg + c) + c_dg);
-                    Dl[r] = v;
-                    cp[r] = c;
-                    d_up = v;
-                    d_dg = oD;
-                    c_dg = oC;
+                    update(r, fmaf(pr.nu, fabsf(rt[r] - tb), dd));
                 }
             }
             diagD = upD;
             diagC = upC;
             botD = Dl[R - 1];
             botC = cp[R - 1];
+            if constexpr (KH) {
+                diagL = upL;
+                botL = Dlo[R - 1];
+            }
             if (io.down != nullptr && lane == 31) {
-                __stcg(io.down + (j - 1), make_float2(botD, botC));
+                if constexpr (KH) __stcg(down4 + (j - 1), make_float4(botD, botL, botC, 0.f));
+                else __stcg(io.down + (j - 1), make_float2(botD, botC));
                 if (io.down_flag != nullptr && io.publish && (((j & 31) == 0) || j == m))
                     st_release(io.down_flag, (unsigned)j);
+            }
+            if (io.down_local != nullptr && lane == 31) {
+                const int slot_d = (j - 1) & (kRingCols - 1);
+                if constexpr (KH) dloc4[slot_d] = make_float4(botD, botL, botC, 0.f);
+                else dloc2[slot_d] = make_float2(botD, botC);
+                if (io.publish && (((j & 7) == 0) || j == m)) {
+                    __threadfence_block();
+                    *io.down_prog = j;
+                }
             }
             if (j == m) {
                 const int rr = pr.n - r0 - lane * R;
 #pragma unroll
                 for (int r = 0; r < R; ++r) {
                     if (r == rr) {
-                        if (result_a) *result_a = Dl[r];
-                        if (result_b) *result_b = Dl[r];
+                        const float v = KH ? Dl[r] + Dlo[r] : Dl[r];
+                        if (result_a) *result_a = v;
+                        if (result_b) *result_b = v;
                     }
                 }
             }

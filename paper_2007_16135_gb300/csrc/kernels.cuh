@@ -12,20 +12,21 @@ namespace twed {
 template <typename T, int DIM>
 constexpr bool kStaged = (sizeof(T) == 4 && DIM > 0);
 
-template <typename T, int DIM>
+// KH = compensated running cost (staged FP32 only; other paths ignore it).
+template <typename T, int DIM, bool KH = false>
 __host__ __device__ constexpr int smem_per_warp() {
-    if constexpr (kStaged<T, DIM>) return staged_bytes_per_warp<DIM>();
+    if constexpr (kStaged<T, DIM>) return staged_bytes_per_warp<DIM, KH>();
     else return 0;
 }
 
-template <typename T, int DIM, int P, int R>
+template <typename T, int DIM, int P, int R, bool KH = false>
 __device__ __forceinline__ bool strip_call(const PairRef<T>& pr, int r0, int rows,
                                            const StripIO<T>& io, const SyncCtl& sc, T* o1, T* o2,
                                            unsigned char* wsmem) {
     if constexpr (kStaged<T, DIM>) {
         float* ring = reinterpret_cast<float*>(wsmem);
-        float2* bring = reinterpret_cast<float2*>(wsmem + kRingCols * Rec<float, DIM>::kLen * 4);
-        return run_strip_staged<DIM, P, R>(pr, r0, rows, io, sc, o1, o2, ring, bring);
+        void* bring = wsmem + kRingCols * Rec<float, DIM>::kLen * 4;
+        return run_strip_staged<DIM, P, R, KH>(pr, r0, rows, io, sc, o1, o2, ring, bring);
     } else {
         (void)wsmem;
         return run_strip<T, DIM, P, R>(pr, r0, rows, io, sc, o1, o2);
@@ -103,11 +104,13 @@ __global__ void __launch_bounds__(256) records_kernel(RecordsArgs<T> a) {
 // not started, whatever the residency.  A strip publishes its bottom row
 // every 32 columns into a ring slot (release store of the column count) and
 // its successor polls that count (acquire, bounded by %globaltimer).
-template <typename T, int DIM, int P, int R>
+template <typename T, int DIM, int P, int R, bool KH>
 __global__ void __launch_bounds__(128) coop_kernel(CoopArgs<T> a) {
     using V2 = typename Pair2<T>::V;
+    // ring entries: (D, c) pairs, or (D_hi, D_lo, c, 0) quads when KH
+    using Entry = typename std::conditional<KH && kStaged<T, DIM>, float4, V2>::type;
     extern __shared__ __align__(16) unsigned char dyn_smem[];
-    unsigned char* wsmem = dyn_smem + (threadIdx.x >> 5) * smem_per_warp<T, DIM>();
+    unsigned char* wsmem = dyn_smem + (threadIdx.x >> 5) * smem_per_warp<T, DIM, KH>();
     const int lane = threadIdx.x & 31;
     PairRef<T> pr;
     pr.rec_a = a.rec_a;
@@ -121,7 +124,7 @@ __global__ void __launch_bounds__(128) coop_kernel(CoopArgs<T> a) {
     pr.dim = a.dim;
     pr.p = a.p;
     pr.nu = a.nu;
-    V2* ring = reinterpret_cast<V2*>(a.ring);
+    Entry* ring = reinterpret_cast<Entry*>(a.ring);
     while (true) {
         unsigned k = 0;
         if (lane == 0) k = atomicAdd(a.strip_counter, 1u);
@@ -130,14 +133,94 @@ __global__ void __launch_bounds__(128) coop_kernel(CoopArgs<T> a) {
         if (*(volatile unsigned*)a.sc.err != 0u) break;
         const int r0 = (int)k * 32 * R + 1;
         const int rows = min(32 * R, a.n - r0 + 1);
-        StripIO<T> io;
-        io.up = k == 0 ? nullptr : ring + (int64_t)((k - 1) % a.nslot) * a.ring_stride;
-        io.up_flag = k == 0 ? nullptr : a.flags + (k - 1);
         const bool last = (int64_t)k == a.nstrips - 1;
-        io.down = last ? nullptr : ring + (int64_t)(k % a.nslot) * a.ring_stride;
-        io.down_flag = last ? nullptr : a.flags + k;
-        io.publish = (long long)k != a.sc.stall_strip;
-        if (!strip_call<T, DIM, P, R>(pr, r0, rows, io, a.sc, a.out, nullptr, wsmem)) break;
+        StripIO<T> io = strip_io_global<T>(
+            k == 0 ? nullptr
+                   : reinterpret_cast<const V2*>(ring + (int64_t)((k - 1) % a.nslot) * a.ring_stride),
+            k == 0 ? nullptr : a.flags + (k - 1),
+            last ? nullptr : reinterpret_cast<V2*>(ring + (int64_t)(k % a.nslot) * a.ring_stride),
+            last ? nullptr : a.flags + k, (long long)k != a.sc.stall_strip);
+        if (!strip_call<T, DIM, P, R, KH>(pr, r0, rows, io, a.sc, a.out, nullptr, wsmem)) break;
+    }
+}
+
+// ------------------------------------------------ one long pair, by bands
+// Block-cooperative variant for FP32 with a compiled point layout.  A block
+// of W warps claims a band of W consecutive strips (bands in increasing order
+// from an atomic counter, so every band waits only on a band that is already
+// running).  Inside the band, warp w writes its bottom row straight into the
+// shared-memory boundary ring of warp w+1 and publishes progress every 8
+// columns with a block-scope fence; only the band's first warp reads, and its
+// last warp writes, a global boundary row with gpu-scope release/acquire
+// flags.  This cuts the fences on the path to one gpu-scope hand-off per W
+// strips and the lag between consecutive strips to about 40 columns.
+template <int DIM, int P, int R, bool KH>
+__global__ void __launch_bounds__(256) band_kernel(CoopArgs<float> a) {
+    using Entry = typename std::conditional<KH, float4, float2>::type;
+    constexpr int SPW = smem_per_warp<float, DIM, KH>();
+    constexpr int kRecBytes = kRingCols * Rec<float, DIM>::kLen * 4;
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    __shared__ int prog[32], cons[32];
+    __shared__ long long band_sh;
+    const int W = blockDim.x >> 5;
+    const int w = threadIdx.x >> 5;
+    unsigned char* wsmem = dyn_smem + w * SPW;
+    const long long nbands = (a.nstrips + W - 1) / W;
+    Entry* ring = reinterpret_cast<Entry*>(a.ring);
+    PairRef<float> pr;
+    pr.rec_a = a.rec_a;
+    pr.rec_b = a.rec_b;
+    pr.vals_a = a.vals_a;
+    pr.vals_b = a.vals_b;
+    pr.a_first = 0;
+    pr.b_first = 0;
+    pr.n = a.n;
+    pr.m = a.m;
+    pr.dim = a.dim;
+    pr.p = a.p;
+    pr.nu = a.nu;
+    while (true) {
+        __syncthreads();  // every warp is done with the previous band
+        if (threadIdx.x == 0) {
+            const bool failed = *(volatile unsigned*)a.sc.err != 0u;
+            band_sh = failed ? nbands : (long long)atomicAdd(a.strip_counter, 1u);
+        }
+        if (threadIdx.x < 32) {
+            prog[threadIdx.x] = 0;
+            cons[threadIdx.x] = 0;
+        }
+        __syncthreads();
+        const long long b = band_sh;
+        if (b >= nbands) break;
+        const long long k = b * W + w;  // this warp's strip
+        if (k < a.nstrips) {
+            const int r0 = (int)k * 32 * R + 1;
+            const int rows = min(32 * R, a.n - r0 + 1);
+            const bool last_strip = (k == a.nstrips - 1);
+            const bool publish = (long long)k != a.sc.stall_strip;
+            StripIO<float> io = strip_io_global<float>(nullptr, nullptr, nullptr, nullptr, publish);
+            if (w == 0) {
+                if (b > 0) {
+                    io.up = reinterpret_cast<const float2*>(ring + ((b - 1) % a.nslot) * a.ring_stride);
+                    io.up_flag = a.flags + (b - 1);
+                }
+            } else {
+                io.up_local = true;
+                io.up_prog = &prog[w];
+                io.my_cons = &cons[w];
+            }
+            if (!last_strip) {
+                if (w == W - 1) {
+                    io.down = reinterpret_cast<float2*>(ring + (b % a.nslot) * a.ring_stride);
+                    io.down_flag = a.flags + b;
+                } else {
+                    io.down_local = dyn_smem + (w + 1) * SPW + kRecBytes;
+                    io.down_prog = &prog[w + 1];
+                    io.down_cons = &cons[w + 1];
+                }
+            }
+            strip_call<float, DIM, P, R, KH>(pr, r0, rows, io, a.sc, a.out, nullptr, wsmem);
+        }
     }
 }
 
@@ -213,12 +296,8 @@ __global__ void __launch_bounds__(128) pairs_kernel(PairsArgs<T> a) {
             if (kEven) R = min((R + 1) & ~1, rmax);
             const int rows = min(left, 32 * R);
             const bool last = r0 + rows > pr.n;
-            StripIO<T> io;
-            io.up = r0 == 1 ? nullptr : row;
-            io.up_flag = nullptr;
-            io.down = last ? nullptr : row;
-            io.down_flag = nullptr;
-            io.publish = true;
+            StripIO<T> io = strip_io_global<T>(r0 == 1 ? nullptr : row, nullptr,
+                                               last ? nullptr : row, nullptr, true);
             switch (R) {
                 case 1: if constexpr (!kEven) strip_call<T, DIM, P, 1>(pr, r0, rows, io, a.sc, o1, o2, wsmem); break;
                 case 2: if constexpr (RMAX >= 2) strip_call<T, DIM, P, 2>(pr, r0, rows, io, a.sc, o1, o2, wsmem); break;
@@ -280,18 +359,25 @@ cudaError_t launch_records_t(const RecordsArgs<T>& a, cudaStream_t st) {
 
 // Launch (or size) a kernel with `threads` threads and its per-warp dynamic
 // shared memory; the opt-in above 48 KB is set on every call (cheap).
+// Dynamic plus static shared memory above 48 KB needs the opt-in; kernels
+// here also carry a little static shared memory, so opt in whenever the
+// dynamic part is not small.
 template <typename K>
 cudaError_t prepare_smem(K kernel, int smem) {
-    if (smem <= 48 * 1024) return cudaSuccess;
+    if (smem <= 32 * 1024) return cudaSuccess;
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
 }
 
+// Launch errors are read with cudaGetLastError, which also returns any
+// earlier unchecked failure: clear that state first so the status belongs
+// to this launch.
 template <typename K, typename A>
 cudaError_t launch_with_smem(K kernel, int smem_warp, int blocks, int threads, cudaStream_t st,
                              const A& a) {
     const int smem = smem_warp * (threads / 32);
     cudaError_t e = prepare_smem(kernel, smem);
     if (e != cudaSuccess) return e;
+    (void)cudaGetLastError();
     kernel<<<blocks, threads, smem, st>>>(a);
     return cudaGetLastError();
 }
@@ -299,9 +385,12 @@ cudaError_t launch_with_smem(K kernel, int smem_warp, int blocks, int threads, c
 template <typename K>
 int blocks_per_sm(K kernel, int smem_warp, int threads) {
     const int smem = smem_warp * (threads / 32);
-    if (prepare_smem(kernel, smem) != cudaSuccess) return 0;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, smem) != cudaSuccess) return 0;
+    if (prepare_smem(kernel, smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, threads, smem) != cudaSuccess) {
+        (void)cudaGetLastError();  // a failed query must not surface at the next launch
+        return 0;
+    }
     return nb;
 }
 
@@ -322,27 +411,68 @@ int pairs_blocks_per_sm_t(int dim, int p, int threads) {
     return nb;
 }
 
-template <typename T>
-cudaError_t launch_coop_t(const CoopArgs<T>& a, int R, int blocks, int threads, cudaStream_t st) {
+template <bool KH>
+cudaError_t launch_band_kh(const CoopArgs<float>& a, int R, int blocks, int warps, cudaStream_t st) {
+    cudaError_t e = cudaErrorNotSupported;
+    const int threads = 32 * warps;
+#define TWED_BAND_R(RR)                                                                           \
+    TWED_DISPATCH(a.dim, a.p,                                                                     \
+                  (e = (DIM_ > 0 ? launch_with_smem(band_kernel<(DIM_ > 0 ? DIM_ : 1), P_, RR, KH>, \
+                                                    smem_per_warp<float, (DIM_ > 0 ? DIM_ : 1), KH>(), \
+                                                    blocks, threads, st, a)                         \
+                                 : cudaErrorNotSupported)))
+    switch (R) {
+        case 1: TWED_BAND_R(1); break;
+        case 2: TWED_BAND_R(2); break;
+        case 4: TWED_BAND_R(4); break;
+        case 8: TWED_BAND_R(8); break;
+        default: return cudaErrorInvalidValue;
+    }
+#undef TWED_BAND_R
+    return e;
+}
+
+template <bool KH>
+int band_blocks_per_sm_kh(int dim, int p, int R, int warps) {
+    int nb = 0;
+    const int threads = 32 * warps;
+#define TWED_BAND_OCC(RR)                                                                         \
+    TWED_DISPATCH(dim, p, (nb = (DIM_ > 0 ? blocks_per_sm(band_kernel<(DIM_ > 0 ? DIM_ : 1), P_, RR, KH>, \
+                                                          smem_per_warp<float, (DIM_ > 0 ? DIM_ : 1), KH>(), \
+                                                          threads)                              \
+                                          : 0)))
+    switch (R) {
+        case 1: TWED_BAND_OCC(1); break;
+        case 2: TWED_BAND_OCC(2); break;
+        case 4: TWED_BAND_OCC(4); break;
+        case 8: TWED_BAND_OCC(8); break;
+        default: break;
+    }
+#undef TWED_BAND_OCC
+    return nb;
+}
+
+template <typename T, bool KH>
+cudaError_t launch_coop_kh(const CoopArgs<T>& a, int R, int blocks, int threads, cudaStream_t st) {
     cudaError_t e = cudaSuccess;
     switch (R) {
-        case 1: TWED_DISPATCH(a.dim, a.p, (e = launch_with_smem(coop_kernel<T, DIM_, P_, 1>, smem_per_warp<T, DIM_>(), blocks, threads, st, a))); break;
-        case 2: TWED_DISPATCH(a.dim, a.p, (e = launch_with_smem(coop_kernel<T, DIM_, P_, 2>, smem_per_warp<T, DIM_>(), blocks, threads, st, a))); break;
-        case 4: TWED_DISPATCH(a.dim, a.p, (e = launch_with_smem(coop_kernel<T, DIM_, P_, 4>, smem_per_warp<T, DIM_>(), blocks, threads, st, a))); break;
-        case 8: TWED_DISPATCH(a.dim, a.p, (e = launch_with_smem(coop_kernel<T, DIM_, P_, 8>, smem_per_warp<T, DIM_>(), blocks, threads, st, a))); break;
+        case 1: TWED_DISPATCH(a.dim, a.p, (e = launch_with_smem(coop_kernel<T, DIM_, P_, 1, KH>, smem_per_warp<T, DIM_, KH>(), blocks, threads, st, a))); break;
+        case 2: TWED_DISPATCH(a.dim, a.p, (e = launch_with_smem(coop_kernel<T, DIM_, P_, 2, KH>, smem_per_warp<T, DIM_, KH>(), blocks, threads, st, a))); break;
+        case 4: TWED_DISPATCH(a.dim, a.p, (e = launch_with_smem(coop_kernel<T, DIM_, P_, 4, KH>, smem_per_warp<T, DIM_, KH>(), blocks, threads, st, a))); break;
+        case 8: TWED_DISPATCH(a.dim, a.p, (e = launch_with_smem(coop_kernel<T, DIM_, P_, 8, KH>, smem_per_warp<T, DIM_, KH>(), blocks, threads, st, a))); break;
         default: return cudaErrorInvalidValue;
     }
     return e;
 }
 
-template <typename T>
-int coop_blocks_per_sm_t(int dim, int p, int R, int threads) {
+template <typename T, bool KH>
+int coop_blocks_per_sm_kh(int dim, int p, int R, int threads) {
     int nb = 0;
     switch (R) {
-        case 1: TWED_DISPATCH(dim, p, (nb = blocks_per_sm(coop_kernel<T, DIM_, P_, 1>, smem_per_warp<T, DIM_>(), threads))); break;
-        case 2: TWED_DISPATCH(dim, p, (nb = blocks_per_sm(coop_kernel<T, DIM_, P_, 2>, smem_per_warp<T, DIM_>(), threads))); break;
-        case 4: TWED_DISPATCH(dim, p, (nb = blocks_per_sm(coop_kernel<T, DIM_, P_, 4>, smem_per_warp<T, DIM_>(), threads))); break;
-        case 8: TWED_DISPATCH(dim, p, (nb = blocks_per_sm(coop_kernel<T, DIM_, P_, 8>, smem_per_warp<T, DIM_>(), threads))); break;
+        case 1: TWED_DISPATCH(dim, p, (nb = blocks_per_sm(coop_kernel<T, DIM_, P_, 1, KH>, smem_per_warp<T, DIM_, KH>(), threads))); break;
+        case 2: TWED_DISPATCH(dim, p, (nb = blocks_per_sm(coop_kernel<T, DIM_, P_, 2, KH>, smem_per_warp<T, DIM_, KH>(), threads))); break;
+        case 4: TWED_DISPATCH(dim, p, (nb = blocks_per_sm(coop_kernel<T, DIM_, P_, 4, KH>, smem_per_warp<T, DIM_, KH>(), threads))); break;
+        case 8: TWED_DISPATCH(dim, p, (nb = blocks_per_sm(coop_kernel<T, DIM_, P_, 8, KH>, smem_per_warp<T, DIM_, KH>(), threads))); break;
         default: break;
     }
     return nb;

@@ -14,12 +14,15 @@ int rec_len<float>(int dim, int p) {
 cudaError_t launch_records(const RecordsArgs<float>& a, cudaStream_t st) {
     return launch_records_t(a, st);
 }
-cudaError_t launch_coop(const CoopArgs<float>& a, int R, int blocks, int threads, cudaStream_t st) {
-    return launch_coop_t(a, R, blocks, threads, st);
+cudaError_t launch_coop(const CoopArgs<float>& a, int R, bool kahan, int blocks, int threads,
+                        cudaStream_t st) {
+    return kahan ? launch_coop_kh<float, true>(a, R, blocks, threads, st)
+                 : launch_coop_kh<float, false>(a, R, blocks, threads, st);
 }
 template <>
-int coop_blocks_per_sm<float>(int dim, int p, int R, int threads) {
-    return coop_blocks_per_sm_t<float>(dim, p, R, threads);
+int coop_blocks_per_sm<float>(int dim, int p, int R, bool kahan, int threads) {
+    return kahan ? coop_blocks_per_sm_kh<float, true>(dim, p, R, threads)
+                 : coop_blocks_per_sm_kh<float, false>(dim, p, R, threads);
 }
 cudaError_t launch_pairs(const PairsArgs<float>& a, int blocks, int threads, cudaStream_t st) {
     return launch_pairs_t<float, kRmaxF32>(a, blocks, threads, st);
@@ -30,6 +33,20 @@ int pairs_blocks_per_sm<float>(int dim, int p, int threads) {
 }
 template <>
 int pairs_rmax_limit<float>() { return kRmaxF32; }
+cudaError_t launch_band(const CoopArgs<float>& a, int R, bool kahan, int blocks, int warps,
+                        cudaStream_t st) {
+    return kahan ? launch_band_kh<true>(a, R, blocks, warps, st)
+                 : launch_band_kh<false>(a, R, blocks, warps, st);
+}
+int band_blocks_per_sm(int dim, int p, int R, bool kahan, int warps) {
+    return kahan ? band_blocks_per_sm_kh<true>(dim, p, R, warps)
+                 : band_blocks_per_sm_kh<false>(dim, p, R, warps);
+}
+bool compiled_layout(int dim, int p) {
+    int d = 0;
+    TWED_DISPATCH(dim, p, (d = DIM_));
+    return d > 0;
+}
 
 }  // namespace twed
 

@@ -14,12 +14,15 @@ int rec_len<double>(int dim, int p) {
 cudaError_t launch_records(const RecordsArgs<double>& a, cudaStream_t st) {
     return launch_records_t(a, st);
 }
-cudaError_t launch_coop(const CoopArgs<double>& a, int R, int blocks, int threads, cudaStream_t st) {
-    return launch_coop_t(a, R, blocks, threads, st);
+cudaError_t launch_coop(const CoopArgs<double>& a, int R, bool kahan, int blocks, int threads,
+                        cudaStream_t st) {
+    if (kahan) return cudaErrorNotSupported;  // compensation is an FP32 option
+    return launch_coop_kh<double, false>(a, R, blocks, threads, st);
 }
 template <>
-int coop_blocks_per_sm<double>(int dim, int p, int R, int threads) {
-    return coop_blocks_per_sm_t<double>(dim, p, R, threads);
+int coop_blocks_per_sm<double>(int dim, int p, int R, bool kahan, int threads) {
+    (void)kahan;
+    return coop_blocks_per_sm_kh<double, false>(dim, p, R, threads);
 }
 cudaError_t launch_pairs(const PairsArgs<double>& a, int blocks, int threads, cudaStream_t st) {
     return launch_pairs_t<double, kRmaxF64>(a, blocks, threads, st);

@@ -81,11 +81,23 @@ int rec_len(int dim, int p);
 cudaError_t launch_records(const RecordsArgs<float>& a, cudaStream_t st);
 cudaError_t launch_records(const RecordsArgs<double>& a, cudaStream_t st);
 
-// R (rows of the DP per lane) in {1, 2, 4, 8}.
-cudaError_t launch_coop(const CoopArgs<float>& a, int R, int blocks, int threads, cudaStream_t st);
-cudaError_t launch_coop(const CoopArgs<double>& a, int R, int blocks, int threads, cudaStream_t st);
+// R (rows of the DP per lane) in {1, 2, 4, 8}.  kahan: compensated FP32
+// running cost (float, dims with a compiled point layout only; ring entries
+// are then (D_hi, D_lo, c, 0) float4).
+cudaError_t launch_coop(const CoopArgs<float>& a, int R, bool kahan, int blocks, int threads,
+                        cudaStream_t st);
+cudaError_t launch_coop(const CoopArgs<double>& a, int R, bool kahan, int blocks, int threads,
+                        cudaStream_t st);
 template <typename T>
-int coop_blocks_per_sm(int dim, int p, int R, int threads);
+int coop_blocks_per_sm(int dim, int p, int R, bool kahan, int threads);
+// One long FP32 pair by bands of `warps` strips per block (compiled point
+// layouts only; strip_counter counts bands, flags[b] is band b's progress).
+cudaError_t launch_band(const CoopArgs<float>& a, int R, bool kahan, int blocks, int warps,
+                        cudaStream_t st);
+int band_blocks_per_sm(int dim, int p, int R, bool kahan, int warps);
+// true when (dim, p) has a compiled point layout (dims 1, 2, 3, 4, 8 with
+// p = 1, 2): the compensated variant needs one.
+bool compiled_layout(int dim, int p);
 
 // a.rmax (largest rows per lane) is clamped to pairs_rmax_limit<T>().
 cudaError_t launch_pairs(const PairsArgs<float>& a, int blocks, int threads, cudaStream_t st);

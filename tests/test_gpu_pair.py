@@ -167,3 +167,26 @@ def test_invalid_arguments_rejected(tw, bad):
     with pytest.raises(tw.TwedError) as ei:
         tw.twed_f64(**args)
     assert ei.value.status == tw.TWED_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("n,m", [(1, 1), (33, 65), (257, 300), (1000, 17), (2100, 700)])
+@pytest.mark.parametrize("dim,p", [(1, 2), (3, 2), (4, 1), (8, 2), (2, 2)])
+def test_pair_f32_compensated(tw, n, m, dim, p):
+    # compensated (TwoSum) FP32 running cost against the FP64 oracle on the
+    # same FP32-rounded inputs
+    rng = np.random.default_rng(17 + n * 1000 + m * 10 + dim + 100 * p)
+    a, ta = series(rng, n, dim, np.float32)
+    b, tb = series(rng, m, dim, np.float32)
+    got = tw.twed_f32(a, ta, b, tb, 0.25, 1.0, p, opts=tw.make_opts(accum=tw.ACCUM_KAHAN))
+    want = oracle.twed(a.astype(np.float64), ta.astype(np.float64), b.astype(np.float64),
+                       tb.astype(np.float64), 0.25, 1.0, p)
+    assert rel_err(got, want) <= 1e-5, (got, want)
+
+
+def test_compensated_unsupported_layout_is_reported(tw):
+    # dim 5 has no compiled point layout: an explicit request is refused
+    rng = np.random.default_rng(1)
+    a, ta = series(rng, 50, 5, np.float32)
+    with pytest.raises(tw.TwedError) as ei:
+        tw.twed_f32(a, ta, a, ta, 1.0, 1.0, 2, opts=tw.make_opts(accum=tw.ACCUM_KAHAN))
+    assert ei.value.status == tw.TWED_ERR_UNSUPPORTED
