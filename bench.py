@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--nseries", type=int, default=4096, help="w3 set size (profiling runs)")
     ap.add_argument("--accum", choices=["auto", "f32", "kahan"], default="auto",
                     help="w2 FP32 running-cost accumulation")
+    ap.add_argument("--rows-per-lane", type=int, default=0, help="w1/w2 schedule override")
+    ap.add_argument("--timeout", type=float, default=0.0, help="bound on inter-warp waits (s)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -294,7 +296,7 @@ def bench_pair(args, rank, world, dev, workload):
     out = torch.empty(1, dtype=td, device=dev)
     stream = torch.cuda.current_stream()
     accum = {"auto": twed.ACCUM_AUTO, "f32": twed.ACCUM_F32, "kahan": twed.ACCUM_KAHAN}[args.accum]
-    opts = twed.make_opts(accum=accum)
+    opts = twed.make_opts(accum=accum, rows_per_lane=args.rows_per_lane, timeout_s=args.timeout)
     kahan = dtype == "f32" and (args.accum == "kahan" or (args.accum == "auto" and 2 * n > 100000))
     for _ in range(args.warmup):
         twed.twed_dev(A, TA, B, TB, nu, lam, p, out=out, stream=stream, opts=opts)

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <numeric>
 #include <string>
@@ -41,6 +42,8 @@ struct Carver {
 struct twed_handle_s {
     int device = 0;
     int sms = 0;
+    unsigned sleep_ns = 32;  // poll back-off (env TWED_WAIT_SLEEP_NS)
+    int band_warps = 8;      // strips per band (env TWED_BAND_WARPS: 2, 4 or 8)
     cudaStream_t stream = nullptr;
     void* ws = nullptr;  // grow-only device workspace
     size_t ws_bytes = 0;
@@ -134,6 +137,7 @@ twed::SyncCtl make_sync(twed_handle_t h, const twed_opts_t* o) {
     sc.sticky = h->ctl + 1;
     sc.timeout_ns = timeout_ns(o);
     sc.stall_strip = o ? o->stall_strip : -1;
+    sc.sleep_ns = h->sleep_ns;
     return sc;
 }
 
@@ -155,11 +159,10 @@ int coop_rows_per_lane(twed_handle_t h, int64_t n, const twed_opts_t* o) {
 }
 
 // Band schedule (FP32, compiled point layouts): strips of 32*R rows, bands of
-// kBandWarps strips per block.  R is picked with a small cost model: a step
+// h->band_warps strips per block.  R is picked with a small cost model: a step
 // costs the larger of one warp's dependency chain and the SM's issue slots
 // shared by its active warps; consecutive strips start ~40 steps apart; bands
 // beyond the resident blocks run in further rounds.
-constexpr int kBandWarps = 8;
 
 int band_rows_per_lane(twed_handle_t h, int64_t n, int64_t m, int dim, int p, bool kahan,
                        const twed_opts_t* o) {
@@ -173,16 +176,16 @@ int band_rows_per_lane(twed_handle_t h, int64_t n, int64_t m, int dim, int p, bo
     int best = 1;
     double best_t = 1e300;
     for (int R : {8, 4, 2, 1}) {
-        const int per_sm = twed::band_blocks_per_sm(dim, p, R, kahan, kBandWarps);
+        const int per_sm = twed::band_blocks_per_sm(dim, p, R, kahan, h->band_warps);
         if (per_sm < 1) continue;
         const double nstrips = std::ceil((double)n / (32.0 * R));
-        const double nbands = std::ceil(nstrips / kBandWarps);
+        const double nbands = std::ceil(nstrips / h->band_warps);
         const double conc = (double)per_sm * h->sms;
         const double rounds = std::ceil(nbands / conc);
         const double active = std::min(nbands, conc);
-        const double warps_sm = active * kBandWarps / h->sms;
+        const double warps_sm = active * h->band_warps / h->sms;
         const double t_step = std::max(60.0 + lat_row * R, (c_row * R + c_step) * warps_sm / 4.0);
-        const double t = rounds * ((double)m + active * kBandWarps * 40.0) * t_step;
+        const double t = rounds * ((double)m + active * h->band_warps * 40.0) * t_step;
         if (t < best_t) {
             best_t = t;
             best = R;
@@ -292,10 +295,11 @@ twed_status_t run_pair_dev(twed_handle_t h, const T* a, const T* ta, int64_t la,
     ca.sc = make_sync(h, o);
     if constexpr (sizeof(T) == 4) {
         if (L.band) {
-            const int per_sm = std::max(1, twed::band_blocks_per_sm(dim, p, R, L.kahan, kBandWarps));
-            const int64_t nbands = (nstrips + kBandWarps - 1) / kBandWarps;
+            const int bw = h->band_warps;
+            const int per_sm = std::max(1, twed::band_blocks_per_sm(dim, p, R, L.kahan, bw));
+            const int64_t nbands = (nstrips + bw - 1) / bw;
             const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(nbands, (int64_t)per_sm * h->sms));
-            const cudaError_t e = twed::launch_band(ca, R, L.kahan, (int)blocks, kBandWarps, st);
+            const cudaError_t e = twed::launch_band(ca, R, L.kahan, (int)blocks, bw, st);
             if (e != cudaSuccess)
                 return fail(h, TWED_ERR_CUDA, "band launch (dim %d, p %d, R %d, kahan %d, blocks %lld, per_sm %d): %s",
                             dim, p, R, (int)L.kahan, (long long)blocks, per_sm, cudaGetErrorString(e));
@@ -378,6 +382,11 @@ extern "C" twed_status_t twed_create(twed_handle_t* out) {
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaMalloc(&h->ctl, 64);
     if (e == cudaSuccess) e = cudaMemset(h->ctl, 0, 64);
+    if (const char* v = getenv("TWED_WAIT_SLEEP_NS")) h->sleep_ns = (unsigned)atoi(v);
+    if (const char* v = getenv("TWED_BAND_WARPS")) {
+        const int w = atoi(v);
+        h->band_warps = (w == 2 || w == 4 || w == 8) ? w : 8;
+    }
     if (e != cudaSuccess) {
         cudaGetLastError();
         if (h->stream) cudaStreamDestroy(h->stream);
@@ -676,6 +685,7 @@ twed_status_t plan_create(twed_handle_t h, const S* A, const S* B, int dim, T nu
     pa.sc.sticky = pl->ctl + 1;
     pa.sc.timeout_ns = timeout_ns(o);
     pa.sc.stall_strip = -1;
+    pa.sc.sleep_ns = h->sleep_ns;
 
     e = cudaStreamCreateWithFlags(&pl->cap, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreate(&pl->ev0);

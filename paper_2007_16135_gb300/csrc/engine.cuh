@@ -243,7 +243,7 @@ __device__ __forceinline__ bool wait_progress(const unsigned* flag, unsigned tar
                 return false;
             }
         }
-        __nanosleep(64);
+        if (sc.sleep_ns) __nanosleep(sc.sleep_ns);
     }
 }
 
@@ -305,7 +305,7 @@ __device__ __forceinline__ bool wait_local(volatile int* word, int target, const
                 return false;
             }
         }
-        __nanosleep(32);
+        if (sc.sleep_ns) __nanosleep(sc.sleep_ns);
     }
     __threadfence_block();
     return true;

@@ -81,27 +81,6 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 // would poison TwoSum): kBig is far above any reachable cost.
 constexpr float kBig = 1.2676506e30f;  // 2^100
 
-__device__ __forceinline__ void kahan_cell(float uh, float ul, float lh, float ll, float dh,
-                                           float dl, float del_a, float del_b, float c,
-                                           float c_dg, float& oh, float& ol) {
-    float s1, e1, s2, e2, s3, e3, s4, e4;
-    two_sum(uh, del_a, s1, e1);
-    const float l1 = ul + e1;
-    const float v1 = s1 + l1;
-    two_sum(lh, del_b, s2, e2);
-    const float l2 = ll + e2;
-    const float v2 = s2 + l2;
-    two_sum(dh, c, s3, e3);
-    two_sum(s3, c_dg, s4, e4);
-    const float l3 = (dl + e3) + e4;
-    const float v3 = s4 + l3;
-    float h = s1, l = l1, v = v1;
-    if (v2 < v) { h = s2; l = l2; v = v2; }
-    if (v3 < v) { h = s4; l = l3; }
-    oh = h;
-    ol = l;
-}
-
 // One strip (rows r0 .. r0+rows-1, rows <= 32*R) of an FP32 pair with the
 // dimension known at compile time.  `ring` / `bring` are this warp's staging
 // areas (kRingCols records, kRingCols boundary entries).  Boundary rows hold
@@ -275,29 +254,9 @@ __device__ __forceinline__ bool run_strip_staged(const PairRef<float>& pr, int r
             }
             const float tb = rec[RL::kT];
             const float delb = rec[RL::kDel];
-            float d_up = upD, d_dg = diagD, c_dg = diagC;
-            float l_up = upL, l_dg = diagL;
-            // one DP cell: plain or compensated
-            auto update = [&](int r, float c) {
-                const float oD = Dl[r], oC = cp[r];
-                if constexpr (KH) {
-                    const float oL = Dlo[r];
-                    float h, l;
-                    kahan_cell(d_up, l_up, oD, oL, d_dg, l_dg, rdel[r], delb, c, c_dg, h, l);
-                    Dl[r] = h;
-                    Dlo[r] = l;
-                    d_up = h;
-                    l_up = l;
-                    l_dg = oL;
-                } else {
-                    const float v = min3f(d_up + rdel[r], oD + delb, (d_dg + c) + c_dg);
-                    Dl[r] = v;
-                    d_up = v;
-                }
-                cp[r] = c;
-                d_dg = oD;
-                c_dg = oC;
-            };
+            // (1) all R cell costs: independent of each other and of this
+            //     step's D values, so they overlap freely
+            float cc[R];
             if constexpr (PACK) {
                 unsigned long long B2[DIM];
 #pragma unroll
@@ -313,20 +272,71 @@ __device__ __forceinline__ bool run_strip_staged(const PairRef<float>& pr, int r
                     }
                     float s0, s1;
                     f2_unpack(s2, s0, s1);
-                    const int r = 2 * q;
-                    const float c0 = fmaf(pr.nu, fabsf(rt[r] - tb), Arith<float>::root(s0));
-                    const float c1 = fmaf(pr.nu, fabsf(rt[r + 1] - tb), Arith<float>::root(s1));
-                    update(r, c0);
-                    update(r + 1, c1);
+                    cc[2 * q] = fmaf(pr.nu, fabsf(rt[2 * q] - tb), Arith<float>::root(s0));
+                    cc[2 * q + 1] = fmaf(pr.nu, fabsf(rt[2 * q + 1] - tb), Arith<float>::root(s1));
                 }
             } else {
                 float bv[DIM];
 #pragma unroll
                 for (int k = 0; k < DIM; ++k) bv[k] = rec[2 * k];
 #pragma unroll
+                for (int r = 0; r < R; ++r)
+                    cc[r] = fmaf(pr.nu, fabsf(rt[r] - tb), dist<float, DIM, P>(ra[r], bv, DIM, pr.p));
+            }
+            // (2) the parts of each update that do not depend on the row just
+            //     above in this step: deletion in b and the match candidate
+            //     (both read only the previous column)
+            if constexpr (KH) {
+                float h2[R], l2[R], v2[R];
+#pragma unroll
                 for (int r = 0; r < R; ++r) {
-                    const float dd = dist<float, DIM, P>(ra[r], bv, DIM, pr.p);
-                    update(r, fmaf(pr.nu, fabsf(rt[r] - tb), dd));
+                    const float dh = r == 0 ? diagD : Dl[r - 1];
+                    const float dl = r == 0 ? diagL : Dlo[r - 1];
+                    const float cd = r == 0 ? diagC : cp[r - 1];
+                    float sb, eb, s3, e3, s4, e4;
+                    two_sum(Dl[r], delb, sb, eb);
+                    const float lb = Dlo[r] + eb;
+                    const float vb = sb + lb;
+                    two_sum(dh, cc[r], s3, e3);
+                    two_sum(s3, cd, s4, e4);
+                    const float lm = (dl + e3) + e4;
+                    const float vm = s4 + lm;
+                    const bool mb = vm < vb;
+                    h2[r] = mb ? s4 : sb;
+                    l2[r] = mb ? lm : lb;
+                    v2[r] = mb ? vm : vb;
+                }
+                // (3) the chain down the lane's rows: deletion in a
+                float uh = upD, ul = upL;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    float sa, ea;
+                    two_sum(uh, rdel[r], sa, ea);
+                    const float la = ul + ea;
+                    const float va = sa + la;
+                    const bool ma = va < v2[r];
+                    uh = ma ? sa : h2[r];
+                    ul = ma ? la : l2[r];
+                    Dl[r] = uh;
+                    Dlo[r] = ul;
+                    cp[r] = cc[r];
+                }
+            } else {
+                float tb_[R], tm_[R];
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const float dg = r == 0 ? diagD : Dl[r - 1];
+                    const float cd = r == 0 ? diagC : cp[r - 1];
+                    tb_[r] = Dl[r] + delb;         // deletion in b
+                    tm_[r] = (dg + cc[r]) + cd;    // match
+                }
+                // (3) the chain down the lane's rows: deletion in a
+                float d_up = upD;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    d_up = min3f(d_up + rdel[r], tb_[r], tm_[r]);
+                    Dl[r] = d_up;
+                    cp[r] = cc[r];
                 }
             }
             diagD = upD;

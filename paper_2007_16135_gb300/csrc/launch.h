@@ -15,6 +15,7 @@ struct SyncCtl {
     unsigned* sticky;
     unsigned long long timeout_ns;
     long long stall_strip;  // fault injection: strip that never publishes (-1 off)
+    unsigned sleep_ns;      // back-off between polls of a progress word (0 = spin)
 };
 
 // Prologue: one record per point (see Rec<> in engine.cuh).

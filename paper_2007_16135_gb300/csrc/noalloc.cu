@@ -134,6 +134,7 @@ extern "C" twed_status_t twed_batch_f32_noalloc(const twed_set_f32_t* A, const t
     pa.sc.sticky = ctl + 1;
     pa.sc.timeout_ns = 2000000000ull;
     pa.sc.stall_strip = -1;
+    pa.sc.sleep_ns = 32;
     if (twed::launch_pairs(pa, (int)blocks, kThreads, st) != cudaSuccess) return TWED_ERR_CUDA;
     return TWED_OK;
 }
