@@ -41,10 +41,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["w3", "w2", "w1"], default="w3")
+    ap.add_argument("--workload", choices=["w3", "w4", "w2", "w1"], default="w3")
+    ap.add_argument("--xterm", choices=["tf32", "off"], default="tf32",
+                    help="w4: cross term on the tensor cores (tf32) or CUDA cores (off)")
     ap.add_argument("--dtype", choices=["f32", "f64"], default=None)
     ap.add_argument("--n", type=int, default=None, help="series length override (w1/w2)")
-    ap.add_argument("--nseries", type=int, default=4096, help="w3 set size (profiling runs)")
+    ap.add_argument("--nseries", type=int, default=0, help="w3/w4 set size (profiling runs)")
     ap.add_argument("--accum", choices=["auto", "f32", "kahan"], default="auto",
                     help="w2 FP32 running-cost accumulation")
     ap.add_argument("--rows-per-lane", type=int, default=0, help="w1/w2 schedule override")
@@ -154,18 +156,20 @@ def w3_set(rank: int, nseries: int = 4096):
     return W.set_w3(nseries=nseries, stream=0 if rank == 0 else 10 + rank).astype(np.float32)
 
 
-def run_cpu_baseline(S, pairs, seconds: float, nu, lam, p):
+def run_cpu_baseline(S, pairs, seconds: float, nu, lam, p, SB=None):
     """Time the oracle on a bounded, seeded sample of pairs of the workload."""
     import oracle
     cores = os.cpu_count() or 1
     S64 = S.astype(np.float64)
+    SB64 = S64 if SB is None else SB.astype(np.float64)
     L = S.lengths.astype(np.int64)
+    LB = L if SB is None else SB.lengths.astype(np.int64)
     done, cells, vals, t0 = 0, 0, [], time.perf_counter()
     chunk = max(cores, 8)
     while done < len(pairs) and time.perf_counter() - t0 < seconds:
         pc = pairs[done:done + chunk]
-        vals.append(oracle.twed_pairs(S64.as_tuple(), S64.as_tuple(), pc, nu, lam, p, nthreads=cores))
-        cells += int((L[pc[:, 0]] * L[pc[:, 1]]).sum())
+        vals.append(oracle.twed_pairs(S64.as_tuple(), SB64.as_tuple(), pc, nu, lam, p, nthreads=cores))
+        cells += int((L[pc[:, 0]] * LB[pc[:, 1]]).sum())
         done += len(pc)
     el = time.perf_counter() - t0
     return {"value": cells / el / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -174,22 +178,36 @@ def run_cpu_baseline(S, pairs, seconds: float, nu, lam, p):
 
 
 # ---------------------------------------------------------------- our arm
-def bench_w3(args, rank, world, dev):
+def bench_plan(args, rank, world, dev, workload):
+    """All-pairs (w3, symmetric) or block (w4) plan: one execute per step."""
     import torch
 
     from paper_2007_16135_gb300 import twed
     from paper_2007_16135_gb300 import workloads as W
 
-    nu, lam, p = 0.5, 0.5, 2
-    S = w3_set(rank, args.nseries)
+    if workload == "w3":
+        nu, lam, p, dim = 0.5, 0.5, 2, 8
+        S = w3_set(rank, args.nseries or 4096)
+        SB = None
+        opts = None
+        xterm = False
+    else:
+        nu, lam, p, dim = 1.0, 1.0, 2, 64
+        ns = args.nseries or 2048
+        S = W.set_w4(nseries=ns, stream=0 if rank == 0 else 10 + rank).astype(np.float32)
+        SB = W.set_w4(nseries=ns, stream=1 if rank == 0 else 20 + rank).astype(np.float32)
+        xterm = args.xterm == "tf32"
+        opts = twed.make_opts(xterm=twed.XTERM_TF32 if xterm else twed.XTERM_OFF)
     D = twed.DeviceSet.from_numpy(S.vals, S.ts, S.offs, torch.float32, device=dev)
-    plan = twed.Plan(D, None, nu, lam, p)
+    DB = twed.DeviceSet.from_numpy(SB.vals, SB.ts, SB.offs, torch.float32, device=dev) if SB is not None else None
+    plan = twed.Plan(D, DB, nu, lam, p, opts=opts)
     out = plan.new_output()
     cells = plan.cells
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
         plan.execute(out, stream)
     torch.cuda.synchronize()
+    twed.default_handle().sync_status(stream)
     barrier(world)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     kern_ms = []
@@ -215,29 +233,38 @@ def bench_w3(args, rank, world, dev):
            "ms_per_step": ms_step, "value": value, "clocks": clk.summary(),
            "kernel_ms": float(np.mean(kern_ms))}
 
-    # roofline of the dominant kernel (pairs launch), ALU-bound (FP32 pipe)
+    # roofline of the dominant kernel (the pairs launch): FP32-pipe bound
     props = torch.cuda.get_device_properties(dev)
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", FALLBACK_SM_MAX_MHZ))
     peak_ops = props.multi_processor_count * FP32_LANES_PER_SM * sm_max * 1e6
-    opc = ops_per_cell(8, p)
-    achieved = cells * opc / (res["kernel_ms"] / 1e3)
+    opc = 7 if xterm else ops_per_cell(dim, p)
+    kern_s = res["kernel_ms"] / 1e3
+    achieved = cells * opc / kern_s
     traffic = None
-    tp = os.path.join(ROOT, "profiles", "pairs_kernel_w3_traffic.json")
+    tp = os.path.join(ROOT, "profiles", f"pairs_kernel_{workload}_traffic.json")
     if os.path.exists(tp):
         with open(tp) as f:
             tj = json.load(f)
         if tj.get("src_hash") == kernel_src_hash():
             traffic = tj.get("dram_bytes_per_launch")
+    kname = "xterm_pairs_kernel (tcgen05 tf32)" if xterm else f"pairs_kernel<float,{dim if dim in (1,2,3,4,8) else 0},2,8>"
     res["roofline"] = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                        "unit": "Top/s", "frac": achieved / peak_ops, "traffic": traffic,
                        "ops_per_cell": opc, "peak_basis":
                            f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
                            f"{sm_max:.0f} MHz (max SM clock)",
-                       "kernel": "pairs_kernel<float,8,2,8>"}
+                       "kernel": kname}
+    if xterm:
+        # tensor pipe: 2*64 flops per cell; TF32 dense peak taken as half the
+        # measured BF16 GEMM peak (the nominal TF32:BF16 ratio)
+        tf32_peak = float(peaks.get("bf16_tflops", 1858.6)) / 2.0
+        tflops = cells * 2 * dim / kern_s / 1e12
+        res["tensor"] = {"achieved": tflops, "peak": tf32_peak, "unit": "TFLOP/s",
+                         "frac": tflops / tf32_peak, "basis": "TF32 = measured BF16 burst / 2"}
 
-    # end to end through the public host API (pinned host buffers)
-    if not args.no_e2e:
+    # end to end through the public host API (pinned host buffers): w3 only
+    if not args.no_e2e and workload == "w3":
         pv = torch.from_numpy(np.ascontiguousarray(S.vals)).pin_memory().numpy()
         pt = torch.from_numpy(np.ascontiguousarray(S.ts)).pin_memory().numpy()
         po = np.ascontiguousarray(S.offs)
@@ -253,24 +280,39 @@ def bench_w3(args, rank, world, dev):
                       "h2d_bytes_per_step": int(pv.nbytes + pt.nbytes + po.nbytes),
                       "d2h_bytes_per_step": int(pout.nbytes), "ms_per_step": el,
                       "api": "twed_allpairs_host_f32"}
-    res["gpu_launches"] = 3 * args.steps  # records + pairs + zero-diagonal per step
+    res["gpu_launches"] = (3 if workload == "w3" else 3) * args.steps  # records (+B), pairs, diag
 
     # oracle on a bounded sample: CPU baseline and the error of our output
     if rank == 0 and not args.no_cpu:
         M = out.cpu().numpy()
-        pairs = W.sample_upper_pairs(S.n, min(20000, S.n * (S.n - 1) // 2), 3)
-        cpu, done_pairs, ref = run_cpu_baseline(S, pairs, args.cpu_seconds, nu, lam, p)
+        if workload == "w3":
+            pairs = W.sample_upper_pairs(S.n, min(20000, S.n * (S.n - 1) // 2), 3)
+            SBo = S
+        else:
+            pairs = W.sample_block_pairs(S.n, SB.n, 2000, 4)
+            SBo = SB
+        cpu, done_pairs, ref = run_cpu_baseline(S, pairs, args.cpu_seconds, nu, lam, p, SBo)
         got = M[done_pairs[:, 0], done_pairs[:, 1]].astype(np.float64)
         relerr = np.abs(got - ref) / np.maximum(np.abs(ref), 1e-300)
         res["cpu_baseline"] = cpu
         res["error_vs_oracle"] = {"max_rel": float(relerr.max()), "mean_rel": float(relerr.mean()),
-                                  "pairs": int(len(done_pairs)), "bound": 1e-5}
-    res["config"] = {"workload": f"w3 all-pairs: {S.n} series, dim 8, len U[64,2048], sinusoid "
-                                 "mixtures + N(0,0.1), t_i=i, nu=lambda=0.5, p=2, FP32",
-                     "pairs": plan.pairs, "cells": cells, "series": S.n, "dim": 8,
-                     "l2": "inputs larger than L2 (point records 208 MB > 126 MB L2)",
-                     "parallelism": f"{world} independent replica(s)"}
-    res["dtype"] = "f32"
+                                  "pairs": int(len(done_pairs)),
+                                  "bound": 2e-3 if xterm else 1e-5}
+    if workload == "w3":
+        res["config"] = {"workload": f"w3 all-pairs: {S.n} series, dim 8, len U[64,2048], sinusoid "
+                                     "mixtures + N(0,0.1), t_i=i, nu=lambda=0.5, p=2, FP32",
+                         "pairs": plan.pairs, "cells": cells, "series": S.n, "dim": 8,
+                         "l2": "inputs larger than L2 (point records 208 MB > 126 MB L2)",
+                         "parallelism": f"{world} independent replica(s)"}
+    else:
+        res["config"] = {"workload": f"w4 block: {S.n} x {SB.n} series, dim 64, len U[256,1024], "
+                                     "N(0,1) with a length-5 moving mean, t_i=i, nu=lambda=1, p=2, "
+                                     + ("cross term on tensor cores (TF32 in, FP32 accumulate, FP32 norms)"
+                                        if xterm else "FP32 CUDA cores"),
+                         "pairs": plan.pairs, "cells": cells, "series": [S.n, SB.n], "dim": 64,
+                         "l2": "series values 2 x 336 MB > 126 MB L2",
+                         "parallelism": f"{world} independent replica(s)"}
+    res["dtype"] = "f32" if not xterm else "tf32xf32"
     return res
 
 
@@ -421,8 +463,8 @@ def main():
     dist_init(world, local, True)
     from paper_2007_16135_gb300 import twed
     twed.load()
-    if args.workload == "w3":
-        res = bench_w3(args, rank, world, dev)
+    if args.workload in ("w3", "w4"):
+        res = bench_plan(args, rank, world, dev, args.workload)
     else:
         res = bench_pair(args, rank, world, dev, args.workload)
     if rank == 0:
@@ -431,8 +473,8 @@ def main():
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": res.get("dtype", "f32"), "data": "synthetic (seeded generators)",
                 "config": res["config"]}
-        for k in ("roofline", "cpu_baseline", "e2e", "gpu_launches", "clocks", "error_vs_oracle",
-                  "kernel_ms", "plan", "cells_per_step", "result"):
+        for k in ("roofline", "tensor", "cpu_baseline", "e2e", "gpu_launches", "clocks",
+                  "error_vs_oracle", "kernel_ms", "plan", "cells_per_step", "result"):
             if k in res:
                 line[k] = res[k]
         print(json.dumps(line), flush=True)

@@ -520,6 +520,7 @@ struct twed_plan_s {
     RecordsArgs<double> rda{}, rdb{};
     unsigned* ctl = nullptr;  // plan's own [live err, sticky err]
     unsigned long long* counter = nullptr;
+    bool xterm = false;  // tensor-core cross-term kernel (dim 64, FP32)
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around the pairs launch
     std::string desc;
 };
@@ -542,11 +543,27 @@ RecordsArgs<double>& plan_rec<double>(twed_plan_t pl, int w) { return w ? pl->rd
 
 // Enqueue the whole plan (prologue + persistent pairs launch) on `st`.
 template <typename T>
+cudaError_t launch_plan_records(twed_plan_t pl, const RecordsArgs<T>& r, cudaStream_t st) {
+    if constexpr (sizeof(T) == 4) {
+        if (pl->xterm) return twed::launch_xrecords(r, st);
+    }
+    return twed::launch_records(r, st);
+}
+
+template <typename T>
+cudaError_t launch_plan_pairs(twed_plan_t pl, const PairsArgs<T>& pa, cudaStream_t st) {
+    if constexpr (sizeof(T) == 4) {
+        if (pl->xterm) return twed::launch_xterm_pairs(pa, pl->blocks, st);
+    }
+    return twed::launch_pairs(pa, pl->blocks, pl->threads, st);
+}
+
+template <typename T>
 cudaError_t plan_enqueue(twed_plan_t pl, T* out, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(pl->counter, 0, sizeof(unsigned long long), st);
     if (e == cudaSuccess) e = cudaMemsetAsync(pl->ctl, 0, sizeof(unsigned), st);
-    if (e == cudaSuccess) e = twed::launch_records(plan_rec<T>(pl, 0), st);
-    if (e == cudaSuccess && !pl->symmetric) e = twed::launch_records(plan_rec<T>(pl, 1), st);
+    if (e == cudaSuccess) e = launch_plan_records<T>(pl, plan_rec<T>(pl, 0), st);
+    if (e == cudaSuccess && !pl->symmetric) e = launch_plan_records<T>(pl, plan_rec<T>(pl, 1), st);
     PairsArgs<T> pa = plan_pairs<T>(pl);
     pa.out = out;
     // inside a capture the records become graph event-record nodes
@@ -554,7 +571,7 @@ cudaError_t plan_enqueue(twed_plan_t pl, T* out, cudaStream_t st) {
     if (e == cudaSuccess) e = cudaStreamIsCapturing(st, &cs);
     const unsigned evflag = cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0u;
     if (e == cudaSuccess) e = cudaEventRecordWithFlags(pl->ev0, st, evflag);
-    if (e == cudaSuccess) e = twed::launch_pairs(pa, pl->blocks, pl->threads, st);
+    if (e == cudaSuccess) e = launch_plan_pairs<T>(pl, pa, st);
     if (e == cudaSuccess) e = cudaEventRecordWithFlags(pl->ev1, st, evflag);
     if (e == cudaSuccess && pl->symmetric) e = twed::launch_zero_diag(out, pl->f64, pl->na, st);
     return e;
@@ -616,14 +633,33 @@ twed_status_t plan_create(twed_handle_t h, const S* A, const S* B, int dim, T nu
     }
     pl->cells = cells;
 
-    const int rl = twed::rec_len<T>(dim, p);
-    const int threads = 128;
-    const int per_sm = std::max(1, twed::pairs_blocks_per_sm<T>(dim, p, threads));
+    const bool want_x = o && o->xterm == TWED_XTERM_TF32;
+    if (o && (o->xterm < TWED_XTERM_OFF || o->xterm > TWED_XTERM_TF32)) {
+        delete pl;
+        return fail(h, TWED_ERR_INVALID_ARG, "unknown xterm mode %d", o->xterm);
+    }
+    if (want_x && (sizeof(T) != 4 || dim != 64 || p != 2 ||
+                   std::max(maxa, maxb) > twed::xterm_max_cols())) {
+        delete pl;
+        return fail(h, TWED_ERR_UNSUPPORTED,
+                    "tensor-core cross term: FP32, dim 64, p 2 and series of <= %d points only",
+                    twed::xterm_max_cols());
+    }
+    if (want_x && (((uintptr_t)A->vals & 15) || (!sym && ((uintptr_t)B->vals & 15)))) {
+        delete pl;
+        return fail(h, TWED_ERR_UNSUPPORTED, "tensor-core cross term: values must be 16-byte aligned");
+    }
+    pl->xterm = want_x;
+    const int rl = pl->xterm ? 4 : twed::rec_len<T>(dim, p);
+    const int threads = pl->xterm ? 192 : 128;
+    const int per_sm = std::max(1, pl->xterm ? twed::xterm_blocks_per_sm()
+                                             : twed::pairs_blocks_per_sm<T>(dim, p, threads));
     const int64_t want_blocks = (int64_t)per_sm * h->sms;
-    const int64_t need_blocks = std::max<int64_t>(1, (pl->npairs + 3) / 4);
+    const int64_t need_blocks = pl->xterm ? std::max<int64_t>(1, pl->npairs)
+                                          : std::max<int64_t>(1, (pl->npairs + 3) / 4);
     pl->blocks = (int)std::min(want_blocks, need_blocks);
     pl->threads = threads;
-    const int64_t nwarps = (int64_t)pl->blocks * (threads / 32);
+    const int64_t nwarps = pl->xterm ? 0 : (int64_t)pl->blocks * (threads / 32);
     const int64_t scols = (std::max(maxa, maxb) + 2) & ~(int64_t)1;  // >= longest + 1, even
 
     Carver cv;
@@ -697,9 +733,13 @@ twed_status_t plan_create(twed_handle_t h, const S* A, const S* B, int dim, T nu
         return cuda_fail(h, e, "cudaStreamCreate");
     }
     char d[160];
-    snprintf(d, sizeof d, "%s pairs=%lld warps=%lld rows_per_lane<=%d blocks=%d x %d threads",
-             sizeof(T) == 8 ? "f64" : "f32", (long long)pl->npairs, (long long)nwarps, pa.rmax,
-             pl->blocks, threads);
+    if (pl->xterm)
+        snprintf(d, sizeof d, "f32 tensor-core cross term (tf32) pairs=%lld blocks=%d x %d threads",
+                 (long long)pl->npairs, pl->blocks, threads);
+    else
+        snprintf(d, sizeof d, "%s pairs=%lld warps=%lld rows_per_lane<=%d blocks=%d x %d threads",
+                 sizeof(T) == 8 ? "f64" : "f32", (long long)pl->npairs, (long long)nwarps, pa.rmax,
+                 pl->blocks, threads);
     pl->desc = d;
     *out_plan = pl;
     return TWED_OK;

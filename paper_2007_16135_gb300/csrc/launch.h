@@ -108,6 +108,13 @@ int pairs_blocks_per_sm(int dim, int p, int threads);
 template <typename T>
 int pairs_rmax_limit();
 
+// Tensor-core cross-term path (xterm.cu): dim 64, p = 2, FP32.
+// Records are float4 (t, delete cost, |x|^2, 0) per point.
+cudaError_t launch_xrecords(const RecordsArgs<float>& a, cudaStream_t st);
+cudaError_t launch_xterm_pairs(const PairsArgs<float>& a, int blocks, cudaStream_t st);
+int xterm_blocks_per_sm();
+int xterm_max_cols();
+
 // Writes 0 to out[i*n + i], i < n.
 cudaError_t launch_zero_diag(void* out, bool f64, int64_t n, cudaStream_t st);
 

@@ -47,14 +47,18 @@ class TwedError(RuntimeError):
         self.status = status
 
 
+XTERM_OFF, XTERM_TF32 = 0, 1
+
+
 class Opts(ctypes.Structure):
     _fields_ = [("accum", ctypes.c_int), ("rows_per_lane", ctypes.c_int),
                 ("autotune", ctypes.c_int), ("timeout_s", ctypes.c_double),
-                ("stall_strip", ctypes.c_int64)]
+                ("stall_strip", ctypes.c_int64), ("xterm", ctypes.c_int)]
 
 
-def make_opts(accum=0, rows_per_lane=0, autotune=0, timeout_s=0.0, stall_strip=-1) -> Opts:
-    return Opts(accum, rows_per_lane, autotune, timeout_s, stall_strip)
+def make_opts(accum=0, rows_per_lane=0, autotune=0, timeout_s=0.0, stall_strip=-1,
+              xterm=0) -> Opts:
+    return Opts(accum, rows_per_lane, autotune, timeout_s, stall_strip, xterm)
 
 
 class _SetF64(ctypes.Structure):

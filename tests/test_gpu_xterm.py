@@ -1,0 +1,108 @@
+"""Tensor-core cross term (dim 64, p = 2, TF32 inputs, FP32 accumulation).
+
+The cell cost uses |a_i - b_j|^2 = |a_i|^2 + |b_j|^2 - 2 a_i . b_j with the
+dot products on the tensor cores.  TF32 keeps 10 mantissa bits of each
+input, so every cost carries about 1e-4 relative error; the test bounds the
+TWED error at 2e-3 relative and checks that the CUDA-core FP32 path on the
+same inputs stays within the 1e-5 FP32 bound.  Lengths straddle the 128-row
+strips and 16-column tiles (1, 15, 16, 17, 127, 128, 129, ...).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2007_16135_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+LENGTHS_A = [1, 15, 16, 17, 127, 128, 129, 300, 257, 64]
+LENGTHS_B = [1, 16, 33, 128, 200, 255, 256, 513]
+
+
+@pytest.fixture(scope="module")
+def tw():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_2007_16135_gb300 import twed
+    twed.load()
+    return twed
+
+
+def smoothed_set(seed, lengths):
+    rng = np.random.default_rng(seed)
+    out = []
+    for n in lengths:
+        raw = rng.standard_normal((n + 4, 64))
+        c = np.cumsum(np.vstack([np.zeros((1, 64)), raw]), axis=0)
+        out.append(((c[5:] - c[:-5]) / 5.0, np.arange(1, n + 1, dtype=np.float64)))
+    return W.pack(out).astype(np.float32)
+
+
+def matrix(tw, SA, SB, xterm, nu=1.0, lam=1.0):
+    import torch
+    A = tw.DeviceSet.from_numpy(SA.vals, SA.ts, SA.offs, torch.float32)
+    B = tw.DeviceSet.from_numpy(SB.vals, SB.ts, SB.offs, torch.float32) if SB is not None else None
+    plan = tw.Plan(A, B, nu, lam, 2, opts=tw.make_opts(xterm=xterm))
+    M = plan.execute().cpu().numpy()
+    torch.cuda.synchronize()
+    tw.default_handle().sync_status()
+    return M, plan.describe()
+
+
+def oracle_block(SA, SB):
+    pairs = np.array([(i, j) for i in range(SA.n) for j in range(SB.n)])
+    A64, B64 = SA.astype(np.float64), SB.astype(np.float64)
+    return oracle.twed_pairs(A64.as_tuple(), B64.as_tuple(), pairs, 1.0, 1.0, 2).reshape(SA.n, SB.n)
+
+
+def test_tensor_core_block_matches_oracle(tw):
+    SA, SB = smoothed_set(1, LENGTHS_A), smoothed_set(2, LENGTHS_B)
+    ref = oracle_block(SA, SB)
+    Mx, desc = matrix(tw, SA, SB, tw.XTERM_TF32)
+    assert "tensor-core" in desc
+    rel = np.abs(Mx - ref) / ref
+    print(f"tensor-core cross term: max rel err {rel.max():.3e}, mean {rel.mean():.3e}")
+    assert rel.max() <= 2e-3
+    Mc, _ = matrix(tw, SA, SB, tw.XTERM_OFF)
+    assert (np.abs(Mc - ref) / ref).max() <= 1e-5
+
+
+def test_tensor_core_symmetric_plan(tw):
+    S = smoothed_set(3, [40, 129, 1, 256, 17, 90, 300])
+    Mx, _ = matrix(tw, S, None, tw.XTERM_TF32)
+    ref = oracle_block(S, S)
+    iu = np.triu_indices(S.n, 1)
+    assert (np.abs(Mx[iu] - ref[iu]) / ref[iu]).max() <= 2e-3
+    assert np.array_equal(Mx, Mx.T) and np.all(np.diag(Mx) == 0)
+
+
+def test_tensor_core_refuses_other_shapes(tw):
+    import torch
+    S = smoothed_set(4, [20, 30])
+    V = S.vals[:, :32].copy()
+    D = tw.DeviceSet.from_numpy(V, S.ts, S.offs, torch.float32)
+    with pytest.raises(tw.TwedError) as ei:
+        tw.Plan(D, None, 1.0, 1.0, 2, opts=tw.make_opts(xterm=tw.XTERM_TF32))
+    assert ei.value.status == tw.TWED_ERR_UNSUPPORTED
+
+
+def test_w4_full_size_sampled(tw):
+    # 2048 x 2048 series, dim 64, lengths U[256, 1024]: the bench's launch
+    # configuration; 64 sampled pairs against the FP64 oracle
+    import torch
+    SA = W.set_w4(stream=0).astype(np.float32)
+    SB = W.set_w4(stream=1).astype(np.float32)
+    A = tw.DeviceSet.from_numpy(SA.vals, SA.ts, SA.offs, torch.float32)
+    B = tw.DeviceSet.from_numpy(SB.vals, SB.ts, SB.offs, torch.float32)
+    plan = tw.Plan(A, B, 1.0, 1.0, 2, opts=tw.make_opts(xterm=tw.XTERM_TF32))
+    M = plan.execute()
+    torch.cuda.synchronize()
+    tw.default_handle().sync_status()
+    pairs = W.sample_block_pairs(SA.n, SB.n, 64, 4)
+    got = M[torch.as_tensor(pairs[:, 0]).cuda(), torch.as_tensor(pairs[:, 1]).cuda()].cpu().numpy()
+    A64, B64 = SA.astype(np.float64), SB.astype(np.float64)
+    ref = oracle.twed_pairs(A64.as_tuple(), B64.as_tuple(), pairs, 1.0, 1.0, 2)
+    rel = np.abs(got - ref) / ref
+    print(f"w4 full size, 64 sampled pairs: max rel err {rel.max():.3e}")
+    assert rel.max() <= 2e-3
