@@ -184,14 +184,106 @@ __device__ __forceinline__ bool run_strip_staged(const PairRef<float>& pr, int r
     }
     issue(0);
 
+    // The loop is software-pipelined: step s prefetches the record and the
+    // boundary entry of its next column and forms all R cell costs for it
+    // (none of that depends on D), so the shared-memory loads, the distance
+    // arithmetic and the square roots of step s+1 overlap the min-plus chain
+    // of step s.  Staging waits therefore run one step ahead of the columns.
+    // Before step 0: chunk 0 resident, chunk 1 in flight, first 8 hand-off
+    // columns present.
+    cp_async_wait_all();
+    __syncwarp();
+    if (33 <= m) {
+        if (up_global && io.up_flag != nullptr) {
+            const bool w = wait_progress(io.up_flag, (unsigned)min(64, m), sc);
+            if (__any_sync(kFull, !w)) {
+                cp_async_wait_all();
+                return false;
+            }
+        }
+        issue(1);
+    }
+    if (io.up_local) {
+        const bool w = wait_local(io.up_prog, min(8, m), sc);
+        if (__any_sync(kFull, !w)) {
+            cp_async_wait_all();
+            return false;
+        }
+    }
+
+    // next column's inputs (valid when its column is in 1..m)
+    float cn[R];
+    float tbn = 0.f, delbn = 0.f;
+    float4 bndn = make_float4(0.f, 0.f, 0.f, 0.f);
+    float recn[LEN];
+    // (a) the shared-memory loads of the next column's record and boundary entry
+    auto prefetch_load = [&](int jn) {
+        const int jc = jn < 1 ? 1 : (jn > m ? m : jn);
+        const int slot = (jc - 1) & (kRingCols - 1);
+        const float4* rp = reinterpret_cast<const float4*>(ring + slot * LEN);
+#pragma unroll
+        for (int q = 0; q < LEN / 4; ++q) {
+            const float4 v = rp[q];
+            recn[4 * q] = v.x;
+            recn[4 * q + 1] = v.y;
+            recn[4 * q + 2] = v.z;
+            recn[4 * q + 3] = v.w;
+        }
+        if constexpr (KH) {
+            bndn = bring4[slot];
+        } else {
+            const float2 b2 = bring2[slot];
+            bndn = make_float4(b2.x, 0.f, b2.y, 0.f);  // (D, -, c, -)
+        }
+    };
+    // (b) the R cell costs of that column
+    auto prefetch_costs = [&]() {
+        tbn = recn[RL::kT];
+        delbn = recn[RL::kDel];
+        if constexpr (PACK) {
+            unsigned long long B2[DIM];
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) B2[k] = f2_pack(recn[2 * k], recn[2 * k + 1]);
+#pragma unroll
+            for (int q = 0; q < R / 2; ++q) {
+                unsigned long long d2 = f2_sub(A2[q][0], B2[0]);
+                unsigned long long s2 = f2_mul(d2, d2);
+#pragma unroll
+                for (int k = 1; k < DIM; ++k) {
+                    d2 = f2_sub(A2[q][k], B2[k]);
+                    s2 = f2_fma(d2, d2, s2);
+                }
+                float s0, s1;
+                f2_unpack(s2, s0, s1);
+                cn[2 * q] = fmaf(pr.nu, fabsf(rt[2 * q] - tbn), Arith<float>::root(s0));
+                cn[2 * q + 1] = fmaf(pr.nu, fabsf(rt[2 * q + 1] - tbn), Arith<float>::root(s1));
+            }
+        } else {
+            float bv[DIM];
+#pragma unroll
+            for (int k = 0; k < DIM; ++k) bv[k] = recn[2 * k];
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+                cn[r] = fmaf(pr.nu, fabsf(rt[r] - tbn), dist<float, DIM, P>(ra[r], bv, DIM, pr.p));
+        }
+    };
+    prefetch_load(1 - lane);
+    prefetch_costs();
+
     const int steps = m + lanes_used - 1;
     int j = 1 - lane;
     for (int s = 0; s < steps; ++s, ++j) {
-        if ((s & 31) == 0) {
-            // chunk s/32 (issued 32 steps ago) must have landed; then stage the next one
+        // this step's inputs, prefetched by the previous step
+        float cc[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) cc[r] = cn[r];
+        const float delb = delbn;
+        const float4 bnd = bndn;
+        if (((s + 1) & 31) == 0) {
+            // the prefetch below reads chunk (s+1)/32 (issued 32 steps ago); stage the next
             cp_async_wait_all();
             __syncwarp();
-            const int c = (s >> 5) + 1;
+            const int c = ((s + 1) >> 5) + 1;
             if (32 * c + 1 <= m) {
                 if (up_global && io.up_flag != nullptr) {
                     const bool w = wait_progress(io.up_flag, (unsigned)min(32 * c + 32, m), sc);
@@ -203,17 +295,17 @@ __device__ __forceinline__ bool run_strip_staged(const PairRef<float>& pr, int r
                 issue(c);
             }
         }
-        if ((s & 7) == 0 && (io.up_local || io.down_local != nullptr)) {
+        if (((s + 1) & 7) == 0 && (io.up_local || io.down_local != nullptr)) {
             // block-local hand-off, 8 columns at a time: the row above must be
-            // written for lane 0's next 8 columns, and the warp below must have
-            // consumed what lane 31's next 8 writes overwrite (ring of 128)
+            // written for lane 0's next 8 prefetches, and the warp below must
+            // have consumed what lane 31's next 8 writes overwrite (ring of 128)
             bool w = true;
             if (io.up_local) {
                 if (lane == 0) {
                     __threadfence_block();
-                    *io.my_cons = s;  // columns 1..s of the ring are consumed
+                    *io.my_cons = s + 1;  // ring columns 1..s+1 are consumed
                 }
-                if (s < m) w = wait_local(io.up_prog, min(s + 8, m), sc);
+                if (s + 2 <= m) w = wait_local(io.up_prog, min(s + 9, m), sc);
             }
             if (w && io.down_local != nullptr && s - 151 >= 1)
                 w = wait_local(io.down_cons, s - 151, sc);
@@ -222,67 +314,21 @@ __device__ __forceinline__ bool run_strip_staged(const PairRef<float>& pr, int r
                 return false;
             }
         }
+        // one basic block from here to the output test, so that the loads
+        // and arithmetic of the next column interleave with this column's
+        // chain (warps issue in order; a branch would serialise them)
+        prefetch_load(j + 1);
         float upD = __shfl_up_sync(kFull, botD, 1);
         float upC = __shfl_up_sync(kFull, botC, 1);
         float upL = 0.f;
         if constexpr (KH) upL = __shfl_up_sync(kFull, botL, 1);
-        if (j >= 1 && j <= m) {
-            const int slot = (j - 1) & (kRingCols - 1);
-            const float4* rp = reinterpret_cast<const float4*>(ring + slot * LEN);
-            float rec[LEN];
-#pragma unroll
-            for (int q = 0; q < LEN / 4; ++q) {
-                const float4 v = rp[q];
-                rec[4 * q] = v.x;
-                rec[4 * q + 1] = v.y;
-                rec[4 * q + 2] = v.z;
-                rec[4 * q + 3] = v.w;
-            }
-            if constexpr (KH) {
-                const float4 bnd = bring4[slot];
-                if (lane == 0) {
-                    upD = first ? INF : bnd.x;  // D(r0-1, j), hi and lo
-                    upL = first ? 0.f : bnd.y;
-                    upC = first ? 0.f : bnd.z;  // c(r0-1, j)
-                }
-            } else {
-                const float2 bnd = bring2[slot];
-                if (lane == 0) {
-                    upD = first ? INF : bnd.x;  // D(r0-1, j)
-                    upC = first ? 0.f : bnd.y;  // c(r0-1, j)
-                }
-            }
-            const float tb = rec[RL::kT];
-            const float delb = rec[RL::kDel];
-            // (1) all R cell costs: independent of each other and of this
-            //     step's D values, so they overlap freely
-            float cc[R];
-            if constexpr (PACK) {
-                unsigned long long B2[DIM];
-#pragma unroll
-                for (int k = 0; k < DIM; ++k) B2[k] = f2_pack(rec[2 * k], rec[2 * k + 1]);
-#pragma unroll
-                for (int q = 0; q < R / 2; ++q) {
-                    unsigned long long d2 = f2_sub(A2[q][0], B2[0]);
-                    unsigned long long s2 = f2_mul(d2, d2);
-#pragma unroll
-                    for (int k = 1; k < DIM; ++k) {
-                        d2 = f2_sub(A2[q][k], B2[k]);
-                        s2 = f2_fma(d2, d2, s2);
-                    }
-                    float s0, s1;
-                    f2_unpack(s2, s0, s1);
-                    cc[2 * q] = fmaf(pr.nu, fabsf(rt[2 * q] - tb), Arith<float>::root(s0));
-                    cc[2 * q + 1] = fmaf(pr.nu, fabsf(rt[2 * q + 1] - tb), Arith<float>::root(s1));
-                }
-            } else {
-                float bv[DIM];
-#pragma unroll
-                for (int k = 0; k < DIM; ++k) bv[k] = rec[2 * k];
-#pragma unroll
-                for (int r = 0; r < R; ++r)
-                    cc[r] = fmaf(pr.nu, fabsf(rt[r] - tb), dist<float, DIM, P>(ra[r], bv, DIM, pr.p));
-            }
+        upD = lane == 0 ? (first ? INF : bnd.x) : upD;  // D(r0-1, j)
+        upC = lane == 0 ? (first ? 0.f : bnd.z) : upC;  // c(r0-1, j)
+        if constexpr (KH) upL = lane == 0 ? (first ? 0.f : bnd.y) : upL;
+        // a lane that has not reached column 1 sees an infinite row above: its
+        // state then stays exactly at D(i, 0) = inf, so no branch is needed
+        upD = j < 1 ? INF : upD;
+        {
             // (2) the parts of each update that do not depend on the row just
             //     above in this step: deletion in b and the match candidate
             //     (both read only the previous column)
@@ -347,17 +393,22 @@ __device__ __forceinline__ bool run_strip_staged(const PairRef<float>& pr, int r
                 diagL = upL;
                 botL = Dlo[R - 1];
             }
-            if (io.down != nullptr && lane == 31) {
+            prefetch_costs();
+            const bool act = (j >= 1 && j <= m);
+            if (io.down != nullptr && lane == 31 && act) {
                 if constexpr (KH) __stcg(down4 + (j - 1), make_float4(botD, botL, botC, 0.f));
                 else __stcg(io.down + (j - 1), make_float2(botD, botC));
-                if (io.down_flag != nullptr && io.publish && (((j & 31) == 0) || j == m))
-                    st_release(io.down_flag, (unsigned)j);
             }
-            if (io.down_local != nullptr && lane == 31) {
+            if (io.down_local != nullptr && lane == 31 && act) {
                 const int slot_d = (j - 1) & (kRingCols - 1);
                 if constexpr (KH) dloc4[slot_d] = make_float4(botD, botL, botC, 0.f);
                 else dloc2[slot_d] = make_float2(botD, botC);
-                if (io.publish && (((j & 7) == 0) || j == m)) {
+            }
+            if (lane == 31 && act && (((j & 7) == 0) || j == m)) {
+                // progress publication (rare): global every 32 columns, block-local every 8
+                if (io.down_flag != nullptr && io.publish && (((j & 31) == 0) || j == m))
+                    st_release(io.down_flag, (unsigned)j);
+                if (io.down_local != nullptr && io.publish) {
                     __threadfence_block();
                     *io.down_prog = j;
                 }

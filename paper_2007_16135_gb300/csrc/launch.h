@@ -114,6 +114,8 @@ cudaError_t launch_xrecords(const RecordsArgs<float>& a, cudaStream_t st);
 cudaError_t launch_xterm_pairs(const PairsArgs<float>& a, int blocks, cudaStream_t st);
 int xterm_blocks_per_sm();
 int xterm_max_cols();
+int xterm_resident_blocks();
+void xterm_resources(char* buf, int len);
 
 // Writes 0 to out[i*n + i], i < n.
 cudaError_t launch_zero_diag(void* out, bool f64, int64_t n, cudaStream_t st);

@@ -10,16 +10,21 @@
 // same as everywhere else in this library.
 //
 // One persistent block handles one pair at a time (pairs from an atomic
-// counter, longest series first).  Warp roles:
-//   warp 0      producer: cp.async of the strip (A) and column tiles (B) into
-//               shared memory in the K-major core-matrix layout, tcgen05.mma
-//               issue, tcgen05.commit to an mbarrier.  Also owns the TMEM.
-//   warps 1..4  epilogue: tcgen05.ld of their TMEM lane quarter, cost
+// counter, longest series first); three blocks share an SM.  Warp roles:
+//   warp 0      producer: cp.async of the column tiles (B) into a 4-deep
+//               shared-memory ring in the K-major core-matrix layout, two
+//               tiles ahead; tcgen05.mma issue (A from tensor memory),
+//               tcgen05.commit to an mbarrier.  Also owns the TMEM.
+//   warps 1..4  epilogue: at each strip, load the strip's 128 points (one
+//               per thread) into tensor memory with tcgen05.st (A operand);
+//               per tile, tcgen05.ld of their TMEM lane quarter, cost
 //               formation, store into a ring of cost tiles [col][row].
 //   warp 5      wavefront: 32 lanes x 4 rows = the strip's 128 rows, lane L
 //               on column s - L at step s, costs read from the ring.
-// Every wait is bounded (iteration limit, then the launch's error word).
+// Every wait is bounded (%globaltimer, then the launch's error word).
 #include <cuda_runtime.h>
+
+#include <cstdio>
 
 #include "kernels.cuh"
 #include "tc.cuh"
@@ -31,17 +36,20 @@ constexpr int D = 64;         // point dimension (MMA K)
 constexpr int M = 128;        // rows per strip (MMA M)
 constexpr int N = 16;         // columns per tile (MMA N)
 constexpr int R = 4;          // wavefront rows per lane
-constexpr int NB = 2;         // B tiles / TMEM accumulators in flight
+constexpr int NB = 2;         // TMEM accumulators in flight
+constexpr int NBB = 4;        // B tiles in the shared-memory ring
+constexpr int PREF = 2;       // B tiles loaded ahead of the MMA
 constexpr int NC = 6;         // cost tiles in the ring (wavefront span 3 + lead 3)
 constexpr int MAXCOL = 1024;  // longest column series (boundary row kept in smem)
 constexpr int THREADS = 192;
+constexpr int TMEM_COLS = 128;  // NB*N accumulator columns + D columns of A
+constexpr int ACOL = 64;        // first TMEM column of the A strip
 
-constexpr int OFF_A = 0;                               // M*D floats, K-major core layout
-constexpr int OFF_B = OFF_A + M * D * 4;               // NB tiles of N*D floats
-constexpr int OFF_C = OFF_B + NB * N * D * 4;          // NC tiles [N][M] costs
+constexpr int OFF_B = 0;                               // NBB tiles of N*D floats
+constexpr int OFF_C = OFF_B + NBB * N * D * 4;         // NC tiles [N][M] costs
 constexpr int OFF_ROW = OFF_C + NC * N * M * 4;        // MAXCOL float2 boundary row
 constexpr int OFF_BAR = OFF_ROW + MAXCOL * 8;          // mbarriers
-constexpr int NBAR = NB + NB + NC + NC;                // mma_done, tmem_empty, cost_full, cost_empty
+constexpr int NBAR = NB + NB + NC + NC + 1;            // mma_done, tmem_empty, cost_full, cost_empty, a_ready
 constexpr int OFF_MISC = OFF_BAR + NBAR * 8;           // tmem base, pair index
 constexpr int SMEM = OFF_MISC + 64;
 }  // namespace x64
@@ -106,12 +114,20 @@ __device__ __forceinline__ bool xwait(uint64_t* bar, uint32_t parity, const Sync
 
 }  // namespace
 
+// cp.async.wait_group needs an immediate: wait until at most `pending`
+// groups of this thread are still in flight (pending <= PREF).
+__device__ __forceinline__ void cp_async_wait_pending(int pending) {
+    if (pending <= 0) asm volatile("cp.async.wait_group 0;" ::: "memory");
+    else if (pending == 1) asm volatile("cp.async.wait_group 1;" ::: "memory");
+    else asm volatile("cp.async.wait_group 2;" ::: "memory");
+}
+
 // PairsArgs as for pairs_kernel; rec_a / rec_b hold x64 records (float4 per
-// point) and vals_a / vals_b the raw 64-dimensional points.
+// point) and vals_a / vals_b the raw 64-dimensional points (16-byte aligned).
 __global__ void __launch_bounds__(x64::THREADS) xterm_pairs_kernel(PairsArgs<float> a) {
     using namespace x64;
+    static_assert(PREF <= 2 && PREF < NBB, "cp_async_wait_pending covers PREF <= 2");
     extern __shared__ __align__(1024) unsigned char sm[];
-    float* sA = reinterpret_cast<float*>(sm + OFF_A);
     float* sC = reinterpret_cast<float*>(sm + OFF_C);
     float2* sRow = reinterpret_cast<float2*>(sm + OFF_ROW);
     uint64_t* bar = reinterpret_cast<uint64_t*>(sm + OFF_BAR);
@@ -119,6 +135,7 @@ __global__ void __launch_bounds__(x64::THREADS) xterm_pairs_kernel(PairsArgs<flo
     uint64_t* tmem_empty = bar + NB;
     uint64_t* cost_full = bar + 2 * NB;
     uint64_t* cost_empty = bar + 2 * NB + NC;
+    uint64_t* a_ready = bar + 2 * NB + 2 * NC;
     uint32_t* misc = reinterpret_cast<uint32_t*>(sm + OFF_MISC);
     volatile long long* pair_sh = reinterpret_cast<volatile long long*>(misc + 2);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -133,16 +150,18 @@ __global__ void __launch_bounds__(x64::THREADS) xterm_pairs_kernel(PairsArgs<flo
             tc::mbar_init(&cost_full[i], 4);
             tc::mbar_init(&cost_empty[i], 1);
         }
+        tc::mbar_init(a_ready, 4);
     }
-    if (warp == 0) tc::tmem_alloc(misc, 32);  // NB accumulators x N columns
+    if (warp == 0) tc::tmem_alloc(misc, TMEM_COLS);
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = misc[0];
     const uint32_t idesc = tc::idesc_tf32(M, N);
 
-    // per-role running tile counters (identical sequences in every role)
-    long long t_prod = 0, t_epi = 0, t_dp = 0;
+    // per-role running counters (identical sequences in every role)
+    long long t_prod = 0, t_epi = 0, t_dp = 0;  // tiles
+    long long s_prod = 0, s_epi = 0;            // strips
     bool ok = true;
     while (true) {
         __syncthreads();
@@ -182,61 +201,94 @@ __global__ void __launch_bounds__(x64::THREADS) xterm_pairs_kernel(PairsArgs<flo
         const float4* crec = reinterpret_cast<const float4*>(swap ? a.rec_a : a.rec_b) + (swap ? xa : yb);
         const int n = (int)(swap ? ny : nx), m = (int)(swap ? nx : ny);
         const int nstrips = (n + M - 1) / M, ntiles = (m + N - 1) / N;
+        const int K = nstrips * ntiles;  // tiles of this pair, strip-major
 
         if (warp == 0) {
             // ================= producer
-            for (int st = 0; st < nstrips && ok; ++st) {
-                // the previous strip's MMAs read A: wait for the last of them
-                if (t_prod > 0) ok = xwait(&mma_done[(t_prod - 1) % NB], (uint32_t)(((t_prod - 1) / NB) & 1), a.sc);
-                if (!__all_sync(kFull, ok)) { ok = false; break; }
-                const int r0 = st * M;
-                for (int c = lane; c < M * (D / 4); c += 32) {
-                    const int row = c / (D / 4), kq = c % (D / 4);
-                    const bool v = r0 + row < n;
-                    const float* src = rvals + (int64_t)(v ? r0 + row : 0) * D + kq * 4;
-                    cp_async16_zfill(reinterpret_cast<unsigned char*>(sA) + tc::kmajor_offset(row, kq * 4, D), src, v);
+            const long long t_base = t_prod;
+            int issued = 0;  // B tiles of this pair whose copies were issued
+            // B tile k of this pair (column tile k % ntiles) into ring slot (t_base + k) % NBB;
+            // the slot was last read by the MMA of tile t_base + k - NBB.  Tiles of
+            // earlier pairs are all complete (every role finished them before the
+            // block moved on), and waiting on their phases could alias a later
+            // phase of the same barrier, so only this pair's tiles are waited for.
+            auto issue_load = [&](int k) -> bool {
+                const long long t = t_base + k;
+                if (k >= NBB) {
+                    const long long tp = t - NBB;
+                    if (!xwait(&mma_done[tp % NB], (uint32_t)((tp / NB) & 1), a.sc)) return false;
+                }
+                unsigned char* sB = sm + OFF_B + (int)(t % NBB) * N * D * 4;
+                const int c0 = (k % ntiles) * N;
+                for (int c = lane; c < N * (D / 4); c += 32) {
+                    const int col = c / (D / 4), kq = c % (D / 4);
+                    const bool v = c0 + col < m;
+                    const float* src = cvals + (int64_t)(v ? c0 + col : 0) * D + kq * 4;
+                    cp_async16_zfill(sB + tc::kmajor_offset(col, kq * 4, D), src, v);
                 }
                 cp_async_commit();
-                for (int tt = 0; tt < ntiles; ++tt, ++t_prod) {
-                    const int b = (int)(t_prod % NB);
-                    bool w2 = true;
-                    if (t_prod >= NB) w2 = xwait(&mma_done[b], (uint32_t)(((t_prod - NB) / NB) & 1), a.sc);
-                    if (!__all_sync(kFull, w2)) { ok = false; break; }
-                    const int c0 = tt * N;
-                    unsigned char* sB = sm + OFF_B + b * N * D * 4;
-                    for (int c = lane; c < N * (D / 4); c += 32) {
-                        const int col = c / (D / 4), kq = c % (D / 4);
-                        const bool v = c0 + col < m;
-                        const float* src = cvals + (int64_t)(v ? c0 + col : 0) * D + kq * 4;
-                        cp_async16_zfill(sB + tc::kmajor_offset(col, kq * 4, D), src, v);
-                    }
-                    cp_async_commit();
-                    cp_async_wait_all();
-                    tc::fence_proxy_async_smem();
-                    __syncwarp();
-                    if (t_prod >= NB) w2 = xwait(&tmem_empty[b], (uint32_t)(((t_prod - NB) / NB) & 1), a.sc);
-                    if (!__all_sync(kFull, w2)) { ok = false; break; }
-                    tc::fence_after_sync();
-                    if (lane == 0) {
-                        const uint32_t aad = tc::smem_u32(sA), bad = tc::smem_u32(sB);
-#pragma unroll
-                        for (int ks = 0; ks < D / 8; ++ks) {
-                            const uint64_t ad = tc::smem_desc(aad + ks * 2 * tc::kmajor_lbo(), tc::kmajor_lbo(), tc::kmajor_sbo(D));
-                            const uint64_t bd = tc::smem_desc(bad + ks * 2 * tc::kmajor_lbo(), tc::kmajor_lbo(), tc::kmajor_sbo(D));
-                            tc::mma_tf32(tmem + (uint32_t)(b * N), ad, bd, idesc, ks > 0);
-                        }
-                        tc::mma_commit(&mma_done[b]);
-                    }
-                    __syncwarp();
+                return true;
+            };
+            for (int k = 0; k < K && ok; ++k) {
+                while (issued < K && issued <= k + PREF && ok) {
+                    ok = __all_sync(kFull, issue_load(issued));
+                    ++issued;
                 }
+                if (!ok) break;
+                cp_async_wait_pending(issued - k - 1);  // tile k's copies are in
+                tc::fence_proxy_async_smem();
+                __syncwarp();
+                const long long t = t_prod;
+                const int b = (int)(t % NB);
+                bool w2 = true;
+                if (k % ntiles == 0) w2 = xwait(a_ready, (uint32_t)(s_prod & 1), a.sc);  // strip's A in TMEM
+                if (w2 && t >= NB) w2 = xwait(&tmem_empty[b], (uint32_t)(((t - NB) / NB) & 1), a.sc);
+                if (!__all_sync(kFull, w2)) { ok = false; break; }
+                tc::fence_after_sync();
+                if (lane == 0) {
+                    const uint32_t bad = tc::smem_u32(sm + OFF_B + (int)(t % NBB) * N * D * 4);
+#pragma unroll
+                    for (int ks = 0; ks < D / 8; ++ks) {
+                        const uint64_t bd = tc::smem_desc(bad + ks * 2 * tc::kmajor_lbo(), tc::kmajor_lbo(), tc::kmajor_sbo(D));
+                        tc::mma_tf32_tmem_a(tmem + (uint32_t)(b * N), tmem + (uint32_t)(ACOL + ks * 8), bd, idesc, ks > 0);
+                    }
+                    tc::mma_commit(&mma_done[b]);
+                }
+                __syncwarp();
+                ++t_prod;
+                if (k % ntiles == ntiles - 1) ++s_prod;
             }
+            cp_async_wait_all();
         } else if (warp <= 4) {
             // ================= epilogue: TMEM lane quarter q = warp % 4
             const int q = warp & 3;
             for (int st = 0; st < nstrips && ok; ++st) {
                 const int row = st * M + 32 * q + lane;  // 0-based row of the pair
-                const float4 ri = __ldg(rrec + (row < n ? row : n - 1));
+                const int rowc = row < n ? row : n - 1;
+                const float4 ri = __ldg(rrec + rowc);
                 const float na = ri.z, ti = ri.x;
+                {   // this strip's A: every MMA of the previous strip has completed
+                    // (this warp waited for each of them), so TMEM columns ACOL.. are free
+                    const float4* src = reinterpret_cast<const float4*>(rvals + (int64_t)rowc * D);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        float v[32];
+#pragma unroll
+                        for (int u = 0; u < 8; ++u) {
+                            const float4 f = __ldg(src + h * 8 + u);
+                            v[4 * u] = f.x;
+                            v[4 * u + 1] = f.y;
+                            v[4 * u + 2] = f.z;
+                            v[4 * u + 3] = f.w;
+                        }
+                        tc::tmem_st32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(ACOL + 32 * h), v);
+                    }
+                    tc::tmem_wait_st();
+                    tc::fence_before_sync();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(a_ready);
+                    ++s_epi;
+                }
                 for (int tt = 0; tt < ntiles; ++tt, ++t_epi) {
                     const int b = (int)(t_epi % NB), cb = (int)(t_epi % NC);
                     bool w2 = xwait(&mma_done[b], (uint32_t)((t_epi / NB) & 1), a.sc);
@@ -286,36 +338,58 @@ __global__ void __launch_bounds__(x64::THREADS) xterm_pairs_kernel(PairsArgs<flo
                 float diagD = (first && lane == 0) ? 0.f : INF, diagC = 0.f;
                 float botD = INF, botC = 0.f;
                 const long long t0 = t_dp;
+                const int cb0 = (int)(t0 % NC);  // ring slot of this strip's tile 0
                 int released = 0;  // tiles of this strip handed back
                 const int steps = m + lanes_used - 1;
+                // pipelined like the staged engine: step s prefetches the costs,
+                // deletion cost and boundary entry of its next column
+                int cbl = cb0;  // ring slot of this lane's next (prefetched) column
+                float4 c4n = make_float4(0.f, 0.f, 0.f, 0.f);
+                float delbn = 0.f;
+                float2 bndn = make_float2(0.f, 0.f);
+                auto prefetch = [&](int jn) {
+                    if (jn >= 2 && jn <= m && ((jn - 1) & (N - 1)) == 0) cbl = (cbl + 1 == NC) ? 0 : cbl + 1;
+                    const int jc = jn < 1 ? 1 : (jn > m ? m : jn);
+                    const int cb = (jn < 1) ? cb0 : cbl;
+                    c4n = *reinterpret_cast<const float4*>(sC + ((size_t)cb * N + ((jc - 1) & (N - 1))) * M + lane * R);
+                    delbn = __ldg(&crec[jc - 1].y);
+                    bndn = sRow[jc - 1];
+                };
+                {   // tile 0 must be in before the first prefetch
+                    const bool w2 = xwait(&cost_full[cb0], (uint32_t)((t0 / NC) & 1), a.sc);
+                    if (!__all_sync(kFull, w2)) ok = false;
+                }
+                if (ok) prefetch(1 - lane);
                 int j = 1 - lane;
-                for (int s = 0; s < steps; ++s, ++j) {
-                    if ((s & (N - 1)) == 0 && (s >> 4) < ntiles) {
-                        const long long tt = t0 + (s >> 4);  // tile lane 0 enters now
-                        const bool w2 = xwait(&cost_full[tt % NC], (uint32_t)((tt / NC) & 1), a.sc);
+                for (int s = 0; s < steps && ok; ++s, ++j) {
+                    const float4 c4 = c4n;
+                    const float delb = delbn;
+                    const float2 bnd = bndn;
+                    // the prefetch below reads lane 0's column s+2: enter its tile now
+                    if (((s + 1) & (N - 1)) == 0 && ((s + 1) >> 4) < ntiles) {
+                        const int k = (s + 1) >> 4;
+                        const long long tt = t0 + k;
+                        const bool w2 = xwait(&cost_full[(cb0 + k) % NC], (uint32_t)((tt / NC) & 1), a.sc);
                         if (!__all_sync(kFull, w2)) { ok = false; break; }
                     }
-                    // lane 31 has left tile k once it passed column 16(k+1)
+                    // lane 31 read tile k for the last time at step 16k + 45
                     if (s >= 31 + N && ((s - 31) & (N - 1)) == 0) {
                         const int k = (s - 31) / N - 1;
                         if (k == released && k < ntiles) {
                             __syncwarp();
-                            if (lane == 0) tc::mbar_arrive(&cost_empty[(t0 + k) % NC]);
+                            if (lane == 0) tc::mbar_arrive(&cost_empty[(cb0 + k) % NC]);
                             ++released;
                         }
                     }
+                    prefetch(j + 1);
                     float upD = __shfl_up_sync(kFull, botD, 1);
                     float upC = __shfl_up_sync(kFull, botC, 1);
-                    if (j >= 1 && j <= m) {
-                        const int k = (j - 1) >> 4, col = (j - 1) & (N - 1);
-                        const int cb = (int)((t0 + k) % NC);
-                        const float4 c4 = *reinterpret_cast<const float4*>(sC + ((size_t)cb * N + col) * M + lane * R);
-                        const float delb = __ldg(&crec[j - 1].y);
-                        const float2 bnd = sRow[j - 1];
-                        if (lane == 0) {
-                            upD = first ? INF : bnd.x;
-                            upC = first ? 0.f : bnd.y;
-                        }
+                    // branch-free step (see the staged engine): a lane before
+                    // column 1 sees an infinite row above and keeps its state
+                    upD = lane == 0 ? (first ? INF : bnd.x) : upD;
+                    upC = lane == 0 ? (first ? 0.f : bnd.y) : upC;
+                    upD = j < 1 ? INF : upD;
+                    {
                         const float cc[R] = {c4.x, c4.y, c4.z, c4.w};
                         float tb_[R], tm_[R];
 #pragma unroll
@@ -336,7 +410,7 @@ __global__ void __launch_bounds__(x64::THREADS) xterm_pairs_kernel(PairsArgs<flo
                         diagC = upC;
                         botD = Dl[R - 1];
                         botC = cp[R - 1];
-                        if (!last && lane == 31) sRow[j - 1] = make_float2(botD, botC);
+                        if (!last && lane == 31 && j >= 1 && j <= m) sRow[j - 1] = make_float2(botD, botC);
                         if (j == m) {
                             const int rr = n - r0 - lane * R;
 #pragma unroll
@@ -353,7 +427,7 @@ __global__ void __launch_bounds__(x64::THREADS) xterm_pairs_kernel(PairsArgs<flo
                 // hand back the tiles not yet released
                 __syncwarp();
                 for (int k = released; k < ntiles; ++k)
-                    if (lane == 0) tc::mbar_arrive(&cost_empty[(t0 + k) % NC]);
+                    if (lane == 0) tc::mbar_arrive(&cost_empty[(cb0 + k) % NC]);
                 t_dp = t0 + ntiles;
             }
         }
@@ -362,6 +436,7 @@ __global__ void __launch_bounds__(x64::THREADS) xterm_pairs_kernel(PairsArgs<flo
     }
     // drain: the producer's last MMAs must finish before TMEM is freed
     // (bounded by the same timeout as every other wait)
+    (void)s_epi;
     if (warp == 0 && t_prod > 0) {
         const unsigned long long t0 = globaltimer();
         while (!tc::mbar_try_wait(&mma_done[(t_prod - 1) % NB], (uint32_t)(((t_prod - 1) / NB) & 1)) &&
@@ -371,7 +446,7 @@ __global__ void __launch_bounds__(x64::THREADS) xterm_pairs_kernel(PairsArgs<flo
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    if (warp == 0) tc::tmem_dealloc(tmem, 32);
+    if (warp == 0) tc::tmem_dealloc(tmem, TMEM_COLS);
 }
 
 cudaError_t launch_xrecords(const RecordsArgs<float>& a, cudaStream_t st) {
@@ -383,9 +458,19 @@ cudaError_t launch_xrecords(const RecordsArgs<float>& a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
+// Opt in to the shared memory the kernel needs and ask for the largest
+// shared-memory carve-out, so that three blocks fit on one SM.
+static cudaError_t xterm_attributes() {
+    cudaError_t e = cudaFuncSetAttribute(xterm_pairs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, x64::SMEM);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(xterm_pairs_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
+    return e;
+}
+
 cudaError_t launch_xterm_pairs(const PairsArgs<float>& a, int blocks, cudaStream_t st) {
     if (a.npairs <= 0) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(xterm_pairs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, x64::SMEM);
+    cudaError_t e = xterm_attributes();
     if (e != cudaSuccess) return e;
     (void)cudaGetLastError();
     xterm_pairs_kernel<<<blocks, x64::THREADS, x64::SMEM, st>>>(a);
@@ -393,18 +478,52 @@ cudaError_t launch_xterm_pairs(const PairsArgs<float>& a, int blocks, cudaStream
 }
 
 int xterm_blocks_per_sm() {
-    if (cudaFuncSetAttribute(xterm_pairs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, x64::SMEM) != cudaSuccess) {
-        (void)cudaGetLastError();
-        return 0;
-    }
+    cudaError_t e = xterm_attributes();
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, xterm_pairs_kernel, x64::THREADS, x64::SMEM) != cudaSuccess) {
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, xterm_pairs_kernel, x64::THREADS, x64::SMEM);
+    if (e != cudaSuccess) {
         (void)cudaGetLastError();
-        return 0;
+        return -(int)e;  // negative: the CUDA error code, for diagnostics
     }
     return nb;
 }
 
 int xterm_max_cols() { return x64::MAXCOL; }
+
+// Blocks per SM allowed by shared memory (1 KB reserved per block), tensor
+// memory columns and registers.
+int xterm_resident_blocks() {
+    cudaFuncAttributes fa{};
+    int dev = 0, smem_sm = 0, regs_sm = 0;
+    if (xterm_attributes() != cudaSuccess || cudaFuncGetAttributes(&fa, xterm_pairs_kernel) != cudaSuccess ||
+        cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 1;
+    }
+    const int by_smem = smem_sm / (x64::SMEM + (int)fa.sharedSizeBytes + 1024);
+    const int regs_warp = ((fa.numRegs * 32 + 255) / 256) * 256;
+    const int by_regs = regs_sm / (regs_warp * (x64::THREADS / 32));
+    const int by_tmem = 512 / x64::TMEM_COLS;
+    int nb = by_smem < by_regs ? by_smem : by_regs;
+    nb = nb < by_tmem ? nb : by_tmem;
+    return nb > 0 ? nb : 1;
+}
+
+// "regs R static S dyn D smem/SM X": what bounds the blocks per SM.
+void xterm_resources(char* buf, int len) {
+    cudaFuncAttributes fa{};
+    int dev = 0, smem_sm = 0, smem_blk = 0;
+    (void)xterm_attributes();
+    cudaFuncGetAttributes(&fa, xterm_pairs_kernel);
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    cudaDeviceGetAttribute(&smem_blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    (void)cudaGetLastError();
+    snprintf(buf, len, "regs %d static %zu dyn %d max_dyn %d smem/SM %d smem/block %d", fa.numRegs,
+             fa.sharedSizeBytes, x64::SMEM, fa.maxDynamicSharedSizeBytes, smem_sm, smem_blk);
+}
 
 }  // namespace twed
