@@ -234,6 +234,130 @@ twed_status_t twed_allpairs_host_f32(twed_handle_t handle, const float* a_vals,
                                      const int64_t* b_offs, int64_t nb, int dim, float nu,
                                      float lambda, int p, float* out);
 
+/* ---- learned k-NN candidate filter ---------------------------------------
+ * The paper has no learned component; this is a filter in front of its exact
+ * batch mode.  A 1-D convolutional encoder maps a series to e in R^32,
+ * e = (psi in R^31, z), trained so that the additive model
+ *     |psi_a - psi_b|^2 + z_a + z_b   approximates   TWED(a, b) / sigma
+ * on pairs whose TWED the library computes exactly (twed_batch_f32).  A query
+ * takes the n_candidates database series with the smallest model value (an
+ * L2 search: database vectors (psi, sqrt(z - z_min)) against the query vector
+ * (psi, 0)), re-ranks them by exact TWED and returns the k best.
+ *
+ * Encoder (all FP32): per point the inputs a_i (dim values), t_i and the
+ * delete cost dA(i) = d(a_i, a_{i-1}) + nu|t_i - t_{i-1}| + lambda (a_0 = 0,
+ * t_0 = 0), each standardised by the database's per-channel mean and
+ * standard deviation; three convolutions of 64 channels, 5 taps, zero 'same'
+ * padding and ReLU; the sum over time divided by the database's mean length
+ * (a mean pool weighted by length); a linear map 64 -> 32.
+ * Flat parameter layout: W1[64][dim+2][5], b1[64], W2[64][64][5], b2[64],
+ * W3[64][64][5], b3[64], Wl[32][64], bl[32]; conv y[t][o] = b[o] +
+ * sum_k sum_c W[o][c][k] x[t+k-2][c].  dim must be <= 14.
+ *
+ * Training: groups of `group_size` distinct database series are drawn (seeded
+ * splitmix64 shuffles); every pair inside a group is labelled with exact
+ * TWED, so ~train_pairs labels come from group_size * train_pairs /
+ * (group_size (group_size-1) / 2) series.  sigma = mean label.  Each Adam
+ * step (beta 0.9 / 0.999, eps 1e-8, cosine-decayed learning rate) minimises
+ * the mean squared error of the model over the pairs of `groups_per_step`
+ * groups.  Then every database series is embedded. */
+typedef struct twed_knn_s* twed_knn_t;
+typedef struct {
+    int group_size;       /* series per labelled group, 2..64 (default 32) */
+    int groups_per_step;  /* groups per Adam step (default 32) */
+    int epochs;           /* passes over the labelled groups (default 40) */
+    int64_t train_pairs;  /* labelled pairs (default 1,000,000) */
+    float lr;             /* peak learning rate (default 2e-3) */
+    uint64_t seed;        /* group sampling and weight initialisation (default 1) */
+} twed_knn_config_t;
+
+typedef struct {
+    double sigma;          /* label scale (mean training TWED) */
+    double mean_len;       /* mean database series length (pool divisor) */
+    double first_loss;     /* mean loss of the first epoch */
+    double last_loss;      /* mean loss of the last epoch */
+    int64_t label_pairs;   /* pairs labelled with exact TWED */
+    int64_t label_cells;   /* interior cells of those pairs */
+    int64_t steps;         /* Adam steps taken */
+    double label_ms;       /* wall time of labelling (exact TWED) */
+    double train_ms;       /* wall time of the Adam steps */
+    double embed_ms;       /* wall time of embedding the database */
+} twed_knn_stats_t;
+
+void twed_knn_config_default(twed_knn_config_t* cfg);
+/* db: device set (offs_host required) owned by the caller; it must stay valid
+ * and unchanged for the index's lifetime.  cfg NULL = defaults.  Allocates
+ * the index's device memory; trains nothing yet. */
+twed_status_t twed_knn_create(twed_handle_t handle, const twed_set_f32_t* db, int dim, float nu,
+                              float lambda, int p, const twed_knn_config_t* cfg, twed_knn_t* knn);
+/* Labels, trains and embeds the database (blocking; uses the handle's
+ * stream).  May be called again to retrain from a fresh initialisation. */
+twed_status_t twed_knn_train(twed_knn_t knn);
+/* Queries (device set, offs_host required): d_idx[q*k + r] (device int64)
+ * and d_dist[q*k + r] (device float, exact FP32 TWED) receive the k
+ * best of the n_candidates filtered database series, ascending (ties by
+ * smaller database index).  1 <= k <= n_candidates <= min(ndb, 4096).
+ * Enqueued on `stream`; the call waits only for its own host-side setup. */
+twed_status_t twed_knn_search(twed_knn_t knn, const twed_set_f32_t* queries, int k,
+                              int n_candidates, int64_t* d_idx, float* d_dist, void* stream);
+/* Exact batched k-NN (the reference the filter is judged against): the full
+ * queries x database TWED matrix through an all-pairs plan, then the k
+ * smallest per query (ties by smaller index).  1 <= k <= min(ndb, 4096).
+ * Blocking. */
+twed_status_t twed_knn_exact(twed_knn_t knn, const twed_set_f32_t* queries, int k,
+                             int64_t* d_idx, float* d_dist, void* stream);
+twed_status_t twed_knn_get_stats(twed_knn_t knn, twed_knn_stats_t* out);
+/* Parameters (host float[twed_encoder_param_count(dim)]). */
+twed_status_t twed_knn_get_params(twed_knn_t knn, float* out, int64_t n);
+/* Replace the parameters and re-embed the database (blocking). */
+twed_status_t twed_knn_set_params(twed_knn_t knn, const float* in, int64_t n);
+/* Database embeddings e (device float[ndb][32]) after training. */
+twed_status_t twed_knn_get_embeddings(twed_knn_t knn, float* d_out, void* stream);
+void twed_knn_destroy(twed_knn_t knn);
+
+/* ---- encoder building blocks (blocking; each allocates and frees its own
+ * scratch).  They expose the kernels the index uses so each can be checked
+ * on its own. */
+int64_t twed_encoder_param_count(int dim);
+/* d_mu[dim+2], d_sd[dim+2] (device): per-channel mean and population
+ * standard deviation of the encoder inputs over every point of `set`
+ * (a channel with zero spread gets 1). */
+twed_status_t twed_encoder_stats_f32(twed_handle_t handle, const twed_set_f32_t* set, int dim,
+                                     float nu, float lambda, int p, float* d_mu, float* d_sd);
+/* d_emb[set->n][32] (device): embeddings of every series of `set`. */
+twed_status_t twed_encoder_forward_f32(twed_handle_t handle, const twed_set_f32_t* set, int dim,
+                                       float nu, float lambda, int p, const float* d_params,
+                                       const float* d_mu, const float* d_sd, float mean_len,
+                                       float* d_emb);
+/* Loss and parameter gradient over groups of series of `set`:
+ * groups[g*group_size + a] (host int64) index `set`; d_labels[g*npg + q]
+ * (device) is the label of the q-th pair (a < b, row-major) of group g,
+ * npg = group_size (group_size-1) / 2.  loss = (1/npairs) sum (model -
+ * label * inv_sigma)^2; d_grad (device, param_count floats) receives its
+ * gradient and d_loss[0] (device) the loss. */
+twed_status_t twed_encoder_loss_grad_f32(twed_handle_t handle, const twed_set_f32_t* set,
+                                         int dim, float nu, float lambda, int p,
+                                         const float* d_params, const float* d_mu,
+                                         const float* d_sd, float mean_len,
+                                         const int64_t* groups, int64_t ngroups, int group_size,
+                                         const float* d_labels, float inv_sigma, float* d_grad,
+                                         float* d_loss);
+/* One Adam step (step >= 1) on device arrays of n floats. */
+twed_status_t twed_adam_f32(twed_handle_t handle, float* d_theta, const float* d_grad, float* d_m,
+                            float* d_v, int64_t n, int64_t step, float lr, float beta1,
+                            float beta2, float eps);
+/* Candidate search over embeddings (device float[..][32]): for each query,
+ * the k database rows with the smallest |(psi_q, 0) - (psi_x, sqrt(z_x -
+ * z_min))|^2, ascending (ties by smaller index); d_idx[nq*k], d_val[nq*k]. */
+twed_status_t twed_embed_search_f32(twed_handle_t handle, const float* d_db_emb, int64_t ndb,
+                                    const float* d_q_emb, int64_t nq, int k, int64_t* d_idx,
+                                    float* d_val);
+/* Row-wise k smallest of d_D[rows][ld] over the first `cols` columns,
+ * ascending, ties by smaller column; k <= 4096, cols < 2^31. */
+twed_status_t twed_topk_rows_f32(twed_handle_t handle, const float* d_D, int64_t rows,
+                                 int64_t cols, int64_t ld, int k, int64_t* d_idx, float* d_val,
+                                 void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,6 +1,6 @@
 """Builds libtwed.so (the CUDA library behind include/twed.h) for sm_103a.
 
-Three translation units are compiled in parallel with nvcc and linked into
+The translation units are compiled in parallel with nvcc and linked into
 ``paper_2007_16135_gb300/_build/libtwed.so``.  Cross-compiles without a GPU.
 """
 from __future__ import annotations
@@ -14,7 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libtwed.so")
-SOURCES = ["api.cu", "kernels_f32.cu", "kernels_f64.cu", "noalloc.cu", "xterm.cu"]
+SOURCES = ["api.cu", "kernels_f32.cu", "kernels_f64.cu", "noalloc.cu", "xterm.cu", "encoder.cu",
+           "knn.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ARCH + ["-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
                   "-diag-suppress", "177"]

@@ -413,6 +413,18 @@ extern "C" const char* twed_last_error(twed_handle_t h) {
 
 extern "C" const char* twed_version(void) { return TWED_VERSION_STR; }
 
+// Internal accessors for the other translation units (handle.h).
+namespace twed {
+namespace detail {
+twed_status_t set_error(twed_handle_t h, twed_status_t st, const char* msg) {
+    if (h) h->last_error = msg;
+    return st;
+}
+int handle_sms(twed_handle_t h) { return h ? h->sms : 0; }
+int handle_device(twed_handle_t h) { return h ? h->device : 0; }
+}  // namespace detail
+}  // namespace twed
+
 extern "C" twed_status_t twed_sync_status(twed_handle_t h, void* stream) {
     if (!h) return TWED_ERR_INVALID_ARG;
     TWED_CUDA(h, cudaStreamSynchronize((cudaStream_t)stream));

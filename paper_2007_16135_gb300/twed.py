@@ -38,6 +38,11 @@ EXPORTS = (
     "twed_plan_cells", "twed_plan_pairs", "twed_plan_kernel_ms", "twed_plan_describe",
     "twed_plan_destroy",
     "twed_allpairs_host_f32",
+    "twed_knn_config_default", "twed_knn_create", "twed_knn_train", "twed_knn_search",
+    "twed_knn_exact", "twed_knn_get_stats", "twed_knn_get_params", "twed_knn_set_params",
+    "twed_knn_get_embeddings", "twed_knn_destroy",
+    "twed_encoder_param_count", "twed_encoder_stats_f32", "twed_encoder_forward_f32",
+    "twed_encoder_loss_grad_f32", "twed_adam_f32", "twed_embed_search_f32", "twed_topk_rows_f32",
 )
 
 
@@ -109,6 +114,24 @@ def load(path: str | None = None):
             "twed_plan_describe": (ctypes.c_char_p, [P]),
             "twed_plan_destroy": (None, [P]),
             "twed_allpairs_host_f32": (ci, [P, P, P, P, i64, P, P, P, i64, ci, f, f, ci, P]),
+            "twed_knn_config_default": (None, [P]),
+            "twed_knn_create": (ci, [P, P, ci, f, f, ci, P, P]),
+            "twed_knn_train": (ci, [P]),
+            "twed_knn_search": (ci, [P, P, ci, ci, P, P, P]),
+            "twed_knn_exact": (ci, [P, P, ci, P, P, P]),
+            "twed_knn_get_stats": (ci, [P, P]),
+            "twed_knn_get_params": (ci, [P, P, i64]),
+            "twed_knn_set_params": (ci, [P, P, i64]),
+            "twed_knn_get_embeddings": (ci, [P, P, P]),
+            "twed_knn_destroy": (None, [P]),
+            "twed_encoder_param_count": (i64, [ci]),
+            "twed_encoder_stats_f32": (ci, [P, P, ci, f, f, ci, P, P]),
+            "twed_encoder_forward_f32": (ci, [P, P, ci, f, f, ci, P, P, P, f, P]),
+            "twed_encoder_loss_grad_f32": (ci, [P, P, ci, f, f, ci, P, P, P, f, P, i64, ci, P, f,
+                                                P, P]),
+            "twed_adam_f32": (ci, [P, P, P, P, P, i64, i64, f, f, f, f]),
+            "twed_embed_search_f32": (ci, [P, P, i64, P, i64, ci, P, P]),
+            "twed_topk_rows_f32": (ci, [P, P, i64, i64, i64, ci, P, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -413,3 +436,188 @@ def twed_allpairs_host_f32(a_vals, a_ts, a_offs, b=None, nu=1.0, lam=1.0, p=2,
                                          ptr(bt), ptr(bo), nb if b is not None else 0,
                                          av.shape[1], float(nu), float(lam), p, _np_ptr(out)))
     return out
+
+
+# ------------------------------------------------------- learned k-NN filter
+class KnnConfig(ctypes.Structure):
+    _fields_ = [("group_size", ctypes.c_int), ("groups_per_step", ctypes.c_int),
+                ("epochs", ctypes.c_int), ("train_pairs", ctypes.c_int64), ("lr", ctypes.c_float),
+                ("seed", ctypes.c_uint64)]
+
+
+class KnnStats(ctypes.Structure):
+    _fields_ = [("sigma", ctypes.c_double), ("mean_len", ctypes.c_double),
+                ("first_loss", ctypes.c_double), ("last_loss", ctypes.c_double),
+                ("label_pairs", ctypes.c_int64), ("label_cells", ctypes.c_int64),
+                ("steps", ctypes.c_int64), ("label_ms", ctypes.c_double),
+                ("train_ms", ctypes.c_double), ("embed_ms", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+def knn_config(**kw) -> KnnConfig:
+    c = KnnConfig()
+    load().twed_knn_config_default(ctypes.byref(c))
+    for k, v in kw.items():
+        setattr(c, k, v)
+    return c
+
+
+def encoder_param_count(dim: int) -> int:
+    return int(load().twed_encoder_param_count(dim))
+
+
+class KnnIndex:
+    """twed_knn_create / train / search / exact / destroy over a float32
+    DeviceSet database (kept alive by the index)."""
+
+    def __init__(self, db: DeviceSet, nu, lam, p=2, config: KnnConfig | None = None,
+                 handle: Handle | None = None):
+        self.handle = handle or default_handle()
+        self.db = db
+        self._sdb = db.cstruct()
+        k = ctypes.c_void_p()
+        self.handle.check(self.handle.lib.twed_knn_create(
+            self.handle.h, ctypes.byref(self._sdb), db.dim, float(nu), float(lam), p,
+            ctypes.byref(config) if config is not None else None, ctypes.byref(k)))
+        self.k = k
+        self.dim = db.dim
+
+    def train(self):
+        self.handle.check(self.handle.lib.twed_knn_train(self.k))
+        return self.stats()
+
+    def stats(self) -> dict:
+        st = KnnStats()
+        self.handle.check(self.handle.lib.twed_knn_get_stats(self.k, ctypes.byref(st)))
+        return st.as_dict()
+
+    def params(self) -> np.ndarray:
+        n = encoder_param_count(self.dim)
+        out = np.empty(n, dtype=np.float32)
+        self.handle.check(self.handle.lib.twed_knn_get_params(self.k, _np_ptr(out), n))
+        return out
+
+    def set_params(self, w):
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        self.handle.check(self.handle.lib.twed_knn_set_params(self.k, _np_ptr(w), w.size))
+
+    def embeddings(self, stream=None):
+        import torch
+        out = torch.empty((self.db.n, 32), dtype=torch.float32, device=self.db.vals.device)
+        self.handle.check(self.handle.lib.twed_knn_get_embeddings(self.k, _t_ptr(out),
+                                                                  _stream_ptr(stream)))
+        return out
+
+    def _outputs(self, nq, k):
+        import torch
+        dev = self.db.vals.device
+        return (torch.empty((nq, k), dtype=torch.int64, device=dev),
+                torch.empty((nq, k), dtype=torch.float32, device=dev))
+
+    def search(self, queries: DeviceSet, k=10, n_candidates=200, stream=None, out=None):
+        idx, dist = out if out is not None else self._outputs(queries.n, k)
+        sq = queries.cstruct()
+        self.handle.check(self.handle.lib.twed_knn_search(self.k, ctypes.byref(sq), k,
+                                                          n_candidates, _t_ptr(idx),
+                                                          _t_ptr(dist), _stream_ptr(stream)))
+        return idx, dist
+
+    def exact(self, queries: DeviceSet, k=10, stream=None, out=None):
+        idx, dist = out if out is not None else self._outputs(queries.n, k)
+        sq = queries.cstruct()
+        self.handle.check(self.handle.lib.twed_knn_exact(self.k, ctypes.byref(sq), k, _t_ptr(idx),
+                                                         _t_ptr(dist), _stream_ptr(stream)))
+        return idx, dist
+
+    def close(self):
+        if getattr(self, "k", None):
+            self.handle.lib.twed_knn_destroy(self.k)
+            self.k = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+twed_knn_create = KnnIndex
+
+
+def encoder_stats(S: DeviceSet, nu, lam, p=2, handle: Handle | None = None):
+    import torch
+    h = handle or default_handle()
+    mu = torch.empty(S.dim + 2, dtype=torch.float32, device=S.vals.device)
+    sd = torch.empty_like(mu)
+    s = S.cstruct()
+    h.check(h.lib.twed_encoder_stats_f32(h.h, ctypes.byref(s), S.dim, float(nu), float(lam), p,
+                                         _t_ptr(mu), _t_ptr(sd)))
+    return mu, sd
+
+
+def encoder_forward(S: DeviceSet, nu, lam, p, params, mu, sd, mean_len,
+                    handle: Handle | None = None):
+    import torch
+    h = handle or default_handle()
+    out = torch.empty((S.n, 32), dtype=torch.float32, device=S.vals.device)
+    s = S.cstruct()
+    h.check(h.lib.twed_encoder_forward_f32(h.h, ctypes.byref(s), S.dim, float(nu), float(lam), p,
+                                           _t_ptr(params), _t_ptr(mu), _t_ptr(sd),
+                                           float(mean_len), _t_ptr(out)))
+    return out
+
+
+def encoder_loss_grad(S: DeviceSet, nu, lam, p, params, mu, sd, mean_len, groups, labels,
+                      inv_sigma, handle: Handle | None = None):
+    """groups: host int array [ngroups, group_size]; labels: device float32
+    [ngroups, npg].  Returns (loss, grad) on the device."""
+    import torch
+    h = handle or default_handle()
+    groups = np.ascontiguousarray(groups, dtype=np.int64)
+    ng, gs = groups.shape
+    grad = torch.empty(encoder_param_count(S.dim), dtype=torch.float32, device=S.vals.device)
+    loss = torch.empty(1, dtype=torch.float32, device=S.vals.device)
+    s = S.cstruct()
+    labels = labels.contiguous()
+    h.check(h.lib.twed_encoder_loss_grad_f32(h.h, ctypes.byref(s), S.dim, float(nu), float(lam), p,
+                                             _t_ptr(params), _t_ptr(mu), _t_ptr(sd),
+                                             float(mean_len), _np_ptr(groups), ng, gs,
+                                             _t_ptr(labels), float(inv_sigma), _t_ptr(grad),
+                                             _t_ptr(loss)))
+    return loss, grad
+
+
+def adam_step(theta, grad, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8,
+              handle: Handle | None = None):
+    h = handle or default_handle()
+    h.check(h.lib.twed_adam_f32(h.h, _t_ptr(theta), _t_ptr(grad), _t_ptr(m), _t_ptr(v),
+                                theta.numel(), int(step), float(lr), float(beta1), float(beta2),
+                                float(eps)))
+
+
+def embed_search(db_emb, q_emb, k, handle: Handle | None = None):
+    import torch
+    h = handle or default_handle()
+    db_emb = db_emb.contiguous()
+    q_emb = q_emb.contiguous()
+    nq = q_emb.shape[0]
+    idx = torch.empty((nq, k), dtype=torch.int64, device=db_emb.device)
+    val = torch.empty((nq, k), dtype=torch.float32, device=db_emb.device)
+    h.check(h.lib.twed_embed_search_f32(h.h, _t_ptr(db_emb), db_emb.shape[0], _t_ptr(q_emb), nq, k,
+                                        _t_ptr(idx), _t_ptr(val)))
+    return idx, val
+
+
+def topk_rows(D, k, cols=None, stream=None, handle: Handle | None = None):
+    """k smallest per row of a float32 device matrix (ties by smaller column)."""
+    import torch
+    h = handle or default_handle()
+    rows, ld = D.shape
+    cols = ld if cols is None else cols
+    idx = torch.empty((rows, k), dtype=torch.int64, device=D.device)
+    val = torch.empty((rows, k), dtype=torch.float32, device=D.device)
+    h.check(h.lib.twed_topk_rows_f32(h.h, _t_ptr(D), rows, cols, ld, k, _t_ptr(idx), _t_ptr(val),
+                                     _stream_ptr(stream)))
+    return idx, val
