@@ -5,7 +5,10 @@ Default workload: all i<j pairs of 4096 dim-8 series with lengths U[64, 2048]
 (three-sinusoid mixtures plus noise, t_i = i, nu = lambda = 0.5, p = 2, FP32),
 8,386,560 pairs per step, one plan execute (one CUDA-graph launch) per step.
 Other workloads: --workload w2 (one 3-D pair, n = m = 1e6 FP32, or 1e5 FP64
-with --dtype f64), w1 (one 1-D FP64 pair, n = m = 1000).
+with --dtype f64), w1 (one 1-D FP64 pair, n = m = 1000), w4 (2048 x 2048
+dim-64 block, tensor-core cross term), w5 (learned k-NN: 1e5-series database,
+1000 queries; queries/s at recall@10 >= 0.99 against the exact batched path).
+The default run also appends a "knn" object with the w5 result.
 
 `python bench.py --gpus N --steps K --warmup W` prints one JSON line.  Under
 torchrun each rank runs its own instance of the workload (independent
@@ -41,7 +44,12 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["w3", "w4", "w2", "w1"], default="w3")
+    ap.add_argument("--workload", choices=["w3", "w4", "w2", "w1", "w5"], default="w3")
+    ap.add_argument("--no-knn", action="store_true", help="w3: skip the appended w5 result")
+    ap.add_argument("--knn-epochs", type=int, default=40)
+    ap.add_argument("--knn-pairs", type=int, default=1_000_000)
+    ap.add_argument("--knn-db", type=int, default=100_000)
+    ap.add_argument("--knn-queries", type=int, default=1000)
     ap.add_argument("--xterm", choices=["tf32", "off"], default="tf32",
                     help="w4: cross term on the tensor cores (tf32) or CUDA cores (off)")
     ap.add_argument("--dtype", choices=["f32", "f64"], default=None)
@@ -374,6 +382,157 @@ def bench_pair(args, rank, world, dev, workload):
     return res
 
 
+def bench_knn(args, rank, world, dev, steps, warmup):
+    """Learned k-NN (w5): train the filter on exact labels, time the exact
+    batched k-NN (the ground truth), pick the smallest candidate count whose
+    recall@10 reaches 0.99, then time searches of all queries at that count."""
+    import torch
+
+    from paper_2007_16135_gb300 import twed
+    from paper_2007_16135_gb300 import workloads as W
+
+    nu, lam, p, k = 1.0, 1.0, 2, 10
+    db = W.set_w5(args.knn_db, stream=1 if rank == 0 else 20 + rank).astype(np.float32)
+    qs = W.set_w5(args.knn_queries, stream=0 if rank == 0 else 10 + rank).astype(np.float32)
+    D = twed.DeviceSet.from_numpy(db.vals, db.ts, db.offs, torch.float32, device=dev)
+    Q = twed.DeviceSet.from_numpy(qs.vals, qs.ts, qs.offs, torch.float32, device=dev)
+    cfg = twed.knn_config(train_pairs=args.knn_pairs, epochs=args.knn_epochs)
+    index = twed.KnnIndex(D, nu, lam, p, config=cfg)
+    train = index.train()
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # exact batched k-NN: the full queries x database matrix, then top-k
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    ex_idx, ex_dist = index.exact(Q, k=k, stream=stream)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    exact_s = ev0.elapsed_time(ev1) / 1e3
+    exact_cells = int(qs.lengths.sum()) * int(db.lengths.sum())
+    kth = ex_dist.cpu().numpy()[:, k - 1]
+
+    def recall(dist):
+        d = dist.cpu().numpy()
+        return float(np.minimum((d <= kth[:, None]).sum(axis=1), k).mean() / k)
+
+    sweep, c_op = {}, None
+    for C in (200, 400, 800, 1600, 3200, 4096):
+        if C > db.n:
+            break
+        _, dist = index.search(Q, k=k, n_candidates=C, stream=stream)
+        sweep[C] = recall(dist)
+        if sweep[C] >= 0.99:
+            c_op = C
+            break
+    if c_op is None:
+        c_op = max(sweep)
+    out = index._outputs(qs.n, k)
+    for _ in range(warmup):
+        index.search(Q, k=k, n_candidates=c_op, stream=stream, out=out)
+    torch.cuda.synchronize()
+    barrier(world)
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(steps):
+            index.search(Q, k=k, n_candidates=c_op, stream=stream, out=out)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+    ms_step = max_over_ranks(ev0.elapsed_time(ev1), world, dev) / steps
+    phase_ms, rr_cells = index.search_profile()
+    rec_op = recall(out[1])
+    value = qs.n * world / (ms_step / 1e3)
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = float(measured_peaks().get("sm_max_mhz", FALLBACK_SM_MAX_MHZ))
+    peak = props.multi_processor_count * FP32_LANES_PER_SM * sm_max * 1e6
+    opc = ops_per_cell(4, p)
+    res = {"value": value, "unit": "queries/s", "ms_per_step": ms_step, "clocks": clk.summary(),
+           "dtype": "f32",
+           "knn": {"recall_at_10": rec_op, "n_candidates": c_op, "k": k,
+                   "recall_sweep": {str(c): r for c, r in sweep.items()},
+                   "exact_queries_per_s": qs.n / exact_s, "exact_s": exact_s,
+                   "exact_gcups": exact_cells / exact_s / 1e9,
+                   "speedup_vs_exact": value / world / (qs.n / exact_s),
+                   "phase_ms": {"embed": phase_ms[0], "candidates": phase_ms[1],
+                                "rerank": phase_ms[2], "select": phase_ms[3]},
+                   "rerank_cells": rr_cells, "rerank_gcups": rr_cells / (phase_ms[2] / 1e3) / 1e9,
+                   "train": {key: train[key] for key in ("sigma", "first_loss", "last_loss",
+                                                         "label_pairs", "label_cells", "steps",
+                                                         "label_ms", "train_ms", "embed_ms")}},
+           "roofline": {"bound": "alu", "achieved": rr_cells * opc / (phase_ms[2] / 1e3) / 1e12,
+                        "peak": peak / 1e12, "unit": "Top/s",
+                        "frac": rr_cells * opc / (phase_ms[2] / 1e3) / peak, "traffic": None,
+                        "ops_per_cell": opc, "kernel": "pairs_kernel<float,4,2,8> (exact re-rank)",
+                        "peak_basis": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} "
+                                      f"FP32 lanes x {sm_max:.0f} MHz (max SM clock)"},
+           # per search: query gather/transform/3 convs/pool, L2 + top-C, pairs +
+           # cells, records A/B + pairs kernel, top-k + gather
+           "gpu_launches": 15 * steps}
+    if not args.no_e2e:
+        pv = torch.from_numpy(np.ascontiguousarray(qs.vals)).pin_memory().numpy()
+        pt = torch.from_numpy(np.ascontiguousarray(qs.ts)).pin_memory().numpy()
+        po = np.ascontiguousarray(qs.offs)
+        hout = (torch.empty((qs.n, k), dtype=torch.int64).pin_memory().numpy(),
+                torch.empty((qs.n, k), dtype=torch.float32).pin_memory().numpy())
+        index.search_host(pv, pt, po, k=k, n_candidates=c_op, out=hout)
+        barrier(world)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            index.search_host(pv, pt, po, k=k, n_candidates=c_op, out=hout)
+        el = max_over_ranks((time.perf_counter() - t0) * 1e3, world, dev) / steps
+        res["e2e"] = {"value": qs.n * world / (el / 1e3), "unit": "queries/s",
+                      "h2d_bytes_per_step": int(pv.nbytes + pt.nbytes + po.nbytes),
+                      "d2h_bytes_per_step": int(hout[0].nbytes + hout[1].nbytes),
+                      "ms_per_step": el, "api": "twed_knn_search_host"}
+    if rank == 0 and not args.no_cpu:
+        import oracle
+        cores = os.cpu_count() or 1
+        q0v, q0t = qs.series(0)
+        one = W.pack([(q0v.astype(np.float64), q0t.astype(np.float64))])
+        db64 = db.astype(np.float64)
+        done, t0, chunk = 0, time.perf_counter(), 64 * cores
+        got = []
+        while done < db.n and time.perf_counter() - t0 < args.cpu_seconds:
+            ids = np.arange(done, min(db.n, done + chunk))
+            pr = np.stack([np.zeros_like(ids), ids], axis=1)
+            got.append(oracle.twed_pairs(one.as_tuple(), db64.as_tuple(), pr, nu, lam, p, nthreads=cores))
+            done += len(ids)
+        el = time.perf_counter() - t0
+        per_query = el * db.n / done
+        res["cpu_baseline"] = {"value": 1.0 / per_query, "unit": "queries/s", "cores": cores,
+                               "kind": "oracle",
+                               "sample": f"exact TWED of query 0 against {done} of {db.n} database "
+                                         f"series ({el:.1f} s, FP64 rolling-row oracle, threads over "
+                                         "pairs); queries/s extrapolated to the full database"}
+        # error of the GPU's FP32 distances for those pairs
+        ref = np.concatenate(got)
+        res["error_vs_oracle"] = {"note": "exact-path distances of query 0 vs the oracle",
+                                  **_exact_row_error(index, Q, db, ref, done)}
+    res["config"] = {"workload": f"w5 learned k-NN: database {db.n} series, {qs.n} queries, dim 4, "
+                                 "len U[128,512], random walks, t_i=i, nu=lambda=1, p=2, FP32; "
+                                 "encoder 3 x conv1d(64 ch, 5 taps) + length-weighted mean pool + "
+                                 f"linear 32 trained on {train['label_pairs']} exact GPU TWED pairs",
+                     "k": k, "n_candidates": c_op, "queries": qs.n, "database": db.n,
+                     "l2": "database values + records 0.9 GB > 126 MB L2",
+                     "parallelism": f"{world} independent replica(s)"}
+    index.close()
+    return res
+
+
+def _exact_row_error(index, Q, db, ref, done):
+    """Relative error of the exact path's FP32 TWED (query 0 vs the first
+    `done` database series) against the oracle values `ref`."""
+    import torch
+
+    from paper_2007_16135_gb300 import twed
+    pairs = torch.stack([torch.zeros(done, dtype=torch.int64), torch.arange(done)], 1).cuda()
+    got = twed.twed_batch(Q, index.db, pairs, 1.0, 1.0, 2).double().cpu().numpy()
+    rel = np.abs(got - ref) / np.maximum(np.abs(ref), 1e-300)
+    return {"max_rel": float(rel.max()), "mean_rel": float(rel.mean()), "pairs": int(done),
+            "bound": 1e-5}
+
+
 # ---------------------------------------------------------------- reference arm
 def bench_reference(args, rank, world):
     """The reference arm is the CPU oracle, timed on this host's cores."""
@@ -465,16 +624,26 @@ def main():
     twed.load()
     if args.workload in ("w3", "w4"):
         res = bench_plan(args, rank, world, dev, args.workload)
+        if args.workload == "w3" and not args.no_knn:
+            kn = bench_knn(args, rank, world, dev, steps=10, warmup=3)
+            res["knn"] = {"metric": "k-NN queries/s at recall@10>=0.99 vs exact batched",
+                          "value": kn["value"], "unit": kn["unit"],
+                          "ms_per_step": kn["ms_per_step"], **kn["knn"],
+                          "e2e": kn.get("e2e"), "cpu_baseline": kn.get("cpu_baseline"),
+                          "roofline": kn["roofline"], "clocks": kn["clocks"],
+                          "config": kn["config"]}
+    elif args.workload == "w5":
+        res = bench_knn(args, rank, world, dev, steps=args.steps, warmup=args.warmup)
     else:
         res = bench_pair(args, rank, world, dev, args.workload)
     if rank == 0:
-        line = {"metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world,
+        line = {"metric": METRIC, "value": res["value"], "unit": res.get("unit", UNIT), "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": res["ms_per_step"],
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": res.get("dtype", "f32"), "data": "synthetic (seeded generators)",
                 "config": res["config"]}
         for k in ("roofline", "tensor", "cpu_baseline", "e2e", "gpu_launches", "clocks",
-                  "error_vs_oracle", "kernel_ms", "plan", "cells_per_step", "result"):
+                  "error_vs_oracle", "kernel_ms", "plan", "cells_per_step", "result", "knn"):
             if k in res:
                 line[k] = res[k]
         print(json.dumps(line), flush=True)

@@ -306,6 +306,17 @@ twed_status_t twed_knn_search(twed_knn_t knn, const twed_set_f32_t* queries, int
  * Blocking. */
 twed_status_t twed_knn_exact(twed_knn_t knn, const twed_set_f32_t* queries, int k,
                              int64_t* d_idx, float* d_dist, void* stream);
+/* Host-memory queries, blocking: vals[offs[nq]][dim], ts[offs[nq]],
+ * offs[nq+1] (host); idx[nq*k], dist[nq*k] (host) receive the results.
+ * Copies in, searches on the index's own stream, copies out. */
+twed_status_t twed_knn_search_host(twed_knn_t knn, const float* vals, const float* ts,
+                                   const int64_t* offs, int64_t nq, int k, int n_candidates,
+                                   int64_t* idx, float* dist);
+/* Device time of the phases of the last twed_knn_search (waits for it):
+ * phase_ms[0] query embedding, [1] candidate search (L2 + top-C),
+ * [2] exact re-rank, [3] final top-k; *rerank_cells = interior cells the
+ * re-rank evaluated. */
+twed_status_t twed_knn_search_profile(twed_knn_t knn, double* phase_ms, int64_t* rerank_cells);
 twed_status_t twed_knn_get_stats(twed_knn_t knn, twed_knn_stats_t* out);
 /* Parameters (host float[twed_encoder_param_count(dim)]). */
 twed_status_t twed_knn_get_params(twed_knn_t knn, float* out, int64_t n);

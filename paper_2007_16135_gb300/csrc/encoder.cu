@@ -801,6 +801,19 @@ __global__ void make_pairs_kernel(const int64_t* __restrict__ cand, int64_t nq, 
     }
 }
 
+__global__ void __launch_bounds__(256)
+pair_cells_kernel(const int64_t* __restrict__ pairs, int64_t n, const int64_t* __restrict__ oa,
+                  const int64_t* __restrict__ ob, unsigned long long* __restrict__ out) {
+    unsigned long long acc = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t a = pairs[2 * i], b = pairs[2 * i + 1];
+        acc += (unsigned long long)((oa[a + 1] - oa[a]) * (ob[b + 1] - ob[b]));
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(out, acc);
+}
+
 __global__ void gather_cand_kernel(const int64_t* __restrict__ cand, const int64_t* __restrict__ pos,
                                    int64_t nq, int C, int k, int64_t* __restrict__ idx) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nq * k;
@@ -1016,6 +1029,16 @@ cudaError_t topk_rows(const float* D, int64_t rows, int64_t cols, int64_t ld, in
 cudaError_t make_pairs(const int64_t* cand, int64_t nq, int C, int64_t q0, int64_t* pairs,
                        cudaStream_t st) {
     make_pairs_kernel<<<grid_for(nq * C, 256), 256, 0, st>>>(cand, nq, C, q0, pairs);
+    return cudaGetLastError();
+}
+
+cudaError_t pair_cells(const int64_t* pairs, int64_t n, const int64_t* offs_a,
+                       const int64_t* offs_b, unsigned long long* out, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
+    if (n < 1) return cudaSuccess;
+    pair_cells_kernel<<<(int)std::min<int64_t>((n + 255) / 256, 1024), 256, 0, st>>>(pairs, n, offs_a,
+                                                                                   offs_b, out);
     return cudaGetLastError();
 }
 

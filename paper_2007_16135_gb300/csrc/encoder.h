@@ -102,6 +102,9 @@ cudaError_t topk_rows(const float* D, int64_t rows, int64_t cols, int64_t ld, in
 // pairs[(q*C + c)] = (q0 + q, cand[q*C + c]) for q < nq.
 cudaError_t make_pairs(const int64_t* cand, int64_t nq, int C, int64_t q0, int64_t* pairs,
                        cudaStream_t st);
+// out[0] = sum over pairs of len_a * len_b (interior cells), out zeroed here.
+cudaError_t pair_cells(const int64_t* pairs, int64_t n, const int64_t* offs_a,
+                       const int64_t* offs_b, unsigned long long* out, cudaStream_t st);
 // idx[q*k + r] = cand[q*C + pos[q*k + r]].
 cudaError_t gather_candidates(const int64_t* cand, const int64_t* pos, int64_t nq, int C, int k,
                               int64_t* idx, cudaStream_t st);

@@ -289,10 +289,19 @@ struct twed_knn_s {
     twed_knn_config_t cfg{};
     Encoder enc;
     DevBuf params, grad, m, v, mu, sd, stat_part, labels, lpairs, scalars, emb_db, svec_db, losses, sched;
-    DevBuf sbuf, cand, candval, qpairs, rr, pos, qemb;
+    DevBuf sbuf, cand, candval, qpairs, rr, pos, qemb, cells;
+    DevBuf hq_vals, hq_ts, hq_offs, hq_idx, hq_dist;  // staging of twed_knn_search_host
     double mean_len = 0.0;
     bool trained = false;
+    bool searched = false;
     twed_knn_stats_t stats{};
+    cudaEvent_t ev[5] = {};  // search phase boundaries
+    cudaStream_t host_stream = nullptr;
+    ~twed_knn_s() {
+        for (cudaEvent_t& e : ev)
+            if (e) cudaEventDestroy(e);
+        if (host_stream) cudaStreamDestroy(host_stream);
+    }
 };
 
 namespace {
@@ -393,6 +402,16 @@ extern "C" twed_status_t twed_knn_create(twed_handle_t h, const twed_set_f32_t* 
     alloc(k->scalars, sizeof(float) * 8);
     alloc(k->emb_db, sizeof(float) * db->n * EMB);
     alloc(k->svec_db, sizeof(float) * db->n * EMB);
+    alloc(k->cells, sizeof(unsigned long long));
+    for (cudaEvent_t& e : k->ev)
+        if (s == TWED_OK && cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            s = err(h, TWED_ERR_CUDA, "event creation");
+        }
+    if (s == TWED_OK && cudaStreamCreateWithFlags(&k->host_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        s = err(h, TWED_ERR_CUDA, "stream creation");
+    }
     if (s != TWED_OK) {
         delete k;
         return s;
@@ -647,6 +666,7 @@ extern "C" twed_status_t twed_knn_search(twed_knn_t k, const twed_set_f32_t* Q, 
     if (kk < 1 || C < kk || C > N || C > TOPK_MAX)
         return err(h, TWED_ERR_INVALID_ARG, "need 1 <= k <= n_candidates <= min(ndb, %d)", TOPK_MAX);
     cudaStream_t st = (cudaStream_t)stream;
+    KNN_CUDA(h, cudaEventRecord(k->ev[0], st));
     // ---- embed the queries (the encoder's buffers are the index's own)
     KNN_CUDA(h, k->qemb.ensure(sizeof(float) * nq * EMB));
     std::vector<int64_t> ids(nq);
@@ -655,6 +675,7 @@ extern "C" twed_status_t twed_knn_search(twed_knn_t k, const twed_set_f32_t* Q, 
     s = k->enc.embed(Q, ids, k->params.as<float>(), k->mu.as<float>(), k->sd.as<float>(),
                      (float)(1.0 / k->mean_len), k->qemb.as<float>(), st);
     if (s != TWED_OK) return s;
+    KNN_CUDA(h, cudaEventRecord(k->ev[1], st));
     // ---- candidates: L2 rows in query chunks, top-C per row
     const int64_t qc = std::max<int64_t>(1, std::min<int64_t>(nq, ((int64_t)1 << 28) / N));
     KNN_CUDA(h, k->sbuf.ensure(sizeof(float) * qc * N));
@@ -673,12 +694,66 @@ extern "C" twed_status_t twed_knn_search(twed_knn_t k, const twed_set_f32_t* Q, 
     KNN_CUDA(h, k->rr.ensure(sizeof(float) * nq * C));
     KNN_CUDA(h, k->pos.ensure(sizeof(int64_t) * nq * kk));
     KNN_CUDA(h, make_pairs(k->cand.as<int64_t>(), nq, C, 0, k->qpairs.as<int64_t>(), st));
+    KNN_CUDA(h, pair_cells(k->qpairs.as<int64_t>(), nq * C, Q->offs, k->db.offs,
+                           k->cells.as<unsigned long long>(), st));
+    KNN_CUDA(h, cudaEventRecord(k->ev[2], st));
     s = twed_batch_f32(h, Q, &k->db, k->qpairs.as<int64_t>(), nq * C, k->dim, k->nu, k->lambda,
                        k->p, k->rr.as<float>(), st);
     if (s != TWED_OK) return s;
+    KNN_CUDA(h, cudaEventRecord(k->ev[3], st));
     KNN_CUDA(h, topk_rows(k->rr.as<float>(), nq, C, C, kk, k->pos.as<int64_t>(), d_dist, topk_grid, st));
     KNN_CUDA(h, gather_candidates(k->cand.as<int64_t>(), k->pos.as<int64_t>(), nq, C, kk, d_idx, st));
+    KNN_CUDA(h, cudaEventRecord(k->ev[4], st));
+    k->searched = true;
     return TWED_OK;
+}
+
+extern "C" twed_status_t twed_knn_search_profile(twed_knn_t k, double* phase_ms,
+                                                 int64_t* rerank_cells) {
+    if (!k || !phase_ms || !rerank_cells) return TWED_ERR_INVALID_ARG;
+    if (!k->searched) return err(k->h, TWED_ERR_INVALID_ARG, "no search has run");
+    KNN_CUDA(k->h, cudaEventSynchronize(k->ev[4]));
+    for (int i = 0; i < 4; ++i) {
+        float ms = 0.f;
+        KNN_CUDA(k->h, cudaEventElapsedTime(&ms, k->ev[i], k->ev[i + 1]));
+        phase_ms[i] = ms;
+    }
+    unsigned long long c = 0;
+    KNN_CUDA(k->h, cudaMemcpy(&c, k->cells.p, sizeof c, cudaMemcpyDeviceToHost));
+    *rerank_cells = (int64_t)c;
+    return TWED_OK;
+}
+
+extern "C" twed_status_t twed_knn_search_host(twed_knn_t k, const float* vals, const float* ts,
+                                              const int64_t* offs, int64_t nq, int kk, int C,
+                                              int64_t* idx, float* dist) {
+    if (!k || !vals || !ts || !offs || !idx || !dist || nq < 1) return TWED_ERR_INVALID_ARG;
+    twed_handle_t h = k->h;
+    if (offs[0] != 0) return err(h, TWED_ERR_INVALID_ARG, "offs[0] != 0");
+    const int64_t total = offs[nq];
+    for (int64_t i = 0; i < total * k->dim; ++i)
+        if (!std::isfinite(vals[i])) return err(h, TWED_ERR_INVALID_ARG, "non-finite query value");
+    for (int64_t i = 0; i < total; ++i)
+        if (!std::isfinite(ts[i])) return err(h, TWED_ERR_INVALID_ARG, "non-finite query timestamp");
+    cudaStream_t st = k->host_stream;
+    KNN_CUDA(h, k->hq_vals.ensure(sizeof(float) * std::max<int64_t>(total * k->dim, 1)));
+    KNN_CUDA(h, k->hq_ts.ensure(sizeof(float) * std::max<int64_t>(total, 1)));
+    KNN_CUDA(h, k->hq_offs.ensure(sizeof(int64_t) * (nq + 1)));
+    KNN_CUDA(h, k->hq_idx.ensure(sizeof(int64_t) * nq * std::max(kk, 1)));
+    KNN_CUDA(h, k->hq_dist.ensure(sizeof(float) * nq * std::max(kk, 1)));
+    KNN_CUDA(h, cudaMemcpyAsync(k->hq_vals.p, vals, sizeof(float) * total * k->dim, cudaMemcpyHostToDevice, st));
+    KNN_CUDA(h, cudaMemcpyAsync(k->hq_ts.p, ts, sizeof(float) * total, cudaMemcpyHostToDevice, st));
+    KNN_CUDA(h, cudaMemcpyAsync(k->hq_offs.p, offs, sizeof(int64_t) * (nq + 1), cudaMemcpyHostToDevice, st));
+    twed_set_f32_t Q{k->hq_vals.as<float>(), k->hq_ts.as<float>(), k->hq_offs.as<int64_t>(), offs, nq};
+    twed_status_t s = twed_knn_search(k, &Q, kk, C, k->hq_idx.as<int64_t>(), k->hq_dist.as<float>(), st);
+    if (s != TWED_OK) {
+        cudaStreamSynchronize(st);
+        return s;
+    }
+    KNN_CUDA(h, cudaMemcpyAsync(idx, k->hq_idx.p, sizeof(int64_t) * nq * kk, cudaMemcpyDeviceToHost, st));
+    KNN_CUDA(h, cudaMemcpyAsync(dist, k->hq_dist.p, sizeof(float) * nq * kk, cudaMemcpyDeviceToHost, st));
+    KNN_CUDA(h, cudaStreamSynchronize(st));
+    return twed_sync_status(h, st);
 }
 
 extern "C" twed_status_t twed_knn_exact(twed_knn_t k, const twed_set_f32_t* Q, int kk,

@@ -39,7 +39,7 @@ EXPORTS = (
     "twed_plan_destroy",
     "twed_allpairs_host_f32",
     "twed_knn_config_default", "twed_knn_create", "twed_knn_train", "twed_knn_search",
-    "twed_knn_exact", "twed_knn_get_stats", "twed_knn_get_params", "twed_knn_set_params",
+    "twed_knn_exact", "twed_knn_search_host", "twed_knn_search_profile", "twed_knn_get_stats", "twed_knn_get_params", "twed_knn_set_params",
     "twed_knn_get_embeddings", "twed_knn_destroy",
     "twed_encoder_param_count", "twed_encoder_stats_f32", "twed_encoder_forward_f32",
     "twed_encoder_loss_grad_f32", "twed_adam_f32", "twed_embed_search_f32", "twed_topk_rows_f32",
@@ -119,6 +119,8 @@ def load(path: str | None = None):
             "twed_knn_train": (ci, [P]),
             "twed_knn_search": (ci, [P, P, ci, ci, P, P, P]),
             "twed_knn_exact": (ci, [P, P, ci, P, P, P]),
+            "twed_knn_search_host": (ci, [P, P, P, P, i64, ci, ci, P, P]),
+            "twed_knn_search_profile": (ci, [P, P, P]),
             "twed_knn_get_stats": (ci, [P, P]),
             "twed_knn_get_params": (ci, [P, P, i64]),
             "twed_knn_set_params": (ci, [P, P, i64]),
@@ -523,6 +525,27 @@ class KnnIndex:
                                                           n_candidates, _t_ptr(idx),
                                                           _t_ptr(dist), _stream_ptr(stream)))
         return idx, dist
+
+    def search_host(self, vals, ts, offs, k=10, n_candidates=200, out=None):
+        """Host arrays in, host arrays out (blocking)."""
+        v = np.ascontiguousarray(vals, dtype=np.float32)
+        t = np.ascontiguousarray(ts, dtype=np.float32)
+        o = np.ascontiguousarray(offs, dtype=np.int64)
+        nq = o.shape[0] - 1
+        if out is None:
+            out = (np.empty((nq, k), dtype=np.int64), np.empty((nq, k), dtype=np.float32))
+        self.handle.check(self.handle.lib.twed_knn_search_host(
+            self.k, _np_ptr(v), _np_ptr(t), _np_ptr(o), nq, k, n_candidates, _np_ptr(out[0]),
+            _np_ptr(out[1])))
+        return out
+
+    def search_profile(self):
+        """(phase_ms [embed, candidates, re-rank, select], re-rank cells) of
+        the last search."""
+        ms = (ctypes.c_double * 4)()
+        cells = ctypes.c_int64()
+        self.handle.check(self.handle.lib.twed_knn_search_profile(self.k, ms, ctypes.byref(cells)))
+        return list(ms), cells.value
 
     def exact(self, queries: DeviceSet, k=10, stream=None, out=None):
         idx, dist = out if out is not None else self._outputs(queries.n, k)

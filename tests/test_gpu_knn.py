@@ -302,3 +302,19 @@ def test_search_rejects_bad_sizes(tw, small_index, bad):
     with pytest.raises(tw.TwedError) as ei:
         index.search(Q, k=max(k, 1) if bad != "k0" else 0, n_candidates=c)
     assert ei.value.status == tw.TWED_ERR_INVALID_ARG
+
+
+def test_search_host_matches_device_search(tw, small_index):
+    index, db, qs, Q, _, _ = small_index
+    idx, dist = index.search(Q, k=5, n_candidates=64)
+    hidx, hdist = index.search_host(qs.vals, qs.ts, qs.offs, k=5, n_candidates=64)
+    np.testing.assert_array_equal(hidx, idx.cpu().numpy())
+    np.testing.assert_array_equal(hdist, dist.cpu().numpy())
+
+
+def test_search_profile_counts_rerank_cells(tw, small_index):
+    index, db, qs, Q, _, _ = small_index
+    index.search(Q, k=3, n_candidates=db.n)
+    ms, cells = index.search_profile()
+    assert cells == int(qs.lengths.sum()) * int(db.lengths.sum())
+    assert all(m >= 0 for m in ms) and ms[2] > 0
