@@ -147,6 +147,19 @@ class ClockSampler:
                 "reasons": reasons, "samples": int(len(rows)), "samples_under_load": int(load.sum())}
 
 
+_FFMA_PEAK = None
+
+
+def ffma_peak() -> float:
+    """FP32 FFMA lane operations per second measured in this run (library
+    microbenchmark: independent FMA chains on every SM)."""
+    global _FFMA_PEAK
+    if _FFMA_PEAK is None:
+        from paper_2007_16135_gb300 import twed
+        _FFMA_PEAK = twed.pipe_peak(twed.PEAK_FFMA32)
+    return _FFMA_PEAK
+
+
 def ops_per_cell(dim: int, p: int) -> int:
     """FP32-pipe operations (FADD/FMUL/FFMA) the recurrence needs per cell:
     dim subtractions and dim multiply-adds for d (p = 2), the time term
@@ -263,6 +276,9 @@ def bench_plan(args, rank, world, dev, workload):
                            f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
                            f"{sm_max:.0f} MHz (max SM clock)",
                        "kernel": kname}
+    mp = ffma_peak()
+    res["roofline"]["peak_measured"] = mp / 1e12
+    res["roofline"]["frac_of_measured"] = achieved / mp
     if xterm:
         # tensor pipe: 2*64 flops per cell; TF32 dense peak taken as half the
         # measured BF16 GEMM peak (the nominal TF32:BF16 ratio)
@@ -458,14 +474,16 @@ def bench_knn(args, rank, world, dev, steps, warmup):
                                 "rerank": phase_ms[2], "select": phase_ms[3]},
                    "rerank_cells": rr_cells, "rerank_gcups": rr_cells / (phase_ms[2] / 1e3) / 1e9,
                    "train": {key: train[key] for key in ("sigma", "first_loss", "last_loss",
-                                                         "label_pairs", "label_cells", "steps",
+                                                         "label_pairs", "mined_pairs", "label_cells", "steps",
                                                          "label_ms", "train_ms", "embed_ms")}},
            "roofline": {"bound": "alu", "achieved": rr_cells * opc / (phase_ms[2] / 1e3) / 1e12,
                         "peak": peak / 1e12, "unit": "Top/s",
                         "frac": rr_cells * opc / (phase_ms[2] / 1e3) / peak, "traffic": None,
                         "ops_per_cell": opc, "kernel": "pairs_kernel<float,4,2,8> (exact re-rank)",
                         "peak_basis": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} "
-                                      f"FP32 lanes x {sm_max:.0f} MHz (max SM clock)"},
+                                      f"FP32 lanes x {sm_max:.0f} MHz (max SM clock)",
+                        "peak_measured": ffma_peak() / 1e12,
+                        "frac_of_measured": rr_cells * opc / (phase_ms[2] / 1e3) / ffma_peak()},
            # per search: query gather/transform/3 convs/pool, L2 + top-C, pairs +
            # cells, records A/B + pairs kernel, top-k + gather
            "gpu_launches": 15 * steps}

@@ -260,7 +260,12 @@ twed_status_t twed_allpairs_host_f32(twed_handle_t handle, const float* a_vals,
  * (group_size (group_size-1) / 2) series.  sigma = mean label.  Each Adam
  * step (beta 0.9 / 0.999, eps 1e-8, cosine-decayed learning rate) minimises
  * the mean squared error of the model over the pairs of `groups_per_step`
- * groups.  Then every database series is embedded. */
+ * groups.  With mine_fraction f > 0, (1-f) train_pairs come from random
+ * groups, used alone for the first half of the epochs; then the database is
+ * embedded and f train_pairs come from mined groups -- a seeded anchor and
+ * the group_size-1 series nearest to it under the current model -- labelled
+ * exactly and trained on together with the random groups for the other half.
+ * Then every database series is embedded. */
 typedef struct twed_knn_s* twed_knn_t;
 typedef struct {
     int group_size;       /* series per labelled group, 2..64 (default 32) */
@@ -269,6 +274,7 @@ typedef struct {
     int64_t train_pairs;  /* labelled pairs (default 1,000,000) */
     float lr;             /* peak learning rate (default 2e-3) */
     uint64_t seed;        /* group sampling and weight initialisation (default 1) */
+    float mine_fraction;  /* share of train_pairs from mined groups, [0, 1) (default 0) */
 } twed_knn_config_t;
 
 typedef struct {
@@ -276,7 +282,8 @@ typedef struct {
     double mean_len;       /* mean database series length (pool divisor) */
     double first_loss;     /* mean loss of the first epoch */
     double last_loss;      /* mean loss of the last epoch */
-    int64_t label_pairs;   /* pairs labelled with exact TWED */
+    int64_t label_pairs;   /* pairs labelled with exact TWED (random + mined) */
+    int64_t mined_pairs;   /* of which in mined groups */
     int64_t label_cells;   /* interior cells of those pairs */
     int64_t steps;         /* Adam steps taken */
     double label_ms;       /* wall time of labelling (exact TWED) */
@@ -368,6 +375,16 @@ twed_status_t twed_embed_search_f32(twed_handle_t handle, const float* d_db_emb,
 twed_status_t twed_topk_rows_f32(twed_handle_t handle, const float* d_D, int64_t rows,
                                  int64_t cols, int64_t ld, int k, int64_t* d_idx, float* d_val,
                                  void* stream);
+
+/* ---- pipe peaks -----------------------------------------------------------
+ * Not from the paper: measures the issue rate that bounds the ALU-bound
+ * kernels, for their roofline.  Independent FFMA (FP32) or DFMA (FP64)
+ * chains on every SM, timed with CUDA events on the legacy stream (best of
+ * three after a warm-up); *ops_per_s = lane operations per second (one FMA =
+ * one operation).  Blocking. */
+#define TWED_PEAK_FFMA32 0
+#define TWED_PEAK_DFMA64 1
+twed_status_t twed_pipe_peak(twed_handle_t handle, int kind, double* ops_per_s);
 
 #ifdef __cplusplus
 }

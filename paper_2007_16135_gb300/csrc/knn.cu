@@ -350,6 +350,7 @@ extern "C" void twed_knn_config_default(twed_knn_config_t* c) {
     c->train_pairs = 1000000;
     c->lr = 2e-3f;
     c->seed = 1;
+    c->mine_fraction = 0.0f;
 }
 
 extern "C" twed_status_t twed_knn_create(twed_handle_t h, const twed_set_f32_t* db, int dim,
@@ -366,7 +367,8 @@ extern "C" twed_status_t twed_knn_create(twed_handle_t h, const twed_set_f32_t* 
     if (cfg) c = *cfg;
     if (c.group_size < 2 || c.group_size > 64 || c.group_size > db->n)
         return err(h, TWED_ERR_INVALID_ARG, "group_size must be in [2, min(64, ndb)]");
-    if (c.groups_per_step < 1 || c.epochs < 0 || c.train_pairs < 1 || !(c.lr > 0.f))
+    if (c.groups_per_step < 1 || c.epochs < 0 || c.train_pairs < 1 || !(c.lr > 0.f) ||
+        !(c.mine_fraction >= 0.f && c.mine_fraction < 1.f))
         return err(h, TWED_ERR_INVALID_ARG, "bad training configuration");
     twed_knn_t k = new (std::nothrow) twed_knn_s();
     if (!k) return err(h, TWED_ERR_ALLOC, "index");
@@ -433,102 +435,56 @@ extern "C" void twed_knn_destroy(twed_knn_t k) {
     delete k;
 }
 
-extern "C" twed_status_t twed_knn_train(twed_knn_t k) {
-    if (!k) return TWED_ERR_INVALID_ARG;
-    twed_handle_t h = k->h;
-    cudaStream_t st;
-    KNN_CUDA(h, cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
-    struct StreamGuard {
-        cudaStream_t s;
-        ~StreamGuard() { cudaStreamSynchronize(s); cudaStreamDestroy(s); }
-    } guard{st};
-    const twed_knn_config_t& c = k->cfg;
-    const Layout& L = k->enc.L;
-    const int64_t N = k->db.n;
-    const int G = c.group_size;
-    const int64_t npg = (int64_t)G * (G - 1) / 2;
-    const int64_t ngroups = (c.train_pairs + npg - 1) / npg;
-    k->trained = false;
-    // ---- fresh parameters and Adam state
-    std::vector<float> w;
-    init_params(w, L, c.seed);
-    KNN_CUDA(h, cudaMemcpyAsync(k->params.p, w.data(), sizeof(float) * L.total, cudaMemcpyHostToDevice, st));
-    KNN_CUDA(h, cudaMemsetAsync(k->m.p, 0, sizeof(float) * L.total, st));
-    KNN_CUDA(h, cudaMemsetAsync(k->v.p, 0, sizeof(float) * L.total, st));
-    // ---- input statistics
-    KNN_CUDA(h, feature_stats(k->db.vals, k->db.ts, k->db.offs, N, k->db_offs[N], k->dim, k->p,
-                              k->nu, k->lambda, k->stat_part.as<double>(), k->mu.as<float>(),
-                              k->sd.as<float>(), st));
-    // ---- groups: consecutive chunks of seeded permutations of the database
-    uint64_t rng = c.seed * 0x9E3779B97F4A7C15ull + 3;
-    std::vector<int64_t> members((size_t)ngroups * G);
-    {
-        std::vector<int64_t> perm(N);
-        int64_t used = N;
-        for (int64_t g = 0; g < ngroups; ++g) {
-            if (used + G > N) {
-                for (int64_t i = 0; i < N; ++i) perm[i] = i;
-                shuffle(perm, rng);
-                used = 0;
-            }
-            for (int a = 0; a < G; ++a) members[g * G + a] = perm[used + a];
-            used += G;
-        }
-    }
-    // ---- labels: exact TWED of every pair inside every group
-    const int64_t nlab = ngroups * npg;
-    std::vector<int64_t> pairs((size_t)nlab * 2);
+namespace {
+
+// Pair list (a < b, row-major) of groups [g0, g1) of `members`.
+int64_t group_pair_list(const twed_knn_t k, const std::vector<int64_t>& members, int G, int64_t g0,
+                        int64_t g1, std::vector<int64_t>& pairs) {
     int64_t cells = 0;
-    for (int64_t g = 0, q = 0; g < ngroups; ++g)
+    pairs.clear();
+    for (int64_t g = g0; g < g1; ++g)
         for (int a = 0; a < G; ++a)
-            for (int b = a + 1; b < G; ++b, ++q) {
+            for (int b = a + 1; b < G; ++b) {
                 const int64_t x = members[g * G + a], y = members[g * G + b];
-                pairs[2 * q] = x;
-                pairs[2 * q + 1] = y;
+                pairs.push_back(x);
+                pairs.push_back(y);
                 cells += (k->db_offs[x + 1] - k->db_offs[x]) * (k->db_offs[y + 1] - k->db_offs[y]);
             }
-    {
-        cudaError_t e = k->lpairs.ensure(sizeof(int64_t) * 2 * nlab);
-        if (e == cudaSuccess) e = k->labels.ensure(sizeof(float) * nlab);
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return err(h, TWED_ERR_ALLOC, "label memory: %s", cudaGetErrorString(e));
-        }
-    }
-    KNN_CUDA(h, cudaMemcpyAsync(k->lpairs.p, pairs.data(), sizeof(int64_t) * 2 * nlab, cudaMemcpyHostToDevice, st));
+    return cells;
+}
+
+// Exact TWED labels of every pair of groups [g0, g1) into labels[g0 * npg ..].
+twed_status_t label_groups(twed_knn_t k, const std::vector<int64_t>& members, int G, int64_t g0,
+                           int64_t g1, cudaStream_t st) {
+    twed_handle_t h = k->h;
+    const int64_t npg = (int64_t)G * (G - 1) / 2;
+    std::vector<int64_t> pairs;
+    const int64_t cells = group_pair_list(k, members, G, g0, g1, pairs);
+    const int64_t n = (g1 - g0) * npg;
+    KNN_CUDA(h, k->lpairs.ensure(sizeof(int64_t) * 2 * std::max<int64_t>(n, 1)));
+    KNN_CUDA(h, cudaMemcpyAsync(k->lpairs.p, pairs.data(), sizeof(int64_t) * 2 * n, cudaMemcpyHostToDevice, st));
     KNN_CUDA(h, cudaStreamSynchronize(st));
-    auto t0 = std::chrono::steady_clock::now();
-    twed_status_t s = twed_batch_f32(h, &k->db, &k->db, k->lpairs.as<int64_t>(), nlab, k->dim, k->nu,
-                                     k->lambda, k->p, k->labels.as<float>(), st);
+    const auto t0 = std::chrono::steady_clock::now();
+    twed_status_t s = twed_batch_f32(h, &k->db, &k->db, k->lpairs.as<int64_t>(), n, k->dim, k->nu,
+                                     k->lambda, k->p, k->labels.as<float>() + g0 * npg, st);
     if (s != TWED_OK) return s;
     KNN_CUDA(h, cudaStreamSynchronize(st));
     if ((s = twed_sync_status(h, st)) != TWED_OK) return s;
-    k->stats.label_ms = ms_since(t0);
-    k->stats.label_pairs = nlab;
-    k->stats.label_cells = cells;
-    // ---- sigma = mean label; inv_sigma lives on the device for the loss kernel
-    float* sc = k->scalars.as<float>();  // [0] mean label, [1] z_min, [2] inv_sigma, [3] loss
-    KNN_CUDA(h, sum_scaled(k->labels.as<float>(), nlab, 1.0 / (double)nlab, sc, st));
-    float sigma = 0.f;
-    KNN_CUDA(h, cudaMemcpyAsync(&sigma, sc, sizeof(float), cudaMemcpyDeviceToHost, st));
-    KNN_CUDA(h, cudaStreamSynchronize(st));
-    if (!(sigma > 0.f) || !std::isfinite(sigma))
-        return err(h, TWED_ERR_INVALID_ARG, "training labels have no positive scale");
-    const float inv_sigma = 1.0f / sigma;
-    KNN_CUDA(h, cudaMemcpyAsync(sc + 2, &inv_sigma, sizeof(float), cudaMemcpyHostToDevice, st));
-    k->stats.sigma = sigma;
-    k->stats.mean_len = k->mean_len;
-    // ---- Adam steps over shuffled group order, cosine learning rate
+    k->stats.label_ms += ms_since(t0);
+    k->stats.label_pairs += n;
+    k->stats.label_cells += cells;
+    return TWED_OK;
+}
+
+// `epochs` passes over groups [0, ngroups) in seeded shuffled order, one Adam
+// step per `groups_per_step` groups, cosine learning rate over total_steps.
+twed_status_t run_epochs(twed_knn_t k, const std::vector<int64_t>& members, int G, int64_t ngroups,
+                         int epochs, uint64_t& rng, int64_t& step, int64_t total_steps,
+                         cudaStream_t st) {
+    twed_handle_t h = k->h;
+    const twed_knn_config_t& c = k->cfg;
+    const Layout& L = k->enc.L;
     const int64_t gps = std::min<int64_t>(c.groups_per_step, ngroups);
-    const int64_t steps_per_epoch = (ngroups + gps - 1) / gps;
-    const int64_t total_steps = steps_per_epoch * (int64_t)c.epochs;
-    {
-        cudaError_t e = k->losses.ensure(sizeof(float) * std::max<int64_t>(total_steps, 1));
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return err(h, TWED_ERR_ALLOC, "loss history: %s", cudaGetErrorString(e));
-        }
-    }
     std::vector<int64_t> order(ngroups);
     for (int64_t g = 0; g < ngroups; ++g) order[g] = g;
     // The whole schedule (series ids, gapped-row bases, group ids of every
@@ -537,7 +493,7 @@ extern "C" twed_status_t twed_knn_train(twed_knn_t k) {
     std::vector<int64_t> sids, sbase, sgid;
     std::vector<int64_t> step_ng, step_p, step_ids_off, step_base_off, step_gid_off;
     int64_t max_rows = 0, max_ng = 0;
-    for (int ep = 0; ep < c.epochs; ++ep) {
+    for (int ep = 0; ep < epochs; ++ep) {
         shuffle(order, rng);
         for (int64_t g0 = 0; g0 < ngroups; g0 += gps) {
             const int64_t ng = std::min(gps, ngroups - g0);
@@ -556,32 +512,26 @@ extern "C" twed_status_t twed_knn_train(twed_knn_t k) {
             max_ng = std::max(max_ng, ng);
         }
     }
-    {
-        cudaError_t e = k->sched.ensure(sizeof(int64_t) * (sids.size() + sbase.size() + sgid.size() + 3));
-        if (e != cudaSuccess) {
-            cudaGetLastError();
-            return err(h, TWED_ERR_ALLOC, "training schedule: %s", cudaGetErrorString(e));
-        }
-    }
+    if (step_ng.empty()) return TWED_OK;
+    KNN_CUDA(h, cudaStreamSynchronize(st));
+    KNN_CUDA(h, k->sched.ensure(sizeof(int64_t) * (sids.size() + sbase.size() + sgid.size() + 3)));
     int64_t* d_sids = k->sched.as<int64_t>();
     int64_t* d_sbase = d_sids + sids.size();
     int64_t* d_sgid = d_sbase + sbase.size();
     KNN_CUDA(h, cudaMemcpyAsync(d_sids, sids.data(), sizeof(int64_t) * sids.size(), cudaMemcpyHostToDevice, st));
     KNN_CUDA(h, cudaMemcpyAsync(d_sbase, sbase.data(), sizeof(int64_t) * sbase.size(), cudaMemcpyHostToDevice, st));
     KNN_CUDA(h, cudaMemcpyAsync(d_sgid, sgid.data(), sizeof(int64_t) * sgid.size(), cudaMemcpyHostToDevice, st));
-    if ((s = k->enc.reserve(max_rows, max_ng * G, max_ng, true)) != TWED_OK) return s;
-    KNN_CUDA(h, cudaStreamSynchronize(st));
+    twed_status_t s = k->enc.reserve(max_rows, max_ng * G, max_ng, true);
+    if (s != TWED_OK) return s;
     const float inv_mean_len = (float)(1.0 / k->mean_len);
     const double b1 = 0.9, b2 = 0.999;
-    t0 = std::chrono::steady_clock::now();
+    float* sc = k->scalars.as<float>();
     KNN_CUDA(h, transform_weights(k->params.as<float>(), L, k->enc.cin, k->enc.views(), st));
-    int64_t step = 0;
-    for (; step < total_steps; ++step) {
-        s = k->enc.loss_grad(&k->db, d_sids + step_ids_off[step], d_sbase + step_base_off[step],
-                             step_p[step], step_ng[step], G, d_sgid + step_gid_off[step],
-                             k->labels.as<float>(), sc + 2, k->params.as<float>(), k->mu.as<float>(),
-                             k->sd.as<float>(), inv_mean_len, k->grad.as<float>(),
-                             k->losses.as<float>() + step, st);
+    for (size_t i = 0; i < step_ng.size(); ++i, ++step) {
+        s = k->enc.loss_grad(&k->db, d_sids + step_ids_off[i], d_sbase + step_base_off[i], step_p[i],
+                             step_ng[i], G, d_sgid + step_gid_off[i], k->labels.as<float>(), sc + 2,
+                             k->params.as<float>(), k->mu.as<float>(), k->sd.as<float>(),
+                             inv_mean_len, k->grad.as<float>(), k->losses.as<float>() + step, st);
         if (s != TWED_OK) return s;
         const double t = (double)(step + 1);
         const double lr = c.lr * 0.5 * (1.0 + std::cos(M_PI * (double)step / (double)total_steps));
@@ -592,17 +542,157 @@ extern "C" twed_status_t twed_knn_train(twed_knn_t k) {
         KNN_CUDA(h, transform_weights(k->params.as<float>(), L, k->enc.cin, k->enc.views(), st));
     }
     KNN_CUDA(h, cudaStreamSynchronize(st));
-    k->stats.train_ms = ms_since(t0);
+    return TWED_OK;
+}
+
+// Hard groups: an anchor (seeded draw from the database) and the G - 1
+// database series nearest to it under the current model (the search
+// distance, anchor excluded).  Appends nmine groups to `members`.
+twed_status_t mine_groups(twed_knn_t k, int G, int64_t nmine, uint64_t& rng,
+                          std::vector<int64_t>& members, cudaStream_t st) {
+    twed_handle_t h = k->h;
+    const int64_t N = k->db.n;
+    twed_status_t s = embed_database(k, st);
+    if (s != TWED_OK) return s;
+    std::vector<float> emb((size_t)N * EMB);
+    KNN_CUDA(h, cudaMemcpy(emb.data(), k->emb_db.p, sizeof(float) * N * EMB, cudaMemcpyDeviceToHost));
+    std::vector<int64_t> anchors;
+    {
+        std::vector<int64_t> perm(N);
+        while ((int64_t)anchors.size() < nmine) {
+            for (int64_t i = 0; i < N; ++i) perm[i] = i;
+            shuffle(perm, rng);
+            for (int64_t i = 0; i < N && (int64_t)anchors.size() < nmine; ++i) anchors.push_back(perm[i]);
+        }
+    }
+    const int64_t qc = std::max<int64_t>(1, std::min<int64_t>(nmine, ((int64_t)1 << 28) / N));
+    KNN_CUDA(h, k->sbuf.ensure(sizeof(float) * qc * N));
+    KNN_CUDA(h, k->qemb.ensure(sizeof(float) * qc * EMB));
+    KNN_CUDA(h, k->cand.ensure(sizeof(int64_t) * qc * G));
+    KNN_CUDA(h, k->candval.ensure(sizeof(float) * qc * G));
+    std::vector<float> qe((size_t)qc * EMB);
+    std::vector<int64_t> cand((size_t)qc * G);
+    const int topk_grid = twed::detail::handle_sms(h) * 2;
+    for (int64_t a0 = 0; a0 < nmine; a0 += qc) {
+        const int64_t n = std::min(qc, nmine - a0);
+        for (int64_t i = 0; i < n; ++i)
+            std::memcpy(&qe[i * EMB], &emb[anchors[a0 + i] * EMB], sizeof(float) * EMB);
+        KNN_CUDA(h, cudaMemcpyAsync(k->qemb.p, qe.data(), sizeof(float) * n * EMB, cudaMemcpyHostToDevice, st));
+        KNN_CUDA(h, l2_rows(k->qemb.as<float>(), n, k->svec_db.as<float>(), N, k->sbuf.as<float>(), N, st));
+        KNN_CUDA(h, topk_rows(k->sbuf.as<float>(), n, N, N, G, k->cand.as<int64_t>(),
+                              k->candval.as<float>(), topk_grid, st));
+        KNN_CUDA(h, cudaMemcpyAsync(cand.data(), k->cand.p, sizeof(int64_t) * n * G, cudaMemcpyDeviceToHost, st));
+        KNN_CUDA(h, cudaStreamSynchronize(st));
+        for (int64_t i = 0; i < n; ++i) {
+            const int64_t anchor = anchors[a0 + i];
+            members.push_back(anchor);
+            int taken = 0;
+            for (int j = 0; j < G && taken < G - 1; ++j) {
+                if (cand[i * G + j] == anchor) continue;
+                members.push_back(cand[i * G + j]);
+                ++taken;
+            }
+        }
+    }
+    return TWED_OK;
+}
+
+}  // namespace
+
+extern "C" twed_status_t twed_knn_train(twed_knn_t k) {
+    if (!k) return TWED_ERR_INVALID_ARG;
+    twed_handle_t h = k->h;
+    cudaStream_t st;
+    KNN_CUDA(h, cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    struct StreamGuard {
+        cudaStream_t s;
+        ~StreamGuard() { cudaStreamSynchronize(s); cudaStreamDestroy(s); }
+    } guard{st};
+    const twed_knn_config_t& c = k->cfg;
+    const Layout& L = k->enc.L;
+    const int64_t N = k->db.n;
+    const int G = c.group_size;
+    const int64_t npg = (int64_t)G * (G - 1) / 2;
+    const double f = std::min(1.0, std::max(0.0, (double)c.mine_fraction));
+    const int64_t nmine = f > 0.0 ? (int64_t)std::ceil(f * (double)c.train_pairs / (double)npg) : 0;
+    const int64_t nrand = std::max<int64_t>(1, (int64_t)std::ceil((1.0 - f) * (double)c.train_pairs / (double)npg));
+    const int e1 = nmine > 0 ? (c.epochs + 1) / 2 : c.epochs;
+    const int e2 = c.epochs - e1;
+    k->trained = false;
+    k->stats = twed_knn_stats_t{};
+    // ---- fresh parameters and Adam state
+    std::vector<float> w;
+    init_params(w, L, c.seed);
+    KNN_CUDA(h, cudaMemcpyAsync(k->params.p, w.data(), sizeof(float) * L.total, cudaMemcpyHostToDevice, st));
+    KNN_CUDA(h, cudaMemsetAsync(k->m.p, 0, sizeof(float) * L.total, st));
+    KNN_CUDA(h, cudaMemsetAsync(k->v.p, 0, sizeof(float) * L.total, st));
+    // ---- input statistics
+    KNN_CUDA(h, feature_stats(k->db.vals, k->db.ts, k->db.offs, N, k->db_offs[N], k->dim, k->p,
+                              k->nu, k->lambda, k->stat_part.as<double>(), k->mu.as<float>(),
+                              k->sd.as<float>(), st));
+    // ---- random groups: consecutive chunks of seeded permutations
+    uint64_t rng = c.seed * 0x9E3779B97F4A7C15ull + 3;
+    std::vector<int64_t> members;
+    members.reserve((size_t)(nrand + nmine) * G);
+    {
+        std::vector<int64_t> perm(N);
+        int64_t used = N;
+        for (int64_t g = 0; g < nrand; ++g) {
+            if (used + G > N) {
+                for (int64_t i = 0; i < N; ++i) perm[i] = i;
+                shuffle(perm, rng);
+                used = 0;
+            }
+            for (int a = 0; a < G; ++a) members.push_back(perm[used + a]);
+            used += G;
+        }
+    }
+    KNN_CUDA(h, k->labels.ensure(sizeof(float) * (nrand + nmine) * npg));
+    twed_status_t s = label_groups(k, members, G, 0, nrand, st);
+    if (s != TWED_OK) return s;
+    // ---- sigma = mean label of the random pairs (fixed for all of training)
+    float* sc = k->scalars.as<float>();  // [0] mean label, [1] z_min, [2] inv_sigma
+    KNN_CUDA(h, sum_scaled(k->labels.as<float>(), nrand * npg, 1.0 / (double)(nrand * npg), sc, st));
+    float sigma = 0.f;
+    KNN_CUDA(h, cudaMemcpyAsync(&sigma, sc, sizeof(float), cudaMemcpyDeviceToHost, st));
+    KNN_CUDA(h, cudaStreamSynchronize(st));
+    if (!(sigma > 0.f) || !std::isfinite(sigma))
+        return err(h, TWED_ERR_INVALID_ARG, "training labels have no positive scale");
+    const float inv_sigma = 1.0f / sigma;
+    KNN_CUDA(h, cudaMemcpyAsync(sc + 2, &inv_sigma, sizeof(float), cudaMemcpyHostToDevice, st));
+    k->stats.sigma = sigma;
+    k->stats.mean_len = k->mean_len;
+    // ---- steps: e1 epochs on random groups, then (with mining) e2 on all
+    const int64_t gps = std::max<int64_t>(1, c.groups_per_step);
+    const int64_t spe1 = (nrand + gps - 1) / gps;
+    const int64_t spe2 = (nrand + nmine + gps - 1) / gps;
+    const int64_t total_steps = spe1 * e1 + spe2 * e2;
+    KNN_CUDA(h, k->losses.ensure(sizeof(float) * std::max<int64_t>(total_steps, 1)));
+    int64_t step = 0;
+    auto t0 = std::chrono::steady_clock::now();
+    if ((s = run_epochs(k, members, G, nrand, e1, rng, step, total_steps, st)) != TWED_OK) return s;
+    double train_ms = ms_since(t0);
+    if (nmine > 0) {
+        if ((s = mine_groups(k, G, nmine, rng, members, st)) != TWED_OK) return s;
+        if ((s = label_groups(k, members, G, nrand, nrand + nmine, st)) != TWED_OK) return s;
+        k->stats.mined_pairs = nmine * npg;
+        t0 = std::chrono::steady_clock::now();
+        if ((s = run_epochs(k, members, G, nrand + nmine, e2, rng, step, total_steps, st)) != TWED_OK)
+            return s;
+        train_ms += ms_since(t0);
+    }
+    k->stats.train_ms = train_ms;
     k->stats.steps = step;
     if (step > 0) {
         std::vector<float> hist(step);
         KNN_CUDA(h, cudaMemcpy(hist.data(), k->losses.p, sizeof(float) * step, cudaMemcpyDeviceToHost));
-        const int64_t e0 = std::min<int64_t>(steps_per_epoch, step);
+        const int64_t n0 = std::min<int64_t>(spe1, step);
         double a = 0, b = 0;
-        for (int64_t i = 0; i < e0; ++i) a += hist[i];
-        for (int64_t i = step - e0; i < step; ++i) b += hist[i];
-        k->stats.first_loss = a / e0;
-        k->stats.last_loss = b / e0;
+        for (int64_t i = 0; i < n0; ++i) a += hist[i];
+        const int64_t n1 = std::min<int64_t>(e2 > 0 ? spe2 : spe1, step);
+        for (int64_t i = step - n1; i < step; ++i) b += hist[i];
+        k->stats.first_loss = a / n0;
+        k->stats.last_loss = b / n1;
     }
     // ---- embed the database
     t0 = std::chrono::steady_clock::now();

@@ -43,6 +43,7 @@ EXPORTS = (
     "twed_knn_get_embeddings", "twed_knn_destroy",
     "twed_encoder_param_count", "twed_encoder_stats_f32", "twed_encoder_forward_f32",
     "twed_encoder_loss_grad_f32", "twed_adam_f32", "twed_embed_search_f32", "twed_topk_rows_f32",
+    "twed_pipe_peak",
 )
 
 
@@ -134,6 +135,7 @@ def load(path: str | None = None):
             "twed_adam_f32": (ci, [P, P, P, P, P, i64, i64, f, f, f, f]),
             "twed_embed_search_f32": (ci, [P, P, i64, P, i64, ci, P, P]),
             "twed_topk_rows_f32": (ci, [P, P, i64, i64, i64, ci, P, P, P]),
+            "twed_pipe_peak": (ci, [P, ci, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -444,13 +446,14 @@ def twed_allpairs_host_f32(a_vals, a_ts, a_offs, b=None, nu=1.0, lam=1.0, p=2,
 class KnnConfig(ctypes.Structure):
     _fields_ = [("group_size", ctypes.c_int), ("groups_per_step", ctypes.c_int),
                 ("epochs", ctypes.c_int), ("train_pairs", ctypes.c_int64), ("lr", ctypes.c_float),
-                ("seed", ctypes.c_uint64)]
+                ("seed", ctypes.c_uint64), ("mine_fraction", ctypes.c_float)]
 
 
 class KnnStats(ctypes.Structure):
     _fields_ = [("sigma", ctypes.c_double), ("mean_len", ctypes.c_double),
                 ("first_loss", ctypes.c_double), ("last_loss", ctypes.c_double),
-                ("label_pairs", ctypes.c_int64), ("label_cells", ctypes.c_int64),
+                ("label_pairs", ctypes.c_int64), ("mined_pairs", ctypes.c_int64),
+                ("label_cells", ctypes.c_int64),
                 ("steps", ctypes.c_int64), ("label_ms", ctypes.c_double),
                 ("train_ms", ctypes.c_double), ("embed_ms", ctypes.c_double)]
 
@@ -644,3 +647,14 @@ def topk_rows(D, k, cols=None, stream=None, handle: Handle | None = None):
     h.check(h.lib.twed_topk_rows_f32(h.h, _t_ptr(D), rows, cols, ld, k, _t_ptr(idx), _t_ptr(val),
                                      _stream_ptr(stream)))
     return idx, val
+
+
+PEAK_FFMA32, PEAK_DFMA64 = 0, 1
+
+
+def pipe_peak(kind=PEAK_FFMA32, handle: Handle | None = None) -> float:
+    """Measured FMA lane operations per second (FP32 or FP64 pipe)."""
+    h = handle or default_handle()
+    v = ctypes.c_double()
+    h.check(h.lib.twed_pipe_peak(h.h, int(kind), ctypes.byref(v)))
+    return v.value

@@ -318,3 +318,13 @@ def test_search_profile_counts_rerank_cells(tw, small_index):
     ms, cells = index.search_profile()
     assert cells == int(qs.lengths.sum()) * int(db.lengths.sum())
     assert all(m >= 0 for m in ms) and ms[2] > 0
+
+
+def test_pipe_peaks_are_plausible(tw):
+    import torch
+    props = torch.cuda.get_device_properties(0)
+    nominal = props.multi_processor_count * 128 * 2.1e9  # FFMA lanes x a clock above max
+    f32 = tw.pipe_peak(tw.PEAK_FFMA32)
+    f64 = tw.pipe_peak(tw.PEAK_DFMA64)
+    assert 0.2 * nominal < f32 < nominal
+    assert 0 < f64 < f32
