@@ -35,7 +35,8 @@ METRIC = "TWED GCUPS on 1 GB300; k-NN queries/s at recall@10>=0.99 vs exact batc
 UNIT = "GCUPS"
 FALLBACK_SM_MAX_MHZ = 2070.0
 FP32_LANES_PER_SM = 128  # FADD/FMUL/FFMA lanes per SM per clock
-KERNEL_SOURCES = ["engine.cuh", "kernels.cuh", "kernels_f32.cu", "kernels_f64.cu", "launch.h"]
+KERNEL_SOURCES = ["engine.cuh", "engine_f32.cuh", "kernels.cuh", "kernels_f32.cu", "kernels_f64.cu",
+                  "launch.h"]
 
 
 def parse():

@@ -19,6 +19,8 @@ SOURCES = ["api.cu", "kernels_f32.cu", "kernels_f64.cu", "noalloc.cu", "xterm.cu
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ARCH + ["-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
                   "-diag-suppress", "177"]
+# extra nvcc flags for experiments (for example -DTWED_PAIRS_MIN_BLOCKS=4)
+NVFLAGS += os.environ.get("TWED_NVCC_FLAGS", "").split()
 
 
 def _nvcc() -> str:

@@ -2,6 +2,12 @@
 // Included once per precision (kernels_f32.cu, kernels_f64.cu).
 #pragma once
 
+// Resident blocks per SM the many-pairs kernel is compiled for (caps its
+// registers at 65536 / (128 x this)).
+#ifndef TWED_PAIRS_MIN_BLOCKS
+#define TWED_PAIRS_MIN_BLOCKS 1
+#endif
+
 #include "engine.cuh"
 #include "engine_f32.cuh"
 
@@ -239,7 +245,7 @@ __device__ __forceinline__ void triangle_pos(int64_t w, int64_t n, int64_t& p, i
 }
 
 template <typename T, int DIM, int P, int RMAX>
-__global__ void __launch_bounds__(128) pairs_kernel(PairsArgs<T> a) {
+__global__ void __launch_bounds__(128, TWED_PAIRS_MIN_BLOCKS) pairs_kernel(PairsArgs<T> a) {
     using V2 = typename Pair2<T>::V;
     // packed row pairs need an even number of rows per lane
     constexpr bool kEven = kStaged<T, DIM> && P == 2 && DIM >= 2;
