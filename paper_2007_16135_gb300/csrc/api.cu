@@ -758,8 +758,10 @@ twed_status_t plan_create(twed_handle_t h, const S* A, const S* B, int dim, T nu
     if (pl->xterm) {
         char r[200];
         twed::xterm_resources(r, sizeof r);
-        snprintf(d, sizeof d, "f32 tensor-core cross term (tf32) pairs=%lld blocks=%d x %d threads (%d per SM; %s)",
-                 (long long)pl->npairs, pl->blocks, threads, per_sm_raw, r);
+        snprintf(d, sizeof d,
+                 "f32 tensor-core cross term (tf32) pairs=%lld blocks=%d x %d threads "
+                 "(%d resident per SM by shared memory, registers and TMEM; occupancy query %d; %s)",
+                 (long long)pl->npairs, pl->blocks, threads, twed::xterm_resident_blocks(), per_sm_raw, r);
     }
     else
         snprintf(d, sizeof d, "%s pairs=%lld warps=%lld rows_per_lane<=%d blocks=%d x %d threads",

@@ -475,20 +475,22 @@ __device__ __forceinline__ bool run_strip(const PairRef<T>& pr, int r0, int rows
                     st_release(io.down_flag, (unsigned)j);
                 }
             }
-            if (j == m) {
-                const int rr = pr.n - r0 - lane * R;
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    if (r == rr) {
-                        if (result_a) *result_a = Dl[r];
-                        if (result_b) *result_b = Dl[r];
-                    }
-                }
-            }
         }
 #pragma unroll
         for (int q = 0; q < RL::kLen; ++q) cur[q] = nxt[q];
         __syncwarp();
+    }
+    // the lane holding row n ends its last step on column m (and no lane
+    // updates past its column m), so its final state holds D(n, m)
+    if (lane == lanes_used - 1) {
+        const int rr = pr.n - r0 - lane * R;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (r == rr) {
+                if (result_a) *result_a = Dl[r];
+                if (result_b) *result_b = Dl[r];
+            }
+        }
     }
     return true;
 }

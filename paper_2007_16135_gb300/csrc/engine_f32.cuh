@@ -314,7 +314,7 @@ __device__ __forceinline__ bool run_strip_staged(const PairRef<float>& pr, int r
                 return false;
             }
         }
-        // one basic block from here to the output test, so that the loads
+        // one basic block from here to the end of the step, so that the loads
         // and arithmetic of the next column interleave with this column's
         // chain (warps issue in order; a branch would serialise them)
         prefetch_load(j + 1);
@@ -404,28 +404,35 @@ __device__ __forceinline__ bool run_strip_staged(const PairRef<float>& pr, int r
                 if constexpr (KH) dloc4[slot_d] = make_float4(botD, botL, botC, 0.f);
                 else dloc2[slot_d] = make_float2(botD, botC);
             }
-            if (lane == 31 && act && (((j & 7) == 0) || j == m)) {
-                // progress publication (rare): global every 32 columns, block-local every 8
-                if (io.down_flag != nullptr && io.publish && (((j & 31) == 0) || j == m))
-                    st_release(io.down_flag, (unsigned)j);
-                if (io.down_local != nullptr && io.publish) {
-                    __threadfence_block();
-                    *io.down_prog = j;
-                }
-            }
-            if (j == m) {
-                const int rr = pr.n - r0 - lane * R;
-#pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    if (r == rr) {
-                        const float v = KH ? Dl[r] + Dlo[r] : Dl[r];
-                        if (result_a) *result_a = v;
-                        if (result_b) *result_b = v;
+            // progress publication (rare): global every 32 columns, block-local
+            // every 8; the outer test depends on the step only (lane 31 is on
+            // column s - 30), so it is a uniform branch taken one step in 8
+            const int j31 = s - 30;
+            if ((((j31 & 7) == 0) || j31 == m) && j31 >= 1 && j31 <= m && io.publish) {
+                if (lane == 31) {
+                    if (io.down_flag != nullptr && (((j31 & 31) == 0) || j31 == m))
+                        st_release(io.down_flag, (unsigned)j31);
+                    if (io.down_local != nullptr) {
+                        __threadfence_block();
+                        *io.down_prog = j31;
                     }
                 }
             }
         }
         __syncwarp();
+    }
+    // the lane holding row n ends its last step on column m, so its final
+    // state holds D(n, m)
+    if (lane == lanes_used - 1) {
+        const int rr = pr.n - r0 - lane * R;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (r == rr) {
+                const float v = KH ? Dl[r] + Dlo[r] : Dl[r];
+                if (result_a) *result_a = v;
+                if (result_b) *result_b = v;
+            }
+        }
     }
     cp_async_wait_all();
     __syncwarp();

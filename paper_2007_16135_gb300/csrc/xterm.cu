@@ -37,9 +37,9 @@ constexpr int M = 128;        // rows per strip (MMA M)
 constexpr int N = 16;         // columns per tile (MMA N)
 constexpr int R = 4;          // wavefront rows per lane
 constexpr int NB = 2;         // TMEM accumulators in flight
-constexpr int NBB = 4;        // B tiles in the shared-memory ring
+constexpr int NBB = 3;        // B tiles in the shared-memory ring
 constexpr int PREF = 2;       // B tiles loaded ahead of the MMA
-constexpr int NC = 6;         // cost tiles in the ring (wavefront span 3 + lead 3)
+constexpr int NC = 4;         // cost tiles in the ring (wavefront span 3 + lead 1)
 constexpr int MAXCOL = 1024;  // longest column series (boundary row kept in smem)
 constexpr int THREADS = 192;
 constexpr int TMEM_COLS = 128;  // NB*N accumulator columns + D columns of A
@@ -47,7 +47,8 @@ constexpr int ACOL = 64;        // first TMEM column of the A strip
 
 constexpr int OFF_B = 0;                               // NBB tiles of N*D floats
 constexpr int OFF_C = OFF_B + NBB * N * D * 4;         // NC tiles [N][M] costs
-constexpr int OFF_ROW = OFF_C + NC * N * M * 4;        // MAXCOL float2 boundary row
+constexpr int OFF_DEL = OFF_C + NC * N * M * 4;        // NC tiles of N column delete costs
+constexpr int OFF_ROW = OFF_DEL + NC * N * 4;          // MAXCOL float2 boundary row
 constexpr int OFF_BAR = OFF_ROW + MAXCOL * 8;          // mbarriers
 constexpr int NBAR = NB + NB + NC + NC + 1;            // mma_done, tmem_empty, cost_full, cost_empty, a_ready
 constexpr int OFF_MISC = OFF_BAR + NBAR * 8;           // tmem base, pair index
@@ -129,6 +130,7 @@ __global__ void __launch_bounds__(x64::THREADS) xterm_pairs_kernel(PairsArgs<flo
     static_assert(PREF <= 2 && PREF < NBB, "cp_async_wait_pending covers PREF <= 2");
     extern __shared__ __align__(1024) unsigned char sm[];
     float* sC = reinterpret_cast<float*>(sm + OFF_C);
+    float* sDel = reinterpret_cast<float*>(sm + OFF_DEL);
     float2* sRow = reinterpret_cast<float2*>(sm + OFF_ROW);
     uint64_t* bar = reinterpret_cast<uint64_t*>(sm + OFF_BAR);
     uint64_t* mma_done = bar;
@@ -316,6 +318,9 @@ __global__ void __launch_bounds__(x64::THREADS) xterm_pairs_kernel(PairsArgs<flo
                         const float dd = Arith<float>::root(fmaxf(d2, 0.f));
                         ct[c * M + 32 * q + lane] = fmaf(a.nu, fabsf(ti - ci.x), dd);
                     }
+                    // the tile's column delete costs, next to its costs: the
+                    // wavefront step then reads only shared memory
+                    if (q == 0 && lane < N) sDel[cb * N + lane] = __ldg(crec + min(c0 + lane, m - 1)).y;
                     __syncwarp();
                     if (lane == 0) tc::mbar_arrive(&cost_full[cb]);
                 }
@@ -352,7 +357,7 @@ __global__ void __launch_bounds__(x64::THREADS) xterm_pairs_kernel(PairsArgs<flo
                     const int jc = jn < 1 ? 1 : (jn > m ? m : jn);
                     const int cb = (jn < 1) ? cb0 : cbl;
                     c4n = *reinterpret_cast<const float4*>(sC + ((size_t)cb * N + ((jc - 1) & (N - 1))) * M + lane * R);
-                    delbn = __ldg(&crec[jc - 1].y);
+                    delbn = sDel[cb * N + ((jc - 1) & (N - 1))];
                     bndn = sRow[jc - 1];
                 };
                 {   // tile 0 must be in before the first prefetch
@@ -411,18 +416,20 @@ __global__ void __launch_bounds__(x64::THREADS) xterm_pairs_kernel(PairsArgs<flo
                         botD = Dl[R - 1];
                         botC = cp[R - 1];
                         if (!last && lane == 31 && j >= 1 && j <= m) sRow[j - 1] = make_float2(botD, botC);
-                        if (j == m) {
-                            const int rr = n - r0 - lane * R;
-#pragma unroll
-                            for (int r = 0; r < R; ++r) {
-                                if (r == rr) {
-                                    *o1 = Dl[r];
-                                    if (o2) *o2 = Dl[r];
-                                }
-                            }
-                        }
                     }
                     __syncwarp();
+                }
+                // the lane holding row n ends its last step on column m, so
+                // its final state holds D(n, m)
+                if (ok && last && lane == lanes_used - 1) {
+                    const int rr = n - r0 - lane * R;
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        if (r == rr) {
+                            *o1 = Dl[r];
+                            if (o2) *o2 = Dl[r];
+                        }
+                    }
                 }
                 // hand back the tiles not yet released
                 __syncwarp();
