@@ -61,6 +61,7 @@ def parse():
     ap.add_argument("--rows-per-lane", type=int, default=0, help="w1/w2 schedule override")
     ap.add_argument("--timeout", type=float, default=0.0, help="bound on inter-warp waits (s)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="plans: skip the schedule autotuner")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     return ap.parse_args()
@@ -211,7 +212,7 @@ def bench_plan(args, rank, world, dev, workload):
         nu, lam, p, dim = 0.5, 0.5, 2, 8
         S = w3_set(rank, args.nseries or 4096)
         SB = None
-        opts = None
+        opts = twed.make_opts(autotune=0 if args.no_autotune else 1)
         xterm = False
     else:
         nu, lam, p, dim = 1.0, 1.0, 2, 64
@@ -219,7 +220,8 @@ def bench_plan(args, rank, world, dev, workload):
         S = W.set_w4(nseries=ns, stream=0 if rank == 0 else 10 + rank).astype(np.float32)
         SB = W.set_w4(nseries=ns, stream=1 if rank == 0 else 20 + rank).astype(np.float32)
         xterm = args.xterm == "tf32"
-        opts = twed.make_opts(xterm=twed.XTERM_TF32 if xterm else twed.XTERM_OFF)
+        opts = twed.make_opts(xterm=twed.XTERM_TF32 if xterm else twed.XTERM_OFF,
+                              autotune=0 if args.no_autotune else 1)
     D = twed.DeviceSet.from_numpy(S.vals, S.ts, S.offs, torch.float32, device=dev)
     DB = twed.DeviceSet.from_numpy(SB.vals, SB.ts, SB.offs, torch.float32, device=dev) if SB is not None else None
     plan = twed.Plan(D, DB, nu, lam, p, opts=opts)

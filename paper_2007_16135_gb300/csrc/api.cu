@@ -589,6 +589,130 @@ cudaError_t plan_enqueue(twed_plan_t pl, T* out, cudaStream_t st) {
     return e;
 }
 
+// Host copy of the kernels' row-major triangle enumeration {(p, q): p < q < n}.
+void host_triangle_pos(int64_t w, int64_t n, int64_t& p, int64_t& q) {
+    int64_t r = (int64_t)((2.0 * n - 1.0 - std::sqrt((2.0 * n - 1.0) * (2.0 * n - 1.0) - 8.0 * (double)w)) * 0.5);
+    r = std::max<int64_t>(0, std::min<int64_t>(r, n - 2));
+    while (r > 0 && r * (2 * n - r - 1) / 2 > w) --r;
+    while (r < n - 2 && (r + 1) * (2 * n - r - 2) / 2 <= w) ++r;
+    p = r;
+    q = w - r * (2 * n - r - 1) / 2 + r + 1;
+}
+
+// Autotuner: times candidate schedules of this plan on a strided sample of its
+// own pairs (same length mix, about 2e10 cells) and keeps the fastest.
+// Candidates: the rows-per-lane cap (many-pairs kernel) and resident blocks
+// per SM (both kernels).  Timing: CUDA events on a private stream, one
+// warm-up and the best of two runs per candidate.
+template <typename T>
+twed_status_t autotune_plan(twed_handle_t h, twed_plan_t pl, const std::vector<int32_t>& perm_a,
+                            const std::vector<int32_t>& perm_b, const int64_t* offs_a,
+                            const int64_t* offs_b, int max_per_sm, std::string& report) {
+    PairsArgs<T>& pa = plan_pairs<T>(pl);
+    const double target = 2e10;
+    const int64_t stride = std::max<int64_t>(1, (int64_t)((double)pl->cells / target));
+    std::vector<int64_t> sample;
+    double scells = 0;
+    for (int64_t w = 0; w < pl->npairs && (int64_t)sample.size() < 2 * (1 << 21); w += stride) {
+        int64_t x, y;
+        if (pl->symmetric) {
+            int64_t pp, qq;
+            host_triangle_pos(w, pl->na, pp, qq);
+            x = perm_a[pp];
+            y = perm_a[qq];
+        } else {
+            x = perm_a[w / pl->nb];
+            y = perm_b[w % pl->nb];
+        }
+        sample.push_back(x);
+        sample.push_back(y);
+        scells += (double)(offs_a[x + 1] - offs_a[x]) * (double)(offs_b[y + 1] - offs_b[y]);
+    }
+    const int64_t ns = (int64_t)sample.size() / 2;
+    if (ns < 1) return TWED_OK;
+    void* mem = nullptr;
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaMalloc(&mem, sizeof(int64_t) * 2 * ns + sizeof(T) * ns);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(mem, sample.data(), sizeof(int64_t) * 2 * ns, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = launch_plan_records<T>(pl, plan_rec<T>(pl, 0), st);
+    if (e == cudaSuccess && !pl->symmetric) e = launch_plan_records<T>(pl, plan_rec<T>(pl, 1), st);
+    struct Cand {
+        int rmax, per_sm;
+        float ms;
+    };
+    std::vector<Cand> cands;
+    if (pl->xterm) {
+        for (int b = 1; b <= max_per_sm; ++b) cands.push_back({0, b, 0.f});
+    } else {
+        const int lim = twed::pairs_rmax_limit<T>();
+        for (int r : {2, 4, 6, 8})
+            if (r <= lim)
+                for (int b = 1; b <= max_per_sm; ++b) cands.push_back({r, b, 0.f});
+    }
+    const int64_t per_block_pairs = pl->xterm ? 1 : 4;
+    const int64_t cap_blocks = std::max<int64_t>(1, std::min<int64_t>(pl->blocks, (ns + per_block_pairs - 1) / per_block_pairs));
+    PairsArgs<T> q = pa;
+    q.mode = twed::kExplicitPairs;
+    q.pairs = (const int64_t*)mem;
+    q.npairs = ns;
+    q.out = (T*)((char*)mem + sizeof(int64_t) * 2 * ns);
+    for (Cand& c : cands) {
+        if (e != cudaSuccess) break;
+        if (!pl->xterm) q.rmax = c.rmax;
+        const int blocks = (int)std::min<int64_t>((int64_t)c.per_sm * h->sms, cap_blocks);
+        float best = 1e30f;
+        for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+            e = cudaMemsetAsync(pl->counter, 0, sizeof(unsigned long long), st);
+            if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+            if (e == cudaSuccess) {
+                if constexpr (sizeof(T) == 4) {
+                    if (pl->xterm) e = twed::launch_xterm_pairs(q, blocks, st);
+                    else e = twed::launch_pairs(q, blocks, pl->threads, st);
+                } else {
+                    e = twed::launch_pairs(q, blocks, pl->threads, st);
+                }
+            }
+            if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (rep > 0) best = std::min(best, ms);
+        }
+        c.ms = best;
+    }
+    unsigned err = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&err, pl->ctl + 1, sizeof err, cudaMemcpyDeviceToHost);
+    if (st) cudaStreamDestroy(st);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (mem) cudaFree(mem);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return cuda_fail(h, e, "autotune");
+    }
+    if (err != 0u) return fail(h, (twed_status_t)err, "autotune: a bounded wait expired");
+    const Cand* best = &cands[0];
+    for (const Cand& c : cands)
+        if (c.ms < best->ms) best = &c;
+    if (!pl->xterm) pa.rmax = best->rmax;
+    pl->blocks = (int)std::min<int64_t>((int64_t)best->per_sm * h->sms, pl->blocks);
+    char buf[160];
+    snprintf(buf, sizeof buf, "; autotuned on %lld sampled pairs (%.2e cells): rows_per_lane<=%d, %d blocks/SM, %.3f ms [",
+             (long long)ns, scells, best->rmax, best->per_sm, best->ms);
+    report = buf;
+    for (size_t i = 0; i < cands.size(); ++i) {
+        snprintf(buf, sizeof buf, "%s%d/%d:%.3f", i ? " " : "", cands[i].rmax, cands[i].per_sm, cands[i].ms);
+        report += buf;
+    }
+    report += "]";
+    return TWED_OK;
+}
+
 template <typename T, typename S>
 twed_status_t plan_create(twed_handle_t h, const S* A, const S* B, int dim, T nu, T lambda,
                           int p, const twed_opts_t* o, twed_plan_t* out_plan) {
@@ -754,6 +878,19 @@ twed_status_t plan_create(twed_handle_t h, const S* A, const S* B, int dim, T nu
         delete pl;
         return cuda_fail(h, e, "cudaStreamCreate");
     }
+    std::string tuned;
+    if (o && o->autotune) {
+        s = autotune_plan<T>(h, pl, perm_a, perm_b, A->offs_host, sym ? A->offs_host : B->offs_host,
+                             per_sm, tuned);
+        if (s != TWED_OK) {
+            cudaStreamDestroy(pl->cap);
+            cudaEventDestroy(pl->ev0);
+            cudaEventDestroy(pl->ev1);
+            cudaFree(pl->mem);
+            delete pl;
+            return s;
+        }
+    }
     char d[400];
     if (pl->xterm) {
         char r[200];
@@ -767,7 +904,7 @@ twed_status_t plan_create(twed_handle_t h, const S* A, const S* B, int dim, T nu
         snprintf(d, sizeof d, "%s pairs=%lld warps=%lld rows_per_lane<=%d blocks=%d x %d threads",
                  sizeof(T) == 8 ? "f64" : "f32", (long long)pl->npairs, (long long)nwarps, pa.rmax,
                  pl->blocks, threads);
-    pl->desc = d;
+    pl->desc = std::string(d) + tuned;
     *out_plan = pl;
     return TWED_OK;
 }

@@ -118,3 +118,23 @@ def test_w3_recipe_small_matches_oracle(tw):
     pairs = W.sample_upper_pairs(S.n, 400, 3)
     ref = oracle_matrix(S, S, 0.5, 0.5, 2, pairs)
     assert rel(M[pairs[:, 0], pairs[:, 1]], ref).max() <= 1e-5
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_autotuned_plan_matches_default_plan(tw, dtype):
+    # the autotuner only changes the schedule (rows per lane, blocks per SM):
+    # FP64 stays bit-identical, FP32 within rounding of the reordered strips
+    import torch
+    S = W.set_w3(nseries=40, len_lo=20, len_hi=700)
+    td = torch.float64 if dtype == "f64" else torch.float32
+    if dtype == "f32":
+        S = S.astype(np.float32)
+    D = tw.DeviceSet.from_numpy(S.vals, S.ts, S.offs, td)
+    base = tw.Plan(D, None, 0.5, 0.5, 2).execute().cpu().numpy()
+    tuned_plan = tw.Plan(D, None, 0.5, 0.5, 2, opts=tw.make_opts(autotune=1))
+    tuned = tuned_plan.execute().cpu().numpy()
+    assert "autotuned" in tuned_plan.describe()
+    if dtype == "f64":
+        np.testing.assert_array_equal(tuned, base)
+    else:
+        np.testing.assert_allclose(tuned, base, rtol=1e-6)
