@@ -327,6 +327,10 @@ __global__ void __launch_bounds__(x64::THREADS) xterm_pairs_kernel(PairsArgs<flo
             }
         } else {
             // ================= wavefront (warp 5)
+            // Steps run in blocks of N (= one cost tile of lane 0's columns):
+            // the tile wait and release happen once per block, so the steps in
+            // between are one stretch of code without branches.
+            static_assert((NC * N & (NC * N - 1)) == 0, "the cost ring index wraps with a mask");
             for (int st = 0; st < nstrips && ok; ++st) {
                 const int r0 = st * M + 1;  // 1-based first row of the strip
                 const int rows = min(M, n - st * M);
@@ -344,81 +348,98 @@ __global__ void __launch_bounds__(x64::THREADS) xterm_pairs_kernel(PairsArgs<flo
                 float botD = INF, botC = 0.f;
                 const long long t0 = t_dp;
                 const int cb0 = (int)(t0 % NC);  // ring slot of this strip's tile 0
-                int released = 0;  // tiles of this strip handed back
+                int released = 0;                // tiles of this strip handed back
                 const int steps = m + lanes_used - 1;
-                // pipelined like the staged engine: step s prefetches the costs,
-                // deletion cost and boundary entry of its next column
-                int cbl = cb0;  // ring slot of this lane's next (prefetched) column
+                // column jc (1-based) of this strip sits in ring column
+                // (cb0 * N + jc - 1) mod (NC * N): tiles are consecutive slots
+                const int gbase = cb0 * N;
                 float4 c4n = make_float4(0.f, 0.f, 0.f, 0.f);
                 float delbn = 0.f;
                 float2 bndn = make_float2(0.f, 0.f);
                 auto prefetch = [&](int jn) {
-                    if (jn >= 2 && jn <= m && ((jn - 1) & (N - 1)) == 0) cbl = (cbl + 1 == NC) ? 0 : cbl + 1;
                     const int jc = jn < 1 ? 1 : (jn > m ? m : jn);
-                    const int cb = (jn < 1) ? cb0 : cbl;
-                    c4n = *reinterpret_cast<const float4*>(sC + ((size_t)cb * N + ((jc - 1) & (N - 1))) * M + lane * R);
-                    delbn = sDel[cb * N + ((jc - 1) & (N - 1))];
+                    const int g = (gbase + jc - 1) & (NC * N - 1);
+                    c4n = *reinterpret_cast<const float4*>(sC + (size_t)g * M + lane * R);
+                    delbn = sDel[g];
                     bndn = sRow[jc - 1];
+                };
+                // one step: lane L on column j = s - L + 1; the next column's
+                // costs, delete cost and boundary entry are fetched during it
+                auto step = [&](int j) {
+                    const float4 c4 = c4n;
+                    const float delb = delbn;
+                    const float2 bnd = bndn;
+                    prefetch(j + 1);
+                    float upD = __shfl_up_sync(kFull, botD, 1);
+                    float upC = __shfl_up_sync(kFull, botC, 1);
+                    // a lane before column 1 sees an infinite row above and keeps its state
+                    upD = lane == 0 ? (first ? INF : bnd.x) : upD;
+                    upC = lane == 0 ? (first ? 0.f : bnd.y) : upC;
+                    upD = j < 1 ? INF : upD;
+                    const float cc[R] = {c4.x, c4.y, c4.z, c4.w};
+                    float tb_[R], tm_[R];
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        const float dg = r == 0 ? diagD : Dl[r - 1];
+                        const float cd = r == 0 ? diagC : cp[r - 1];
+                        tb_[r] = Dl[r] + delb;
+                        tm_[r] = (dg + cc[r]) + cd;
+                    }
+                    float d_up = upD;
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        d_up = min3f(d_up + rdel[r], tb_[r], tm_[r]);
+                        Dl[r] = d_up;
+                        cp[r] = cc[r];
+                    }
+                    diagD = upD;
+                    diagC = upC;
+                    botD = Dl[R - 1];
+                    botC = cp[R - 1];
+                    if (!last && lane == 31 && j >= 1 && j <= m) sRow[j - 1] = make_float2(botD, botC);
+                    __syncwarp();
+                };
+                // at step s = N k - 1 lane 0's next prefetch enters tile k, and
+                // lane 31 has read tile k - 3 for the last time
+                auto boundary = [&](int s) -> bool {
+                    const int k = (s + 1) / N;
+                    if (k < ntiles) {
+                        const long long tt = t0 + k;
+                        const bool w2 = xwait(&cost_full[(cb0 + k) % NC], (uint32_t)((tt / NC) & 1), a.sc);
+                        if (!__all_sync(kFull, w2)) return false;
+                    }
+                    const int kr = k - 3;
+                    if (kr >= 0 && kr == released && kr < ntiles) {
+                        __syncwarp();
+                        if (lane == 0) tc::mbar_arrive(&cost_empty[(cb0 + kr) % NC]);
+                        ++released;
+                    }
+                    return true;
                 };
                 {   // tile 0 must be in before the first prefetch
                     const bool w2 = xwait(&cost_full[cb0], (uint32_t)((t0 / NC) & 1), a.sc);
                     if (!__all_sync(kFull, w2)) ok = false;
                 }
-                if (ok) prefetch(1 - lane);
-                int j = 1 - lane;
-                for (int s = 0; s < steps && ok; ++s, ++j) {
-                    const float4 c4 = c4n;
-                    const float delb = delbn;
-                    const float2 bnd = bndn;
-                    // the prefetch below reads lane 0's column s+2: enter its tile now
-                    if (((s + 1) & (N - 1)) == 0 && ((s + 1) >> 4) < ntiles) {
-                        const int k = (s + 1) >> 4;
-                        const long long tt = t0 + k;
-                        const bool w2 = xwait(&cost_full[(cb0 + k) % NC], (uint32_t)((tt / NC) & 1), a.sc);
-                        if (!__all_sync(kFull, w2)) { ok = false; break; }
-                    }
-                    // lane 31 read tile k for the last time at step 16k + 45
-                    if (s >= 31 + N && ((s - 31) & (N - 1)) == 0) {
-                        const int k = (s - 31) / N - 1;
-                        if (k == released && k < ntiles) {
-                            __syncwarp();
-                            if (lane == 0) tc::mbar_arrive(&cost_empty[(cb0 + k) % NC]);
-                            ++released;
-                        }
-                    }
-                    prefetch(j + 1);
-                    float upD = __shfl_up_sync(kFull, botD, 1);
-                    float upC = __shfl_up_sync(kFull, botC, 1);
-                    // branch-free step (see the staged engine): a lane before
-                    // column 1 sees an infinite row above and keeps its state
-                    upD = lane == 0 ? (first ? INF : bnd.x) : upD;
-                    upC = lane == 0 ? (first ? 0.f : bnd.y) : upC;
-                    upD = j < 1 ? INF : upD;
-                    {
-                        const float cc[R] = {c4.x, c4.y, c4.z, c4.w};
-                        float tb_[R], tm_[R];
+                if (ok) {
+                    prefetch(1 - lane);
+                    int s = 0;
+                    const int head = min(steps, N - 1);
+                    for (; s < head; ++s) step(s - lane + 1);
+                    while (ok && s + N <= steps) {
+                        if (!boundary(s)) { ok = false; break; }
 #pragma unroll
-                        for (int r = 0; r < R; ++r) {
-                            const float dg = r == 0 ? diagD : Dl[r - 1];
-                            const float cd = r == 0 ? diagC : cp[r - 1];
-                            tb_[r] = Dl[r] + delb;
-                            tm_[r] = (dg + cc[r]) + cd;
-                        }
-                        float d_up = upD;
-#pragma unroll
-                        for (int r = 0; r < R; ++r) {
-                            d_up = min3f(d_up + rdel[r], tb_[r], tm_[r]);
-                            Dl[r] = d_up;
-                            cp[r] = cc[r];
-                        }
-                        diagD = upD;
-                        diagC = upC;
-                        botD = Dl[R - 1];
-                        botC = cp[R - 1];
-                        if (!last && lane == 31 && j >= 1 && j <= m) sRow[j - 1] = make_float2(botD, botC);
+                        for (int u = 0; u < N; ++u) step(s + u - lane + 1);
+                        s += N;
                     }
-                    __syncwarp();
+                    if (ok && s < steps) {
+                        if (!boundary(s)) ok = false;
+                        for (; ok && s < steps; ++s) step(s - lane + 1);
+                    }
                 }
+                // hand back the tiles not yet released
+                __syncwarp();
+                for (int k = released; k < ntiles; ++k)
+                    if (lane == 0) tc::mbar_arrive(&cost_empty[(cb0 + k) % NC]);
                 // the lane holding row n ends its last step on column m, so
                 // its final state holds D(n, m)
                 if (ok && last && lane == lanes_used - 1) {
@@ -431,10 +452,6 @@ __global__ void __launch_bounds__(x64::THREADS) xterm_pairs_kernel(PairsArgs<flo
                         }
                     }
                 }
-                // hand back the tiles not yet released
-                __syncwarp();
-                for (int k = released; k < ntiles; ++k)
-                    if (lane == 0) tc::mbar_arrive(&cost_empty[(cb0 + k) % NC]);
                 t_dp = t0 + ntiles;
             }
         }
