@@ -184,7 +184,7 @@ __device__ __forceinline__ bool run_strip_staged(const PairRef<float>& pr, int r
     }
     issue(0);
 
-    // The loop is software-pipelined: step s prefetches the record and the
+    // The steps are software-pipelined: step s prefetches the record and the
     // boundary entry of its next column and forms all R cell costs for it
     // (none of that depends on D), so the shared-memory loads, the distance
     // arithmetic and the square roots of step s+1 overlap the min-plus chain
@@ -271,31 +271,35 @@ __device__ __forceinline__ bool run_strip_staged(const PairRef<float>& pr, int r
     prefetch_costs();
 
     const int steps = m + lanes_used - 1;
-    int j = 1 - lane;
-    for (int s = 0; s < steps; ++s, ++j) {
-        // this step's inputs, prefetched by the previous step
-        float cc[R];
-#pragma unroll
-        for (int r = 0; r < R; ++r) cc[r] = cn[r];
-        const float delb = delbn;
-        const float4 bnd = bndn;
+
+    // Work due every 8 steps, done at steps s = 8q + 7 before that step's
+    // prefetch: publication of lane 31's progress (its last finished column,
+    // s - 31), the block-local hand-off waits, and every 32 steps the staging
+    // of the next 32-column chunk.  The 8 steps between two such points are
+    // straight-line code.
+    auto boundary = [&](int s) -> bool {
+        const int jp = s - 31;  // lane 31 finished columns 1..jp
+        if (io.publish && jp >= 1 && jp <= m && lane == 31) {
+            if (io.down_flag != nullptr && (jp & 31) == 0) st_release(io.down_flag, (unsigned)jp);
+            if (io.down_local != nullptr) {
+                __threadfence_block();
+                *io.down_prog = jp;
+            }
+        }
         if (((s + 1) & 31) == 0) {
-            // the prefetch below reads chunk (s+1)/32 (issued 32 steps ago); stage the next
+            // the prefetch of this step reads chunk (s+1)/32 (issued 32 steps ago); stage the next
             cp_async_wait_all();
             __syncwarp();
             const int c = ((s + 1) >> 5) + 1;
             if (32 * c + 1 <= m) {
                 if (up_global && io.up_flag != nullptr) {
                     const bool w = wait_progress(io.up_flag, (unsigned)min(32 * c + 32, m), sc);
-                    if (__any_sync(kFull, !w)) {
-                        cp_async_wait_all();
-                        return false;
-                    }
+                    if (__any_sync(kFull, !w)) return false;
                 }
                 issue(c);
             }
         }
-        if (((s + 1) & 7) == 0 && (io.up_local || io.down_local != nullptr)) {
+        if (io.up_local || io.down_local != nullptr) {
             // block-local hand-off, 8 columns at a time: the row above must be
             // written for lane 0's next 8 prefetches, and the warp below must
             // have consumed what lane 31's next 8 writes overwrite (ring of 128)
@@ -309,14 +313,20 @@ __device__ __forceinline__ bool run_strip_staged(const PairRef<float>& pr, int r
             }
             if (w && io.down_local != nullptr && s - 151 >= 1)
                 w = wait_local(io.down_cons, s - 151, sc);
-            if (__any_sync(kFull, !w)) {
-                cp_async_wait_all();
-                return false;
-            }
+            if (__any_sync(kFull, !w)) return false;
         }
-        // one basic block from here to the end of the step, so that the loads
-        // and arithmetic of the next column interleave with this column's
-        // chain (warps issue in order; a branch would serialise them)
+        return true;
+    };
+
+    // One step: lane L on column j = s - L + 1.  The loads and arithmetic of
+    // the next column (prefetch) interleave with this column's min-plus chain.
+    auto step = [&](int j) {
+        // this step's inputs, prefetched by the previous step
+        float cc[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) cc[r] = cn[r];
+        const float delb = delbn;
+        const float4 bnd = bndn;
         prefetch_load(j + 1);
         float upD = __shfl_up_sync(kFull, botD, 1);
         float upC = __shfl_up_sync(kFull, botC, 1);
@@ -328,98 +338,111 @@ __device__ __forceinline__ bool run_strip_staged(const PairRef<float>& pr, int r
         // a lane that has not reached column 1 sees an infinite row above: its
         // state then stays exactly at D(i, 0) = inf, so no branch is needed
         upD = j < 1 ? INF : upD;
-        {
+        if constexpr (KH) {
             // (2) the parts of each update that do not depend on the row just
             //     above in this step: deletion in b and the match candidate
-            //     (both read only the previous column)
-            if constexpr (KH) {
-                float h2[R], l2[R], v2[R];
+            float h2[R], l2[R], v2[R];
 #pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const float dh = r == 0 ? diagD : Dl[r - 1];
-                    const float dl = r == 0 ? diagL : Dlo[r - 1];
-                    const float cd = r == 0 ? diagC : cp[r - 1];
-                    float sb, eb, s3, e3, s4, e4;
-                    two_sum(Dl[r], delb, sb, eb);
-                    const float lb = Dlo[r] + eb;
-                    const float vb = sb + lb;
-                    two_sum(dh, cc[r], s3, e3);
-                    two_sum(s3, cd, s4, e4);
-                    const float lm = (dl + e3) + e4;
-                    const float vm = s4 + lm;
-                    const bool mb = vm < vb;
-                    h2[r] = mb ? s4 : sb;
-                    l2[r] = mb ? lm : lb;
-                    v2[r] = mb ? vm : vb;
-                }
-                // (3) the chain down the lane's rows: deletion in a
-                float uh = upD, ul = upL;
+            for (int r = 0; r < R; ++r) {
+                const float dh = r == 0 ? diagD : Dl[r - 1];
+                const float dl = r == 0 ? diagL : Dlo[r - 1];
+                const float cd = r == 0 ? diagC : cp[r - 1];
+                float sb, eb, s3, e3, s4, e4;
+                two_sum(Dl[r], delb, sb, eb);
+                const float lb = Dlo[r] + eb;
+                const float vb = sb + lb;
+                two_sum(dh, cc[r], s3, e3);
+                two_sum(s3, cd, s4, e4);
+                const float lm = (dl + e3) + e4;
+                const float vm = s4 + lm;
+                const bool mb = vm < vb;
+                h2[r] = mb ? s4 : sb;
+                l2[r] = mb ? lm : lb;
+                v2[r] = mb ? vm : vb;
+            }
+            // (3) the chain down the lane's rows: deletion in a
+            float uh = upD, ul = upL;
 #pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    float sa, ea;
-                    two_sum(uh, rdel[r], sa, ea);
-                    const float la = ul + ea;
-                    const float va = sa + la;
-                    const bool ma = va < v2[r];
-                    uh = ma ? sa : h2[r];
-                    ul = ma ? la : l2[r];
-                    Dl[r] = uh;
-                    Dlo[r] = ul;
-                    cp[r] = cc[r];
-                }
-            } else {
-                float tb_[R], tm_[R];
+            for (int r = 0; r < R; ++r) {
+                float sa, ea;
+                two_sum(uh, rdel[r], sa, ea);
+                const float la = ul + ea;
+                const float va = sa + la;
+                const bool ma = va < v2[r];
+                uh = ma ? sa : h2[r];
+                ul = ma ? la : l2[r];
+                Dl[r] = uh;
+                Dlo[r] = ul;
+                cp[r] = cc[r];
+            }
+        } else {
+            float tb_[R], tm_[R];
 #pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const float dg = r == 0 ? diagD : Dl[r - 1];
-                    const float cd = r == 0 ? diagC : cp[r - 1];
-                    tb_[r] = Dl[r] + delb;         // deletion in b
-                    tm_[r] = (dg + cc[r]) + cd;    // match
-                }
-                // (3) the chain down the lane's rows: deletion in a
-                float d_up = upD;
+            for (int r = 0; r < R; ++r) {
+                const float dg = r == 0 ? diagD : Dl[r - 1];
+                const float cd = r == 0 ? diagC : cp[r - 1];
+                tb_[r] = Dl[r] + delb;         // deletion in b
+                tm_[r] = (dg + cc[r]) + cd;    // match
+            }
+            // (3) the chain down the lane's rows: deletion in a
+            float d_up = upD;
 #pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    d_up = min3f(d_up + rdel[r], tb_[r], tm_[r]);
-                    Dl[r] = d_up;
-                    cp[r] = cc[r];
-                }
-            }
-            diagD = upD;
-            diagC = upC;
-            botD = Dl[R - 1];
-            botC = cp[R - 1];
-            if constexpr (KH) {
-                diagL = upL;
-                botL = Dlo[R - 1];
-            }
-            prefetch_costs();
-            const bool act = (j >= 1 && j <= m);
-            if (io.down != nullptr && lane == 31 && act) {
-                if constexpr (KH) __stcg(down4 + (j - 1), make_float4(botD, botL, botC, 0.f));
-                else __stcg(io.down + (j - 1), make_float2(botD, botC));
-            }
-            if (io.down_local != nullptr && lane == 31 && act) {
-                const int slot_d = (j - 1) & (kRingCols - 1);
-                if constexpr (KH) dloc4[slot_d] = make_float4(botD, botL, botC, 0.f);
-                else dloc2[slot_d] = make_float2(botD, botC);
-            }
-            // progress publication (rare): global every 32 columns, block-local
-            // every 8; the outer test depends on the step only (lane 31 is on
-            // column s - 30), so it is a uniform branch taken one step in 8
-            const int j31 = s - 30;
-            if ((((j31 & 7) == 0) || j31 == m) && j31 >= 1 && j31 <= m && io.publish) {
-                if (lane == 31) {
-                    if (io.down_flag != nullptr && (((j31 & 31) == 0) || j31 == m))
-                        st_release(io.down_flag, (unsigned)j31);
-                    if (io.down_local != nullptr) {
-                        __threadfence_block();
-                        *io.down_prog = j31;
-                    }
-                }
+            for (int r = 0; r < R; ++r) {
+                d_up = min3f(d_up + rdel[r], tb_[r], tm_[r]);
+                Dl[r] = d_up;
+                cp[r] = cc[r];
             }
         }
+        diagD = upD;
+        diagC = upC;
+        botD = Dl[R - 1];
+        botC = cp[R - 1];
+        if constexpr (KH) {
+            diagL = upL;
+            botL = Dlo[R - 1];
+        }
+        prefetch_costs();
+        const bool act = (j >= 1 && j <= m);
+        if (io.down != nullptr && lane == 31 && act) {
+            if constexpr (KH) __stcg(down4 + (j - 1), make_float4(botD, botL, botC, 0.f));
+            else __stcg(io.down + (j - 1), make_float2(botD, botC));
+        }
+        if (io.down_local != nullptr && lane == 31 && act) {
+            const int slot_d = (j - 1) & (kRingCols - 1);
+            if constexpr (KH) dloc4[slot_d] = make_float4(botD, botL, botC, 0.f);
+            else dloc2[slot_d] = make_float2(botD, botC);
+        }
         __syncwarp();
+    };
+
+    int s = 0;
+    const int head = min(steps, 7);
+    for (; s < head; ++s) step(s - lane + 1);
+    bool ok = true;
+    while (s + 8 <= steps) {
+        if (!boundary(s)) {
+            ok = false;
+            break;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) step(s + u - lane + 1);
+        s += 8;
+    }
+    if (ok && s < steps) {
+        ok = boundary(s);
+        for (; ok && s < steps; ++s) step(s - lane + 1);
+    }
+    if (!ok) {
+        cp_async_wait_all();
+        return false;
+    }
+    // lane 31 ends on column m when all 32 lanes hold rows: publish it
+    if (io.publish && lanes_used == 32 && lane == 31) {
+        if (io.down_flag != nullptr) st_release(io.down_flag, (unsigned)m);
+        if (io.down_local != nullptr) {
+            __threadfence_block();
+            *io.down_prog = m;
+        }
     }
     // the lane holding row n ends its last step on column m, so its final
     // state holds D(n, m)
