@@ -237,6 +237,33 @@ PairLayout pair_layout(twed_handle_t h, int64_t n, int64_t m, int dim, int p,
     return L;
 }
 
+// Launch the one-pair schedule chosen in L (band kernel for FP32 compiled
+// layouts, else the cooperative strip kernel) for the pair described by ca.
+template <typename T>
+twed_status_t launch_pair_schedule(twed_handle_t h, const PairLayout& L, const CoopArgs<T>& ca,
+                                   cudaStream_t st) {
+    const int R = L.R;
+    if constexpr (sizeof(T) == 4) {
+        if (L.band) {
+            const int bw = h->band_warps;
+            const int per_sm = std::max(1, twed::band_blocks_per_sm(ca.dim, ca.p, R, L.kahan, bw));
+            const int64_t nbands = (L.nstrips + bw - 1) / bw;
+            const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(nbands, (int64_t)per_sm * h->sms));
+            const cudaError_t e = twed::launch_band(ca, R, L.kahan, (int)blocks, bw, st);
+            if (e != cudaSuccess)
+                return fail(h, TWED_ERR_CUDA, "band launch (dim %d, p %d, R %d, kahan %d, blocks %lld, per_sm %d): %s",
+                            ca.dim, ca.p, R, (int)L.kahan, (long long)blocks, per_sm, cudaGetErrorString(e));
+            return TWED_OK;
+        }
+    }
+    const int threads = 128;
+    const int per_sm = std::max(1, twed::coop_blocks_per_sm<T>(ca.dim, ca.p, R, L.kahan, threads));
+    int64_t blocks = std::min<int64_t>((L.nstrips + 3) / 4, (int64_t)per_sm * h->sms);
+    blocks = std::max<int64_t>(1, blocks);
+    TWED_CUDA(h, twed::launch_coop(ca, R, L.kahan, (int)blocks, threads, st));
+    return TWED_OK;
+}
+
 // Enqueue one pair on `st` with all inputs already on the device.
 template <typename T>
 twed_status_t run_pair_dev(twed_handle_t h, const T* a, const T* ta, int64_t la, const T* b,
@@ -293,25 +320,7 @@ twed_status_t run_pair_dev(twed_handle_t h, const T* a, const T* ta, int64_t la,
     ca.strip_counter = flags + nstrips;
     ca.out = d_out;
     ca.sc = make_sync(h, o);
-    if constexpr (sizeof(T) == 4) {
-        if (L.band) {
-            const int bw = h->band_warps;
-            const int per_sm = std::max(1, twed::band_blocks_per_sm(dim, p, R, L.kahan, bw));
-            const int64_t nbands = (nstrips + bw - 1) / bw;
-            const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(nbands, (int64_t)per_sm * h->sms));
-            const cudaError_t e = twed::launch_band(ca, R, L.kahan, (int)blocks, bw, st);
-            if (e != cudaSuccess)
-                return fail(h, TWED_ERR_CUDA, "band launch (dim %d, p %d, R %d, kahan %d, blocks %lld, per_sm %d): %s",
-                            dim, p, R, (int)L.kahan, (long long)blocks, per_sm, cudaGetErrorString(e));
-            return TWED_OK;
-        }
-    }
-    const int threads = 128;
-    const int per_sm = std::max(1, twed::coop_blocks_per_sm<T>(dim, p, R, L.kahan, threads));
-    int64_t blocks = std::min<int64_t>((nstrips + 3) / 4, (int64_t)per_sm * h->sms);
-    blocks = std::max<int64_t>(1, blocks);
-    TWED_CUDA(h, twed::launch_coop(ca, R, L.kahan, (int)blocks, threads, st));
-    return TWED_OK;
+    return launch_pair_schedule<T>(h, L, ca, st);
 }
 
 // Host-pointer pair: copy in, run, copy out, report wait timeouts.
@@ -535,6 +544,20 @@ struct twed_plan_s {
     bool xterm = false;  // tensor-core cross-term kernel (dim 64, FP32)
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around the pairs launch
     std::string desc;
+    // pairs above the cut-over run one at a time on the one-pair schedule;
+    // rows = the longer series, from set B when r_is_b
+    struct LongPair {
+        int64_t rfirst, cfirst;  // first point of the row / column series
+        int n, m;
+        bool r_is_b;
+        int64_t o1, o2;  // output elements (o2 < 0: none)
+    };
+    std::vector<LongPair> longp;
+    int dim = 0, p = 2;
+    bool has_opts = false;
+    twed_opts_t opts{};
+    void* band_ws = nullptr;
+    size_t band_ring_bytes = 0;
 };
 
 namespace {
@@ -585,6 +608,38 @@ cudaError_t plan_enqueue(twed_plan_t pl, T* out, cudaStream_t st) {
     if (e == cudaSuccess) e = cudaEventRecordWithFlags(pl->ev0, st, evflag);
     if (e == cudaSuccess) e = launch_plan_pairs<T>(pl, pa, st);
     if (e == cudaSuccess) e = cudaEventRecordWithFlags(pl->ev1, st, evflag);
+    for (size_t i = 0; i < pl->longp.size() && e == cudaSuccess; ++i) {
+        const auto& lp = pl->longp[i];
+        const twed_opts_t* o = pl->has_opts ? &pl->opts : nullptr;
+        const PairLayout L = pair_layout<T>(pl->h, lp.n, lp.m, pl->dim, pl->p, o, 0);
+        const int rl = twed::rec_len<T>(pl->dim, pl->p);
+        unsigned* flags = (unsigned*)((char*)pl->band_ws + pl->band_ring_bytes);
+        e = cudaMemsetAsync(flags, 0, sizeof(unsigned) * (size_t)(L.nstrips + 1), st);
+        if (e != cudaSuccess) break;
+        CoopArgs<T> ca;
+        ca.rec_a = (lp.r_is_b ? pa.rec_b : pa.rec_a) + lp.rfirst * rl;
+        ca.rec_b = (lp.r_is_b ? pa.rec_a : pa.rec_b) + lp.cfirst * rl;
+        ca.vals_a = (lp.r_is_b ? pa.vals_b : pa.vals_a) + lp.rfirst * pl->dim;
+        ca.vals_b = (lp.r_is_b ? pa.vals_a : pa.vals_b) + lp.cfirst * pl->dim;
+        ca.n = lp.n;
+        ca.m = lp.m;
+        ca.dim = pl->dim;
+        ca.p = pl->p;
+        ca.nu = pa.nu;
+        ca.nstrips = L.nstrips;
+        ca.ring = pl->band_ws;
+        ca.nslot = kRingSlots;
+        ca.ring_stride = L.ring_stride;
+        ca.flags = flags;
+        ca.strip_counter = flags + L.nstrips;
+        ca.out = out + lp.o1;
+        ca.sc = pa.sc;
+        if (launch_pair_schedule<T>(pl->h, L, ca, st) != TWED_OK) {
+            e = cudaErrorLaunchFailure;
+            break;
+        }
+        if (lp.o2 >= 0) e = cudaMemcpyAsync(out + lp.o2, out + lp.o1, sizeof(T), cudaMemcpyDeviceToDevice, st);
+    }
     if (e == cudaSuccess && pl->symmetric) e = twed::launch_zero_diag(out, pl->f64, pl->na, st);
     return e;
 }
@@ -869,6 +924,75 @@ twed_status_t plan_create(twed_handle_t h, const S* A, const S* B, int dim, T nu
     pa.sc.stall_strip = -1;
     pa.sc.sleep_ns = h->sleep_ns;
 
+    // Schedule cut-over: a pair with more cells than the plan's average work
+    // per warp would leave one warp running long after the others finish;
+    // such pairs (at most kMaxLongPairs, else the load is balanced anyway)
+    // run one at a time on the one-pair block-cooperative schedule.
+    pl->dim = dim;
+    pl->p = p;
+    if (o) {
+        pl->has_opts = true;
+        pl->opts = *o;
+    }
+    if (!pl->xterm && nwarps > 0) {
+        constexpr size_t kMaxLongPairs = 4096;
+        const int64_t cut = std::max<int64_t>(1, cells / nwarps);
+        const int64_t* oa = A->offs_host;
+        const int64_t* ob = sym ? A->offs_host : B->offs_host;
+        auto lena = [&](int64_t r) { const int64_t x = perm_a[r]; return oa[x + 1] - oa[x]; };
+        auto lenb = [&](int64_t r) { const int64_t y = sym ? perm_a[r] : perm_b[r]; return ob[y + 1] - ob[y]; };
+        bool too_many = false;
+        auto add = [&](int64_t x, int64_t y, int64_t o1, int64_t o2) {
+            if (pl->longp.size() >= kMaxLongPairs) {
+                too_many = true;
+                return;
+            }
+            const int64_t lx = oa[x + 1] - oa[x], ly = ob[y + 1] - ob[y];
+            twed_plan_s::LongPair lp;
+            lp.r_is_b = ly > lx;  // rows = the longer series
+            lp.rfirst = lp.r_is_b ? ob[y] : oa[x];
+            lp.cfirst = lp.r_is_b ? oa[x] : ob[y];
+            lp.n = (int)std::max(lx, ly);
+            lp.m = (int)std::min(lx, ly);
+            lp.o1 = o1;
+            lp.o2 = o2;
+            pl->longp.push_back(lp);
+        };
+        const int64_t nb_ = sym ? A->n : B->n;
+        for (int64_t pp = 0; pp < A->n && !too_many; ++pp) {
+            const int64_t lp_ = lena(pp);
+            const int64_t q0 = sym ? pp + 1 : 0;
+            if (q0 >= nb_ || lp_ * lenb(q0) <= cut) {
+                if (sym || lp_ * lenb(0) <= cut) break;
+                continue;
+            }
+            for (int64_t qq = q0; qq < nb_ && !too_many; ++qq) {
+                if (lp_ * lenb(qq) <= cut) break;
+                const int64_t x = perm_a[pp], y = sym ? perm_a[qq] : perm_b[qq];
+                if (sym) add(x, y, x * A->n + y, y * A->n + x);
+                else add(x, y, x * nb_ + y, -1);
+            }
+        }
+        if (too_many) pl->longp.clear();
+        if (!pl->longp.empty()) {
+            size_t ring = 0, flags = 0;
+            for (const auto& lp : pl->longp) {
+                const PairLayout L = pair_layout<T>(h, lp.n, lp.m, dim, p, o, 0);
+                ring = std::max(ring, L.o_flags - L.o_ring);
+                flags = std::max(flags, L.end - L.o_flags);
+            }
+            pl->band_ring_bytes = align_up(ring);
+            e = cudaMalloc(&pl->band_ws, pl->band_ring_bytes + flags);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                cudaFree(pl->mem);
+                delete pl;
+                return fail(h, TWED_ERR_ALLOC, "plan cut-over workspace: %s", cudaGetErrorString(e));
+            }
+            pa.cut_cells = cut;
+        }
+    }
+
     e = cudaStreamCreateWithFlags(&pl->cap, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreate(&pl->ev0);
     if (e == cudaSuccess) e = cudaEventCreate(&pl->ev1);
@@ -886,6 +1010,7 @@ twed_status_t plan_create(twed_handle_t h, const S* A, const S* B, int dim, T nu
             cudaStreamDestroy(pl->cap);
             cudaEventDestroy(pl->ev0);
             cudaEventDestroy(pl->ev1);
+            if (pl->band_ws) cudaFree(pl->band_ws);
             cudaFree(pl->mem);
             delete pl;
             return s;
@@ -905,6 +1030,12 @@ twed_status_t plan_create(twed_handle_t h, const S* A, const S* B, int dim, T nu
                  sizeof(T) == 8 ? "f64" : "f32", (long long)pl->npairs, (long long)nwarps, pa.rmax,
                  pl->blocks, threads);
     pl->desc = std::string(d) + tuned;
+    if (!pl->longp.empty()) {
+        char c[160];
+        snprintf(c, sizeof c, "; cut-over: %zu pairs above %lld cells on the one-pair schedule",
+                 pl->longp.size(), (long long)pa.cut_cells);
+        pl->desc += c;
+    }
     *out_plan = pl;
     return TWED_OK;
 }
@@ -982,6 +1113,7 @@ extern "C" void twed_plan_destroy(twed_plan_t pl) {
     if (pl->ev0) cudaEventDestroy(pl->ev0);
     if (pl->ev1) cudaEventDestroy(pl->ev1);
     cudaDeviceSynchronize();
+    if (pl->band_ws) cudaFree(pl->band_ws);
     if (pl->mem) cudaFree(pl->mem);
     delete pl;
 }

@@ -281,6 +281,9 @@ __global__ void __launch_bounds__(128, TWED_PAIRS_MIN_BLOCKS) pairs_kernel(Pairs
         }
         const int64_t xa = a.offs_a[x], nx = a.offs_a[x + 1] - xa;
         const int64_t yb = a.offs_b[y], ny = a.offs_b[y + 1] - yb;
+        // a pair far larger than a warp's share of the work runs on the
+        // block-cooperative schedule instead (the plan enqueues it)
+        if (a.cut_cells > 0 && nx * ny > a.cut_cells) continue;
         // rows = the shorter series (fewer strips), columns = the longer one;
         // TWED is symmetric, and the swapped evaluation performs the mirrored
         // operations, so the value is the same bit for bit.

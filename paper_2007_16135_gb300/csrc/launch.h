@@ -73,6 +73,7 @@ struct PairsArgs {
     void* scratch;           // per warp: one boundary row of `scratch_cols` (D, c) pairs
     int64_t scratch_cols;    // >= longest series + 1, even
     SyncCtl sc;
+    int64_t cut_cells = 0;   // > 0: pairs with more cells are skipped (run elsewhere)
 };
 
 // Elements per point record for (dim, p) (16-byte multiple; see Rec<>).

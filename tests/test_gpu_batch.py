@@ -138,3 +138,42 @@ def test_autotuned_plan_matches_default_plan(tw, dtype):
         np.testing.assert_array_equal(tuned, base)
     else:
         np.testing.assert_allclose(tuned, base, rtol=1e-6)
+
+
+def _mixed_set(seed, nshort, nlong, dim=3):
+    rng = np.random.default_rng(seed)
+    lens = list(rng.integers(20, 80, size=nshort)) + list(rng.integers(3000, 4000, size=nlong))
+    rng.shuffle(lens)
+    series = [(np.cumsum(rng.normal(size=(n, dim)), axis=0), np.cumsum(rng.exponential(1.0, n)))
+              for n in lens]
+    return W.pack(series)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_plan_cutover_for_long_pairs(tw, dtype):
+    # a few long series among short ones: their pairs exceed a warp's share of
+    # the plan and run on the one-pair block-cooperative schedule
+    import torch
+    S = _mixed_set(21, 46, 4)
+    SB = _mixed_set(22, 20, 3)
+    td = torch.float64 if dtype == "f64" else torch.float32
+    if dtype == "f32":
+        S, SB = S.astype(np.float32), SB.astype(np.float32)
+    for B in (None, SB):
+        D = tw.DeviceSet.from_numpy(S.vals, S.ts, S.offs, td)
+        DB = None if B is None else tw.DeviceSet.from_numpy(B.vals, B.ts, B.offs, td)
+        plan = tw.Plan(D, DB, 0.3, 0.7, 2)
+        assert "cut-over" in plan.describe(), plan.describe()
+        M = plan.execute().cpu().numpy()
+        Bo = S if B is None else B
+        pairs = np.array([(i, j) for i in range(S.n) for j in range(Bo.n) if B is not None or i < j])
+        want = oracle.twed_pairs(S.astype(np.float64).as_tuple(), Bo.astype(np.float64).as_tuple(),
+                                 pairs, 0.3, 0.7, 2)
+        got = M[pairs[:, 0], pairs[:, 1]].astype(np.float64)
+        if dtype == "f64":
+            np.testing.assert_array_equal(got, want)
+        else:
+            np.testing.assert_allclose(got, want, rtol=1e-5)
+        if B is None:
+            assert np.all(M == M.T) and np.all(np.diag(M) == 0)
+        plan.close()

@@ -8,6 +8,11 @@
   tests/golden/make_w2_expected.py, which calls only the oracle.
 * w3 (4096 series, dim 8, all 8.4M pairs in one plan execute): 300 sampled
   pairs against the oracle, plus symmetry and the zero diagonal.
+* w5 (1e5-series database, 1000 queries, the bench's training and search
+  configuration): the exact batched k-NN's distances against the oracle on
+  sampled (query, result) pairs, the filtered search's recall@10 at 1600
+  candidates against that exact k-NN, and its returned distances against
+  the oracle on sampled pairs.
 """
 import json
 import os
@@ -86,3 +91,38 @@ def test_w3_full_size_sampled(tw):
     sub = M[idx][:, idx]
     assert torch.equal(sub, sub.T)
     assert torch.all(torch.diagonal(M) == 0)
+
+
+def test_w5_full_size_knn(tw):
+    import torch
+    db = W.set_w5(100_000, stream=1).astype(np.float32)
+    qs = W.set_w5(1000, stream=0).astype(np.float32)
+    D = tw.DeviceSet.from_numpy(db.vals, db.ts, db.offs, torch.float32)
+    Q = tw.DeviceSet.from_numpy(qs.vals, qs.ts, qs.offs, torch.float32)
+    index = tw.KnnIndex(D, 1.0, 1.0, 2, config=tw.knn_config())
+    index.train()
+    ex_idx, ex_dist = index.exact(Q, k=10)
+    idx, dist = index.search(Q, k=10, n_candidates=1600)
+    torch.cuda.synchronize()
+    ex_idx, ex_dist = ex_idx.cpu().numpy(), ex_dist.cpu().numpy()
+    idx, dist = idx.cpu().numpy(), dist.cpu().numpy()
+    kth = ex_dist[:, 9]
+    recall = np.minimum((dist <= kth[:, None]).sum(axis=1), 10).mean() / 10
+    assert recall >= 0.99, recall
+    # sampled distances of both paths against the oracle
+    rng = np.random.default_rng(55)
+    qsel = rng.choice(qs.n, size=12, replace=False)
+    pairs, got = [], []
+    for q in qsel:
+        for r in (0, 9):
+            pairs.append((q, ex_idx[q, r]))
+            got.append(ex_dist[q, r])
+            pairs.append((q, idx[q, r]))
+            got.append(dist[q, r])
+    want = oracle.twed_pairs(qs.astype(np.float64).as_tuple(), db.astype(np.float64).as_tuple(),
+                             np.array(pairs, dtype=np.int64), 1.0, 1.0, 2)
+    rel = np.abs(np.array(got, dtype=np.float64) - want) / want
+    assert rel.max() <= 1e-5, rel.max()
+    # the exact path's top-10 are no worse than the filtered ones, rank by rank
+    assert np.all(ex_dist <= dist * (1 + 1e-6))
+    index.close()
