@@ -10,17 +10,20 @@
 // same as everywhere else in this library.
 //
 // One persistent block handles one pair at a time (pairs from an atomic
-// counter, longest series first); three blocks share an SM.  Warp roles:
-//   warp 0      producer: cp.async of the column tiles (B) into a 4-deep
+// counter, longest series first); four blocks share an SM (shared memory
+// 54 KB and 128 TMEM columns each).  Warp roles:
+//   warp 0      producer: cp.async of the column tiles (B) into a 3-deep
 //               shared-memory ring in the K-major core-matrix layout, two
 //               tiles ahead; tcgen05.mma issue (A from tensor memory),
 //               tcgen05.commit to an mbarrier.  Also owns the TMEM.
 //   warps 1..4  epilogue: at each strip, load the strip's 128 points (one
 //               per thread) into tensor memory with tcgen05.st (A operand);
 //               per tile, tcgen05.ld of their TMEM lane quarter, cost
-//               formation, store into a ring of cost tiles [col][row].
+//               formation, store into a 4-tile ring of cost tiles [col][row]
+//               with the tile's column delete costs beside it.
 //   warp 5      wavefront: 32 lanes x 4 rows = the strip's 128 rows, lane L
-//               on column s - L at step s, costs read from the ring.
+//               on column s - L at step s, costs read from the ring, in
+//               branch-free blocks of 16 steps (one tile of lane 0).
 // Every wait is bounded (%globaltimer, then the launch's error word).
 #include <cuda_runtime.h>
 
