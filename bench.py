@@ -35,6 +35,7 @@ METRIC = "TWED GCUPS on 1 GB300; k-NN queries/s at recall@10>=0.99 vs exact batc
 UNIT = "GCUPS"
 FALLBACK_SM_MAX_MHZ = 2070.0
 FP32_LANES_PER_SM = 128  # FADD/FMUL/FFMA lanes per SM per clock
+FP64_LANES_PER_SM = 2    # DFMA lanes per SM per clock on GB300
 KERNEL_SOURCES = ["engine.cuh", "engine_f32.cuh", "kernels.cuh", "kernels_f32.cu", "kernels_f64.cu",
                   "launch.h"]
 
@@ -45,7 +46,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["w3", "w4", "w2", "w1", "w5"], default="w3")
+    ap.add_argument("--workload", choices=["w3", "w4", "w2", "w1", "w5", "u1", "u2"], default="w3")
     ap.add_argument("--no-knn", action="store_true", help="w3: skip the appended w5 result")
     ap.add_argument("--knn-epochs", type=int, default=40)
     ap.add_argument("--knn-pairs", type=int, default=1_000_000)
@@ -208,9 +209,23 @@ def bench_plan(args, rank, world, dev, workload):
     from paper_2007_16135_gb300 import twed
     from paper_2007_16135_gb300 import workloads as W
 
+    dtype = "f32"
     if workload == "w3":
         nu, lam, p, dim = 0.5, 0.5, 2, 8
         S = w3_set(rank, args.nseries or 4096)
+        SB = None
+        opts = twed.make_opts(autotune=0 if args.no_autotune else 1)
+        xterm = False
+    elif workload in ("u1", "u2"):
+        # the shapes of the paper's 1-D validation sets; FP64 like its table
+        nu, lam, p, dim = 1.0, 1.0, 2, 1
+        dtype = args.dtype or "f64"
+        if workload == "u1":
+            S = W.set_u1(nseries=args.nseries or 600, stream=rank)
+        else:
+            S = W.set_u2(nseries=args.nseries or 10, length=args.n or 100_000, stream=rank)
+        if dtype == "f32":
+            S = S.astype(np.float32)
         SB = None
         opts = twed.make_opts(autotune=0 if args.no_autotune else 1)
         xterm = False
@@ -222,8 +237,9 @@ def bench_plan(args, rank, world, dev, workload):
         xterm = args.xterm == "tf32"
         opts = twed.make_opts(xterm=twed.XTERM_TF32 if xterm else twed.XTERM_OFF,
                               autotune=0 if args.no_autotune else 1)
-    D = twed.DeviceSet.from_numpy(S.vals, S.ts, S.offs, torch.float32, device=dev)
-    DB = twed.DeviceSet.from_numpy(SB.vals, SB.ts, SB.offs, torch.float32, device=dev) if SB is not None else None
+    td = torch.float64 if dtype == "f64" else torch.float32
+    D = twed.DeviceSet.from_numpy(S.vals, S.ts, S.offs, td, device=dev)
+    DB = twed.DeviceSet.from_numpy(SB.vals, SB.ts, SB.offs, td, device=dev) if SB is not None else None
     plan = twed.Plan(D, DB, nu, lam, p, opts=opts)
     out = plan.new_output()
     cells = plan.cells
@@ -264,6 +280,12 @@ def bench_plan(args, rank, world, dev, workload):
     peak_ops = props.multi_processor_count * FP32_LANES_PER_SM * sm_max * 1e6
     opc = 7 if xterm else ops_per_cell(dim, p)
     kern_s = res["kernel_ms"] / 1e3
+    if workload in ("u1", "u2"):
+        # pairs above the cut-over run after the timed persistent launch:
+        # use the whole step, and the FP64 pipe for FP64
+        kern_s = ms_step / 1e3
+        if dtype == "f64":
+            peak_ops = props.multi_processor_count * FP64_LANES_PER_SM * sm_max * 1e6
     achieved = cells * opc / kern_s
     traffic = None
     tp = os.path.join(ROOT, "profiles", f"pairs_kernel_{workload}_traffic.json")
@@ -273,13 +295,17 @@ def bench_plan(args, rank, world, dev, workload):
         if tj.get("src_hash") == kernel_src_hash():
             traffic = tj.get("dram_bytes_per_launch")
     kname = "xterm_pairs_kernel (tcgen05 tf32)" if xterm else f"pairs_kernel<float,{dim if dim in (1,2,3,4,8) else 0},2,8>"
+    lanes = FP64_LANES_PER_SM if dtype == "f64" else FP32_LANES_PER_SM
+    if workload in ("u1", "u2"):
+        kname = f"whole step ({'double' if dtype == 'f64' else 'float'}; pairs kernel + one-pair schedule)"
     res["roofline"] = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak_ops / 1e12,
                        "unit": "Top/s", "frac": achieved / peak_ops, "traffic": traffic,
                        "ops_per_cell": opc, "peak_basis":
-                           f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
+                           f"{props.multi_processor_count} SMs x {lanes} "
+                           f"{'FP64' if dtype == 'f64' else 'FP32'} lanes x "
                            f"{sm_max:.0f} MHz (max SM clock)",
                        "kernel": kname}
-    mp = ffma_peak()
+    mp = twed.pipe_peak(twed.PEAK_DFMA64) if dtype == "f64" else ffma_peak()
     res["roofline"]["peak_measured"] = mp / 1e12
     res["roofline"]["frac_of_measured"] = achieved / mp
     if xterm:
@@ -315,21 +341,55 @@ def bench_plan(args, rank, world, dev, workload):
         if workload == "w3":
             pairs = W.sample_upper_pairs(S.n, min(20000, S.n * (S.n - 1) // 2), 3)
             SBo = S
+        elif workload == "u1":
+            pairs = W.sample_upper_pairs(S.n, min(20000, S.n * (S.n - 1) // 2), 6)
+            SBo = S
+        elif workload == "u2":
+            pairs = None
         else:
             pairs = W.sample_block_pairs(S.n, SB.n, 2000, 4)
             SBo = SB
-        cpu, done_pairs, ref = run_cpu_baseline(S, pairs, args.cpu_seconds, nu, lam, p, SBo)
-        got = M[done_pairs[:, 0], done_pairs[:, 1]].astype(np.float64)
-        relerr = np.abs(got - ref) / np.maximum(np.abs(ref), 1e-300)
-        res["cpu_baseline"] = cpu
-        res["error_vs_oracle"] = {"max_rel": float(relerr.max()), "mean_rel": float(relerr.mean()),
-                                  "pairs": int(len(done_pairs)),
-                                  "bound": 2e-3 if xterm else 1e-5}
+        if pairs is None:
+            # u2: 1e10-cell pairs; the oracle runs the first 20,000 points of
+            # series 0 and 1 (a bounded slice of the same data)
+            import oracle
+            cut = min(20000, int(S.lengths[0]), int(S.lengths[1]))
+            v0, t0_ = S.series(0)
+            v1, t1_ = S.series(1)
+            t0c = time.perf_counter()
+            oracle.twed_rolling(v0[:cut].astype(np.float64), t0_[:cut].astype(np.float64),
+                                v1[:cut].astype(np.float64), t1_[:cut].astype(np.float64), nu, lam, p)
+            el = time.perf_counter() - t0c
+            res["cpu_baseline"] = {"value": cut * cut / el / 1e9, "unit": UNIT, "cores": 1,
+                                   "kind": "oracle",
+                                   "sample": f"rolling-row FP64 oracle on the first {cut} points of "
+                                             f"series 0 and 1 ({cut * cut:.2e} cells, {el:.1f} s, one core)"}
+        else:
+            cpu, done_pairs, ref = run_cpu_baseline(S, pairs, args.cpu_seconds, nu, lam, p, SBo)
+            got = M[done_pairs[:, 0], done_pairs[:, 1]].astype(np.float64)
+            relerr = np.abs(got - ref) / np.maximum(np.abs(ref), 1e-300)
+            res["cpu_baseline"] = cpu
+            res["error_vs_oracle"] = {"max_rel": float(relerr.max()), "mean_rel": float(relerr.mean()),
+                                      "pairs": int(len(done_pairs)),
+                                      "bound": 2e-3 if xterm else (1e-12 if dtype == "f64" else 1e-5)}
     if workload == "w3":
         res["config"] = {"workload": f"w3 all-pairs: {S.n} series, dim 8, len U[64,2048], sinusoid "
                                      "mixtures + N(0,0.1), t_i=i, nu=lambda=0.5, p=2, FP32",
                          "pairs": plan.pairs, "cells": cells, "series": S.n, "dim": 8,
                          "l2": "inputs larger than L2 (point records 208 MB > 126 MB L2)",
+                         "parallelism": f"{world} independent replica(s)"}
+    elif workload == "u1":
+        res["config"] = {"workload": f"u1 all-pairs: {S.n} 1-D series of 60 points in six pattern classes "
+                                     "(the shape of the paper's first validation set), t_i=i, nu=lambda=1, "
+                                     f"p=2, {dtype.upper()}", "pairs": plan.pairs, "cells": cells,
+                         "series": S.n, "dim": 1, "l2": "inputs fit in L2 (small workload)",
+                         "parallelism": f"{world} independent replica(s)"}
+    elif workload == "u2":
+        res["config"] = {"workload": f"u2 all-pairs: {S.n} 1-D series of {int(S.lengths[0])} points, drifting "
+                                     "pseudo-periodic (the shape of the paper's second validation set), "
+                                     f"t_i=i, nu=lambda=1, p=2, {dtype.upper()}", "pairs": plan.pairs,
+                         "cells": cells, "series": S.n, "dim": 1,
+                         "l2": "each pair streams its 1e5-point series from L2",
                          "parallelism": f"{world} independent replica(s)"}
     else:
         res["config"] = {"workload": f"w4 block: {S.n} x {SB.n} series, dim 64, len U[256,1024], "
@@ -339,7 +399,7 @@ def bench_plan(args, rank, world, dev, workload):
                          "pairs": plan.pairs, "cells": cells, "series": [S.n, SB.n], "dim": 64,
                          "l2": "series values 2 x 336 MB > 126 MB L2",
                          "parallelism": f"{world} independent replica(s)"}
-    res["dtype"] = "f32" if not xterm else "tf32xf32"
+    res["dtype"] = dtype if not xterm else "tf32xf32"
     return res
 
 
@@ -387,13 +447,28 @@ def bench_pair(args, rank, world, dev, workload):
     res = {"ms_per_step": ms, "value": cells * world / (ms / 1e3) / 1e9, "clocks": clk.summary(),
            "cells_per_step": cells, "dtype": dtype, "gpu_launches": 3 * args.steps,
            "result": float(out.item())}
+    opc = ops_per_cell(dim, p)
     if dtype == "f32":
         peak = props.multi_processor_count * FP32_LANES_PER_SM * sm_max * 1e6
-        opc = ops_per_cell(dim, p)
+        mp = ffma_peak()
         res["roofline"] = {"bound": "alu", "achieved": cells * opc / (ms / 1e3) / 1e12,
                            "peak": peak / 1e12, "unit": "Top/s",
                            "frac": cells * opc / (ms / 1e3) / peak, "traffic": None,
-                           "ops_per_cell": opc, "kernel": f"coop_kernel<float,{dim},2,R>"}
+                           "ops_per_cell": opc, "kernel": f"band_kernel<{dim},2,R>",
+                           "peak_measured": mp / 1e12,
+                           "frac_of_measured": cells * opc / (ms / 1e3) / mp}
+    else:
+        # FP64 pipe: 2 DFMA lanes per SM per clock on this part
+        peak = props.multi_processor_count * FP64_LANES_PER_SM * sm_max * 1e6
+        mp = twed.pipe_peak(twed.PEAK_DFMA64)
+        res["roofline"] = {"bound": "alu", "achieved": cells * opc / (ms / 1e3) / 1e12,
+                           "peak": peak / 1e12, "unit": "Top/s",
+                           "frac": cells * opc / (ms / 1e3) / peak, "traffic": None,
+                           "ops_per_cell": opc, "kernel": f"coop_kernel<double,{dim},2,R>",
+                           "peak_basis": f"{props.multi_processor_count} SMs x {FP64_LANES_PER_SM} "
+                                         f"FP64 lanes x {sm_max:.0f} MHz",
+                           "peak_measured": mp / 1e12,
+                           "frac_of_measured": cells * opc / (ms / 1e3) / mp}
     res["config"] = {"workload": f"{workload} one pair n=m={n}, dim {dim}, {dtype}"
                                  + (", compensated (TwoSum) FP32 running cost" if kahan else ""),
                      "n": n, "accumulation": "kahan" if kahan else dtype,

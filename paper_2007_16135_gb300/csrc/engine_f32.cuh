@@ -50,6 +50,13 @@ __device__ __forceinline__ float min3f(float a, float b, float c) {
     return d;
 }
 
+// Steps per straight-line block of the staged engine (a divisor of 8).
+// Measured on GB300: the many-pairs kernel runs fastest with 4 (longer
+// unrolled bodies of its several strip heights miss in the instruction
+// cache), the one-pair band kernel with 8.
+constexpr int kStepBlockPairs = 4;
+constexpr int kStepBlockBand = 8;
+
 // ---------------------------------------------------------------- cp.async
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
     const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
@@ -86,7 +93,7 @@ constexpr float kBig = 1.2676506e30f;  // 2^100
 // areas (kRingCols records, kRingCols boundary entries).  Boundary rows hold
 // (D, c) float2 per column, or (D_hi, D_lo, c, 0) float4 when KH; `io.up`
 // must have at least m+1 readable entries (a staged copy may read one past m).
-template <int DIM, int P, int R, bool KH = false>
+template <int DIM, int P, int R, bool KH = false, int kStepBlock = kStepBlockPairs>
 __device__ __forceinline__ bool run_strip_staged(const PairRef<float>& pr, int r0, int rows,
                                                  const StripIO<float>& io, const SyncCtl& sc,
                                                  float* result_a, float* result_b, float* ring,
@@ -272,12 +279,17 @@ __device__ __forceinline__ bool run_strip_staged(const PairRef<float>& pr, int r
 
     const int steps = m + lanes_used - 1;
 
-    // Work due every 8 steps, done at steps s = 8q + 7 before that step's
-    // prefetch: publication of lane 31's progress (its last finished column,
-    // s - 31), the block-local hand-off waits, and every 32 steps the staging
-    // of the next 32-column chunk.  The 8 steps between two such points are
-    // straight-line code.
+    static_assert(kStepBlock == 1 || kStepBlock == 2 || kStepBlock == 4 || kStepBlock == 8,
+                  "the 8-step duties need block starts at every s = 8q + 7");
+    // Steps run in blocks of kStepBlock (4 or 8).  Work due every 8 steps is
+    // done at steps s = 8q + 7 before that step's prefetch: publication of
+    // lane 31's progress (its last finished column, s - 31) and the
+    // block-local hand-off waits; every 32 steps, the staging of the next
+    // 32-column chunk.  The steps of a block are straight-line code; a
+    // shorter block keeps the unrolled body small enough for the
+    // instruction cache when several strip heights run on one SM.
     auto boundary = [&](int s) -> bool {
+        if (((s + 1) & 7) != 0) return true;
         const int jp = s - 31;  // lane 31 finished columns 1..jp
         if (io.publish && jp >= 1 && jp <= m && lane == 31) {
             if (io.down_flag != nullptr && (jp & 31) == 0) st_release(io.down_flag, (unsigned)jp);
@@ -416,17 +428,17 @@ __device__ __forceinline__ bool run_strip_staged(const PairRef<float>& pr, int r
     };
 
     int s = 0;
-    const int head = min(steps, 7);
+    const int head = min(steps, kStepBlock - 1);
     for (; s < head; ++s) step(s - lane + 1);
     bool ok = true;
-    while (s + 8 <= steps) {
+    while (s + kStepBlock <= steps) {
         if (!boundary(s)) {
             ok = false;
             break;
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) step(s + u - lane + 1);
-        s += 8;
+        for (int u = 0; u < kStepBlock; ++u) step(s + u - lane + 1);
+        s += kStepBlock;
     }
     if (ok && s < steps) {
         ok = boundary(s);

@@ -25,14 +25,14 @@ __host__ __device__ constexpr int smem_per_warp() {
     else return 0;
 }
 
-template <typename T, int DIM, int P, int R, bool KH = false>
+template <typename T, int DIM, int P, int R, bool KH = false, int SB = kStepBlockPairs>
 __device__ __forceinline__ bool strip_call(const PairRef<T>& pr, int r0, int rows,
                                            const StripIO<T>& io, const SyncCtl& sc, T* o1, T* o2,
                                            unsigned char* wsmem) {
     if constexpr (kStaged<T, DIM>) {
         float* ring = reinterpret_cast<float*>(wsmem);
         void* bring = wsmem + kRingCols * Rec<float, DIM>::kLen * 4;
-        return run_strip_staged<DIM, P, R, KH>(pr, r0, rows, io, sc, o1, o2, ring, bring);
+        return run_strip_staged<DIM, P, R, KH, SB>(pr, r0, rows, io, sc, o1, o2, ring, bring);
     } else {
         (void)wsmem;
         return run_strip<T, DIM, P, R>(pr, r0, rows, io, sc, o1, o2);
@@ -225,7 +225,7 @@ __global__ void __launch_bounds__(256) band_kernel(CoopArgs<float> a) {
                     io.down_cons = &cons[w + 1];
                 }
             }
-            strip_call<float, DIM, P, R, KH>(pr, r0, rows, io, a.sc, a.out, nullptr, wsmem);
+            strip_call<float, DIM, P, R, KH, kStepBlockBand>(pr, r0, rows, io, a.sc, a.out, nullptr, wsmem);
         }
     }
 }

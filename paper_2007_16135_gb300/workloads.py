@@ -21,6 +21,11 @@ Workload numbers:
    length-5 box filter, t_i = i (nu = 1, lambda = 1).
 5. 1e5 database + 1000 query series of dim 4, lengths U[128, 512], random
    walks, t_i = i (nu = 1, lambda = 1).
+6. stand-in with the shape of the paper's first validation set: 600 1-D
+   series of 60 points in six pattern classes (level noise, cycles, rising
+   and falling trends, upward and downward shifts), t_i = i.
+7. stand-in with the shape of its second validation set: 10 1-D series of
+   100,000 points (sinusoids whose periods drift, plus noise), t_i = i.
 
 All use p = 2.  The paper's own timing runs used random series of power-of-two
 lengths (section "Basic Methodology and Results"); its UCI and MNIST data are
@@ -38,6 +43,8 @@ PARAMS = {
     3: dict(nu=0.5, lam=0.5, p=2),
     4: dict(nu=1.0, lam=1.0, p=2),
     5: dict(nu=1.0, lam=1.0, p=2),
+    6: dict(nu=1.0, lam=1.0, p=2),
+    7: dict(nu=1.0, lam=1.0, p=2),
 }
 
 
@@ -194,3 +201,45 @@ def sample_block_pairs(na: int, nb: int, k: int, workload: int) -> np.ndarray:
     rng = rng_for(workload, 2)
     flat = rng.choice(na * nb, size=min(k, na * nb), replace=False)
     return np.stack([flat // nb, flat % nb], axis=1).astype(np.int64)
+
+
+def set_u1(nseries: int = 600, length: int = 60, stream: int = 0) -> SeriesSet:
+    """Workload 6: six classes of 1-D pattern series, nseries / 6 each.
+
+    Every series is a level 30 plus N(0, 2) noise; class 1 adds a sine of
+    amplitude U[10, 15] and period U[10, 15]; classes 2 and 3 add a trend of
+    slope +-U[0.2, 0.5]; classes 4 and 5 add a step of height +-U[7.5, 20]
+    at a point U[length/3, 2 length/3].  Class 0 is the noise alone."""
+    rng = rng_for(6, stream)
+    out = []
+    t = np.arange(1, length + 1, dtype=np.float64)
+    for s_ in range(nseries):
+        c = s_ % 6
+        y = 30.0 + rng.normal(0.0, 2.0, length)
+        if c == 1:
+            y += rng.uniform(10, 15) * np.sin(2 * np.pi * t / rng.uniform(10, 15))
+        elif c in (2, 3):
+            y += (1 if c == 2 else -1) * rng.uniform(0.2, 0.5) * t
+        elif c in (4, 5):
+            t0 = rng.integers(length // 3, 2 * length // 3 + 1)
+            y += (1 if c == 4 else -1) * rng.uniform(7.5, 20) * (t >= t0)
+        out.append((y[:, None], t.copy()))
+    return pack(out)
+
+
+def set_u2(nseries: int = 10, length: int = 100_000, stream: int = 0) -> SeriesSet:
+    """Workload 7: long 1-D pseudo-periodic series: sum over r = 1..3 of
+    A_r sin(phi_r(i)) with A_r ~ U[0.5, 1.5], an instantaneous period drifting
+    linearly from U[40, 200] to U[40, 200] samples, plus N(0, 0.05)."""
+    rng = rng_for(7, stream)
+    out = []
+    i = np.arange(length, dtype=np.float64)
+    for _ in range(nseries):
+        y = rng.normal(0.0, 0.05, length)
+        for _r in range(3):
+            p0, p1 = rng.uniform(40, 200, 2)
+            period = p0 + (p1 - p0) * i / max(length - 1, 1)
+            phase = 2 * np.pi * np.cumsum(1.0 / period) + rng.uniform(0, 2 * np.pi)
+            y += rng.uniform(0.5, 1.5) * np.sin(phase)
+        out.append((y[:, None], i + 1.0))
+    return pack(out)

@@ -1,0 +1,66 @@
+"""GPU parity on inputs shaped like the paper's 1-D validation sets.
+
+* u1: 600 series of 60 points in six pattern classes, every i<j pair in one
+  FP64 plan, bit-identical to the oracle (same IEEE operations, p = 2).
+* u2: 10 series of 100,000 points.  Every pair exceeds the plan's per-warp
+  share, so the plan runs each on the one-pair schedule (compensated FP32
+  for n + m > 1e5): within 1e-6 of the stored FP64 oracle values on the
+  same FP32-rounded inputs; one pair in FP64 bit-identical to the stored
+  oracle value.  Stored values: tests/golden/make_u2_expected.py (oracle only).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2007_16135_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "u2_oracle.json")
+
+
+@pytest.fixture(scope="module")
+def tw():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a GPU")
+    from paper_2007_16135_gb300 import twed
+    twed.load()
+    return twed
+
+
+def test_u1_all_pairs_f64_bitwise(tw):
+    import torch
+    S = W.set_u1()
+    D = tw.DeviceSet.from_numpy(S.vals, S.ts, S.offs, torch.float64)
+    M = tw.Plan(D, None, 1.0, 1.0, 2).execute().cpu().numpy()
+    pairs = np.array([(i, j) for i in range(S.n) for j in range(i + 1, S.n)])
+    want = oracle.twed_pairs(S.as_tuple(), S.as_tuple(), pairs, 1.0, 1.0, 2)
+    np.testing.assert_array_equal(M[pairs[:, 0], pairs[:, 1]], want)
+    assert np.all(M == M.T) and np.all(np.diag(M) == 0)
+
+
+def test_u2_plan_f32_against_stored_oracle(tw):
+    import torch
+    with open(GOLD) as f:
+        gold = json.load(f)
+    S = W.set_u2().astype(np.float32)
+    D = tw.DeviceSet.from_numpy(S.vals, S.ts, S.offs, torch.float32)
+    plan = tw.Plan(D, None, 1.0, 1.0, 2)
+    assert "cut-over" in plan.describe()
+    M = plan.execute().cpu().numpy()
+    for (i, j), want in zip(gold["pairs"], gold["f32_rounded_inputs"]):
+        assert abs(float(M[i, j]) - want) <= 1e-6 * want, (i, j, M[i, j], want)
+        assert M[i, j] == M[j, i]
+
+
+def test_u2_pair_f64_bitwise_against_stored_oracle(tw):
+    with open(GOLD) as f:
+        gold = json.load(f)
+    S = W.set_u2()
+    (i, j), want = gold["pairs"][0], gold["f64_inputs"][0]
+    a, ta = S.series(i)
+    b, tb = S.series(j)
+    assert tw.twed_f64(a, ta, b, tb, 1.0, 1.0, 2) == want
