@@ -273,7 +273,7 @@ twed_status_t run_pair_dev(twed_handle_t h, const T* a, const T* ta, int64_t la,
         return fail(h, TWED_ERR_INVALID_ARG, "unknown accumulation mode %d", o->accum);
     if (o && o->accum == TWED_ACCUM_KAHAN && sizeof(T) == 4 && !twed::compiled_layout(dim, p))
         return fail(h, TWED_ERR_UNSUPPORTED,
-                    "compensated FP32 needs dim in {1,2,3,4,8} and p in {1,2} (dim 1: any p)");
+                    "compensated FP32 needs dim <= 8 and p in {1,2} (dim 1: any p)");
     // rows = the longer series: more strips, more warps in flight
     if (lb > la) {
         std::swap(a, b);

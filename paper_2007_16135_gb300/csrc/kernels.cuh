@@ -64,11 +64,14 @@ __global__ void __launch_bounds__(256) records_kernel(RecordsArgs<T> a) {
         T d;
         T* out = a.rec + g * RL::kLen;
         if constexpr (DIM > 0) {
+            // a point of a.dim <= DIM components is zero-padded to DIM: the
+            // padded terms are |0 - 0|^p = 0 and come after the real ones, so
+            // every distance is the same, bit for bit
             T x[DIM], y[DIM];
 #pragma unroll
             for (int k = 0; k < DIM; ++k) {
-                x[k] = a.vals[g * DIM + k];
-                y[k] = first ? T(0) : a.vals[(g - 1) * DIM + k];
+                x[k] = k < a.dim ? a.vals[g * a.dim + k] : T(0);
+                y[k] = (first || k >= a.dim) ? T(0) : a.vals[(g - 1) * a.dim + k];
 #pragma unroll
                 for (int u = 0; u < RL::kVS; ++u) out[k * RL::kVS + u] = x[k];
             }
@@ -349,6 +352,7 @@ __global__ void zero_diag_kernel(T* out, int64_t n) {
             case 4: if (p == 1) { constexpr int DIM_ = 4, P_ = 1; BODY; }      \
                     else if (p == 2) { constexpr int DIM_ = 4, P_ = 2; BODY; } \
                     else { constexpr int DIM_ = 0, P_ = 0; BODY; } break;      \
+            case 5: case 6: case 7: /* zero-padded to the dim-8 layout */    \
             case 8: if (p == 1) { constexpr int DIM_ = 8, P_ = 1; BODY; }      \
                     else if (p == 2) { constexpr int DIM_ = 8, P_ = 2; BODY; } \
                     else { constexpr int DIM_ = 0, P_ = 0; BODY; } break;      \

@@ -48,7 +48,8 @@ def test_w1_pair_f64_bitwise(tw):
 
 
 @pytest.mark.parametrize("n,m", SHAPES)
-@pytest.mark.parametrize("dim,p", [(1, 2), (2, 1), (3, 2), (4, 2), (5, 2), (8, 1), (8, 2), (3, 3)])
+@pytest.mark.parametrize("dim,p", [(1, 2), (2, 1), (3, 2), (4, 2), (5, 2), (7, 1), (8, 1), (8, 2), (3, 3),
+                                   (9, 2)])
 def test_pair_f64(tw, n, m, dim, p):
     rng = np.random.default_rng(n * 1000 + m * 10 + dim + 100 * p)
     a, ta = series(rng, n, dim)
@@ -170,7 +171,7 @@ def test_invalid_arguments_rejected(tw, bad):
 
 
 @pytest.mark.parametrize("n,m", [(1, 1), (33, 65), (257, 300), (1000, 17), (2100, 700)])
-@pytest.mark.parametrize("dim,p", [(1, 2), (3, 2), (4, 1), (8, 2), (2, 2)])
+@pytest.mark.parametrize("dim,p", [(1, 2), (3, 2), (4, 1), (8, 2), (2, 2), (5, 2), (7, 1)])
 def test_pair_f32_compensated(tw, n, m, dim, p):
     # compensated (TwoSum) FP32 running cost against the FP64 oracle on the
     # same FP32-rounded inputs
@@ -184,9 +185,10 @@ def test_pair_f32_compensated(tw, n, m, dim, p):
 
 
 def test_compensated_unsupported_layout_is_reported(tw):
-    # dim 5 has no compiled point layout: an explicit request is refused
+    # dim 9 has no compiled point layout (dims 5-7 are zero-padded to 8): an
+    # explicit request is refused
     rng = np.random.default_rng(1)
-    a, ta = series(rng, 50, 5, np.float32)
+    a, ta = series(rng, 50, 9, np.float32)
     with pytest.raises(tw.TwedError) as ei:
         tw.twed_f32(a, ta, a, ta, 1.0, 1.0, 2, opts=tw.make_opts(accum=tw.ACCUM_KAHAN))
     assert ei.value.status == tw.TWED_ERR_UNSUPPORTED
