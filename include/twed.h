@@ -198,9 +198,13 @@ twed_status_t twed_batch_f32_noalloc(const twed_set_f32_t* A, const twed_set_f32
  * Real Datasets").  B == NULL: symmetric self-matrix of A, out[NA][NA]; only
  * i < j pairs are computed, mirrored, and the diagonal is 0 (TWED(a,a) = 0).
  * Otherwise out[NA][NB], out[i*NB + j] = TWED(A_i, B_j).
- * Creation sorts series by length, picks a schedule (and times candidates if
- * opts->autotune), computes the step-cost records once per execute, and
- * captures one persistent launch into a CUDA graph.  The plan keeps pointers
+ * Creation sorts series by length (longest first) and picks a schedule; with
+ * opts->autotune it times every rows-per-lane cap and resident-block count on
+ * a strided sample of its own pairs (about 2e10 cells) and keeps the fastest.
+ * Pairs whose cells exceed the plan's average work per warp (at most 4096 of
+ * them) run after the persistent launch on the one-pair block-cooperative
+ * schedule.  Execute computes the step-cost records and runs the launches
+ * captured (at the first execute into a given output) in one CUDA graph.  The plan keeps pointers
  * to A and B: they must stay valid and keep their lengths; their values may
  * change between executes.  Execute enqueues one graph launch on `stream`. */
 twed_status_t twed_allpairs_plan_create_f64(twed_handle_t handle, const twed_set_f64_t* A,

@@ -328,3 +328,24 @@ def test_pipe_peaks_are_plausible(tw):
     f64 = tw.pipe_peak(tw.PEAK_DFMA64)
     assert 0.2 * nominal < f32 < nominal
     assert 0 < f64 < f32
+
+
+def test_training_with_mined_groups(tw):
+    # half of the labelled pairs from mined groups (an anchor and its nearest
+    # series under the half-trained model): every pair is labelled exactly and
+    # the index still searches correctly
+    import torch
+    db = W.set_w5(400, stream=1).astype(np.float32)
+    qs = W.set_w5(4, stream=0).astype(np.float32)
+    cfg = tw.knn_config(group_size=8, groups_per_step=8, epochs=4, train_pairs=4000,
+                        mine_fraction=0.5, seed=3)
+    index = tw.KnnIndex(dev_set(tw, db), 1.0, 1.0, 2, config=cfg)
+    stats = index.train()
+    assert stats["mined_pairs"] > 0 and stats["label_pairs"] > stats["mined_pairs"]
+    idx, dist = index.search(dev_set(tw, qs), k=3, n_candidates=50)
+    idx, dist = idx.cpu().numpy(), dist.cpu().numpy()
+    pairs = np.array([(q, int(x)) for q in range(qs.n) for x in idx[q]])
+    want = oracle.twed_pairs(qs.astype(np.float64).as_tuple(), db.astype(np.float64).as_tuple(),
+                             pairs, 1.0, 1.0, 2).reshape(qs.n, 3)
+    np.testing.assert_allclose(dist, want, rtol=1e-5)
+    index.close()
