@@ -718,7 +718,7 @@ def main():
     dist_init(world, local, True)
     from paper_2007_16135_gb300 import twed
     twed.load()
-    if args.workload in ("w3", "w4"):
+    if args.workload in ("w3", "w4", "u1", "u2"):
         res = bench_plan(args, rank, world, dev, args.workload)
         if args.workload == "w3" and not args.no_knn:
             kn = bench_knn(args, rank, world, dev, steps=10, warmup=3)
