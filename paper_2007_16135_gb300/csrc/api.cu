@@ -557,7 +557,15 @@ struct twed_plan_s {
     bool has_opts = false;
     twed_opts_t opts{};
     void* band_ws = nullptr;
-    size_t band_ring_bytes = 0;
+    size_t band_ring_bytes = 0;  // ring part of one lane's slot
+    size_t band_slot_bytes = 0;  // ring + flags of one lane
+    // long pairs run concurrently on `nlanes` side streams (one workspace
+    // slot each), forked from and joined back into the execute's stream
+    static constexpr int kMaxLanes = 8;
+    int nlanes = 0;
+    cudaStream_t lane_st[kMaxLanes] = {};
+    cudaEvent_t fork_ev = nullptr;
+    cudaEvent_t join_ev[kMaxLanes] = {};
 };
 
 namespace {
@@ -608,13 +616,20 @@ cudaError_t plan_enqueue(twed_plan_t pl, T* out, cudaStream_t st) {
     if (e == cudaSuccess) e = cudaEventRecordWithFlags(pl->ev0, st, evflag);
     if (e == cudaSuccess) e = launch_plan_pairs<T>(pl, pa, st);
     if (e == cudaSuccess) e = cudaEventRecordWithFlags(pl->ev1, st, evflag);
+    if (e == cudaSuccess && !pl->longp.empty()) {
+        e = cudaEventRecord(pl->fork_ev, st);
+        for (int k = 0; k < pl->nlanes && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(pl->lane_st[k], pl->fork_ev, 0);
+    }
     for (size_t i = 0; i < pl->longp.size() && e == cudaSuccess; ++i) {
         const auto& lp = pl->longp[i];
+        const int lane = (int)(i % (size_t)pl->nlanes);
+        cudaStream_t ls = pl->lane_st[lane];
+        char* slot = (char*)pl->band_ws + (size_t)lane * pl->band_slot_bytes;
         const twed_opts_t* o = pl->has_opts ? &pl->opts : nullptr;
         const PairLayout L = pair_layout<T>(pl->h, lp.n, lp.m, pl->dim, pl->p, o, 0);
         const int rl = twed::rec_len<T>(pl->dim, pl->p);
-        unsigned* flags = (unsigned*)((char*)pl->band_ws + pl->band_ring_bytes);
-        e = cudaMemsetAsync(flags, 0, sizeof(unsigned) * (size_t)(L.nstrips + 1), st);
+        unsigned* flags = (unsigned*)(slot + pl->band_ring_bytes);
+        e = cudaMemsetAsync(flags, 0, sizeof(unsigned) * (size_t)(L.nstrips + 1), ls);
         if (e != cudaSuccess) break;
         CoopArgs<T> ca;
         ca.rec_a = (lp.r_is_b ? pa.rec_b : pa.rec_a) + lp.rfirst * rl;
@@ -627,18 +642,26 @@ cudaError_t plan_enqueue(twed_plan_t pl, T* out, cudaStream_t st) {
         ca.p = pl->p;
         ca.nu = pa.nu;
         ca.nstrips = L.nstrips;
-        ca.ring = pl->band_ws;
+        ca.ring = slot;
         ca.nslot = kRingSlots;
         ca.ring_stride = L.ring_stride;
         ca.flags = flags;
         ca.strip_counter = flags + L.nstrips;
         ca.out = out + lp.o1;
         ca.sc = pa.sc;
-        if (launch_pair_schedule<T>(pl->h, L, ca, st) != TWED_OK) {
+        if (launch_pair_schedule<T>(pl->h, L, ca, ls) != TWED_OK) {
             e = cudaErrorLaunchFailure;
             break;
         }
-        if (lp.o2 >= 0) e = cudaMemcpyAsync(out + lp.o2, out + lp.o1, sizeof(T), cudaMemcpyDeviceToDevice, st);
+        if (lp.o2 >= 0) e = cudaMemcpyAsync(out + lp.o2, out + lp.o1, sizeof(T), cudaMemcpyDeviceToDevice, ls);
+    }
+    if (!pl->longp.empty()) {
+        // join every lane back, even after a failure (a capture must end joined)
+        for (int k = 0; k < pl->nlanes; ++k) {
+            cudaError_t e2 = cudaEventRecord(pl->join_ev[k], pl->lane_st[k]);
+            if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(st, pl->join_ev[k], 0);
+            if (e == cudaSuccess) e = e2;
+        }
     }
     if (e == cudaSuccess && pl->symmetric) e = twed::launch_zero_diag(out, pl->f64, pl->na, st);
     return e;
@@ -982,9 +1005,22 @@ twed_status_t plan_create(twed_handle_t h, const S* A, const S* B, int dim, T nu
                 flags = std::max(flags, L.end - L.o_flags);
             }
             pl->band_ring_bytes = align_up(ring);
-            e = cudaMalloc(&pl->band_ws, pl->band_ring_bytes + flags);
+            pl->band_slot_bytes = align_up(pl->band_ring_bytes + flags);
+            pl->nlanes = (int)std::min<size_t>(pl->longp.size(), twed_plan_s::kMaxLanes);
+            e = cudaMalloc(&pl->band_ws, pl->band_slot_bytes * (size_t)pl->nlanes);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&pl->fork_ev, cudaEventDisableTiming);
+            for (int k = 0; k < pl->nlanes && e == cudaSuccess; ++k) {
+                e = cudaStreamCreateWithFlags(&pl->lane_st[k], cudaStreamNonBlocking);
+                if (e == cudaSuccess) e = cudaEventCreateWithFlags(&pl->join_ev[k], cudaEventDisableTiming);
+            }
             if (e != cudaSuccess) {
                 cudaGetLastError();
+                for (int k = 0; k < pl->nlanes; ++k) {
+                    if (pl->lane_st[k]) cudaStreamDestroy(pl->lane_st[k]);
+                    if (pl->join_ev[k]) cudaEventDestroy(pl->join_ev[k]);
+                }
+                if (pl->fork_ev) cudaEventDestroy(pl->fork_ev);
+                if (pl->band_ws) cudaFree(pl->band_ws);
                 cudaFree(pl->mem);
                 delete pl;
                 return fail(h, TWED_ERR_ALLOC, "plan cut-over workspace: %s", cudaGetErrorString(e));
@@ -1007,12 +1043,7 @@ twed_status_t plan_create(twed_handle_t h, const S* A, const S* B, int dim, T nu
         s = autotune_plan<T>(h, pl, perm_a, perm_b, A->offs_host, sym ? A->offs_host : B->offs_host,
                              per_sm, tuned);
         if (s != TWED_OK) {
-            cudaStreamDestroy(pl->cap);
-            cudaEventDestroy(pl->ev0);
-            cudaEventDestroy(pl->ev1);
-            if (pl->band_ws) cudaFree(pl->band_ws);
-            cudaFree(pl->mem);
-            delete pl;
+            twed_plan_destroy(pl);
             return s;
         }
     }
@@ -1113,6 +1144,11 @@ extern "C" void twed_plan_destroy(twed_plan_t pl) {
     if (pl->ev0) cudaEventDestroy(pl->ev0);
     if (pl->ev1) cudaEventDestroy(pl->ev1);
     cudaDeviceSynchronize();
+    for (int k = 0; k < pl->nlanes; ++k) {
+        if (pl->lane_st[k]) cudaStreamDestroy(pl->lane_st[k]);
+        if (pl->join_ev[k]) cudaEventDestroy(pl->join_ev[k]);
+    }
+    if (pl->fork_ev) cudaEventDestroy(pl->fork_ev);
     if (pl->band_ws) cudaFree(pl->band_ws);
     if (pl->mem) cudaFree(pl->mem);
     delete pl;
