@@ -520,6 +520,20 @@ def bench_knn(args, rank, world, dev, steps, warmup):
             break
     if c_op is None:
         c_op = max(sweep)
+    else:
+        # bisect between the last count below 0.99 and c_op, to within 100
+        lo = max([c for c in sweep if sweep[c] < 0.99], default=None)
+        while lo is not None and c_op - lo > 100:
+            mid = ((lo + c_op) // 2 + 99) // 100 * 100
+            if mid >= c_op:
+                break
+            _, dist = index.search(Q, k=k, n_candidates=mid, stream=stream)
+            sweep[mid] = recall(dist)
+            if sweep[mid] >= 0.99:
+                c_op = mid
+            else:
+                lo = mid
+    sweep = dict(sorted(sweep.items()))
     out = index._outputs(qs.n, k)
     for _ in range(warmup):
         index.search(Q, k=k, n_candidates=c_op, stream=stream, out=out)
