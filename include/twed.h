@@ -51,7 +51,7 @@ typedef enum {
     TWED_ERR_CUDA = 2,        /* a CUDA runtime call failed */
     TWED_ERR_ALLOC = 3,       /* device workspace allocation failed */
     TWED_ERR_TIMEOUT = 4,     /* a bounded inter-warp wait expired; results invalid */
-    TWED_ERR_UNSUPPORTED = 5  /* valid request this build cannot serve */
+    TWED_ERR_UNSUPPORTED = 5  /* valid request the library does not support */
 } twed_status_t;
 
 typedef struct twed_handle_s* twed_handle_t;
@@ -311,7 +311,7 @@ twed_status_t twed_knn_train(twed_knn_t knn);
  * Enqueued on `stream`; the call waits only for its own host-side setup. */
 twed_status_t twed_knn_search(twed_knn_t knn, const twed_set_f32_t* queries, int k,
                               int n_candidates, int64_t* d_idx, float* d_dist, void* stream);
-/* Exact batched k-NN (the reference the filter is judged against): the full
+/* Exact batched k-NN (the reference the filter's recall is measured against): the full
  * queries x database TWED matrix through an all-pairs plan, then the k
  * smallest per query (ties by smaller index).  1 <= k <= min(ndb, 4096).
  * Blocking. */
