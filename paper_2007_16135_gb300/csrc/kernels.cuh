@@ -287,14 +287,28 @@ __global__ void __launch_bounds__(128, TWED_PAIRS_MIN_BLOCKS) pairs_kernel(Pairs
         // a pair far larger than a warp's share of the work runs on the
         // block-cooperative schedule instead (the plan enqueues it)
         if (a.cut_cells > 0 && nx * ny > a.cut_cells) continue;
-        // rows = the shorter series (fewer strips), columns = the longer one;
-        // TWED is symmetric, and the swapped evaluation performs the mirrored
-        // operations, so the value is the same bit for bit.
+        // Orientation: TWED is symmetric, and the swapped evaluation performs
+        // the mirrored operations, so the value is the same bit for bit.  Take
+        // the one with less estimated work: over its strips, (steps) x (R + 1)
+        // -- R cells per lane per step plus about one row's worth of per-step
+        // overhead -- so a short series whose rows would leave lanes idle
+        // goes to the columns.
+        auto work = [&](int64_t rows_n, int64_t cols_m) -> int64_t {
+            int64_t w_ = 0;
+            for (int64_t left = rows_n; left > 0;) {
+                int R = left >= 32 * rmax ? rmax : (int)((left + 31) / 32);
+                if (kEven) R = min((R + 1) & ~1, rmax);
+                const int64_t rows = left < 32 * (int64_t)R ? left : 32 * (int64_t)R;
+                w_ += (cols_m + (rows + R - 1) / R - 1) * (R + 1);
+                left -= rows;
+            }
+            return w_;
+        };
         PairRef<T> pr;
         pr.dim = a.dim;
         pr.p = a.p;
         pr.nu = a.nu;
-        if (nx <= ny) {
+        if (work(nx, ny) <= work(ny, nx)) {
             pr.rec_a = a.rec_a; pr.vals_a = a.vals_a; pr.a_first = xa; pr.n = (int)nx;
             pr.rec_b = a.rec_b; pr.vals_b = a.vals_b; pr.b_first = yb; pr.m = (int)ny;
         } else {
