@@ -567,7 +567,8 @@ def bench_knn(args, rank, world, dev, steps, warmup):
                    "rerank_cells": rr_cells, "rerank_gcups": rr_cells / (phase_ms[2] / 1e3) / 1e9,
                    "train": {key: train[key] for key in ("sigma", "first_loss", "last_loss",
                                                          "label_pairs", "mined_pairs", "label_cells", "steps",
-                                                         "label_ms", "train_ms", "embed_ms")}},
+                                                         "label_ms", "train_ms", "embed_ms", "rerank_rows_per_lane",
+                                                         "rerank_blocks_per_sm", "tune_ms")}},
            "roofline": {"bound": "alu", "achieved": rr_cells * opc / (phase_ms[2] / 1e3) / 1e12,
                         "peak": peak / 1e12, "unit": "Top/s",
                         "frac": rr_cells * opc / (phase_ms[2] / 1e3) / peak, "traffic": None,

@@ -156,15 +156,34 @@ twed_status_t twed_dev_f32_ex(twed_handle_t handle, const float* d_a, const floa
  * The paper's batch mode (section "cuTWED Implementation Remarks"), here for
  * an arbitrary list of pairs: d_pairs[2k], d_pairs[2k+1] (device int64) index
  * series of A and B; d_out[k] (device) receives TWED(A[d_pairs[2k]],
- * B[d_pairs[2k+1]]).  One persistent launch, one warp per pair.  Pair indices
- * are not range-checked on the device: out-of-range indices are undefined.
- * B may equal A. */
+ * B[d_pairs[2k+1]]).  One persistent launch, one warp per pair, pairs taken
+ * in list order.  Pair indices are not range-checked on the device:
+ * out-of-range indices are undefined.  B may equal A. */
 twed_status_t twed_batch_f64(twed_handle_t handle, const twed_set_f64_t* A,
                              const twed_set_f64_t* B, const int64_t* d_pairs, int64_t npairs,
                              int dim, double nu, double lambda, int p, double* d_out, void* stream);
 twed_status_t twed_batch_f32(twed_handle_t handle, const twed_set_f32_t* A,
                              const twed_set_f32_t* B, const int64_t* d_pairs, int64_t npairs,
                              int dim, float nu, float lambda, int p, float* d_out, void* stream);
+
+/* Run orders of an explicit pair list (the warps take pairs in run order):
+ *   TWED_ORDER_LIST           the list's own order (twed_batch_*), which keeps
+ *                             whatever locality the caller built into it;
+ *   TWED_ORDER_LONGEST_FIRST  decreasing len_a * len_b (quarter-octave
+ *                             classes), so the largest pairs do not start last.
+ * Reordering is a device counting sort (workspace: 8 bytes per pair), done
+ * only when there are more pairs than resident warps.  d_out[k] is always
+ * pair k's value, and values do not depend on the order. */
+#define TWED_ORDER_LIST 0
+#define TWED_ORDER_LONGEST_FIRST 1
+twed_status_t twed_batch_f64_ex(twed_handle_t handle, const twed_set_f64_t* A,
+                                const twed_set_f64_t* B, const int64_t* d_pairs, int64_t npairs,
+                                int dim, double nu, double lambda, int p, int order,
+                                double* d_out, void* stream);
+twed_status_t twed_batch_f32_ex(twed_handle_t handle, const twed_set_f32_t* A,
+                                const twed_set_f32_t* B, const int64_t* d_pairs, int64_t npairs,
+                                int dim, float nu, float lambda, int p, int order, float* d_out,
+                                void* stream);
 
 /* ---- explicit pairs without any allocation -------------------------------
  * The paper has no counterpart to this entry point.  It exists for callers
@@ -293,6 +312,9 @@ typedef struct {
     double label_ms;       /* wall time of labelling (exact TWED) */
     double train_ms;       /* wall time of the Adam steps */
     double embed_ms;       /* wall time of embedding the database */
+    int32_t rerank_rows_per_lane;  /* re-rank launch shape chosen by timing */
+    int32_t rerank_blocks_per_sm;  /* (rows-per-lane cap, resident blocks per SM) */
+    double tune_ms;        /* wall time of that timing */
 } twed_knn_stats_t;
 
 void twed_knn_config_default(twed_knn_config_t* cfg);
@@ -301,8 +323,9 @@ void twed_knn_config_default(twed_knn_config_t* cfg);
  * the index's device memory; trains nothing yet. */
 twed_status_t twed_knn_create(twed_handle_t handle, const twed_set_f32_t* db, int dim, float nu,
                               float lambda, int p, const twed_knn_config_t* cfg, twed_knn_t* knn);
-/* Labels, trains and embeds the database (blocking; uses the handle's
- * stream).  May be called again to retrain from a fresh initialisation. */
+/* Labels, trains and embeds the database, then times the re-rank's launch
+ * shape on random database pairs (blocking; uses the handle's stream).  May
+ * be called again to retrain from a fresh initialisation. */
 twed_status_t twed_knn_train(twed_knn_t knn);
 /* Queries (device set, offs_host required): d_idx[q*k + r] (device int64)
  * and d_dist[q*k + r] (device float, exact FP32 TWED) receive the k
@@ -331,7 +354,8 @@ twed_status_t twed_knn_search_profile(twed_knn_t knn, double* phase_ms, int64_t*
 twed_status_t twed_knn_get_stats(twed_knn_t knn, twed_knn_stats_t* out);
 /* Parameters (host float[twed_encoder_param_count(dim)]). */
 twed_status_t twed_knn_get_params(twed_knn_t knn, float* out, int64_t n);
-/* Replace the parameters and re-embed the database (blocking). */
+/* Replace the parameters and re-embed the database (blocking).  On an index
+ * whose re-rank shape was never timed, also times it (as twed_knn_train). */
 twed_status_t twed_knn_set_params(twed_knn_t knn, const float* in, int64_t n);
 /* Database embeddings e (device float[ndb][32]) after training. */
 twed_status_t twed_knn_get_embeddings(twed_knn_t knn, float* d_out, void* stream);

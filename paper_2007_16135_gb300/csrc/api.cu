@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "../../include/twed.h"
+#include "handle.h"
 #include "launch.h"
 
 using twed::CoopArgs;
@@ -1157,11 +1158,16 @@ extern "C" void twed_plan_destroy(twed_plan_t pl) {
 // =========================================================== explicit pairs
 namespace {
 
+// rmax / per_sm: rows-per-lane cap and resident blocks per SM of the
+// many-pairs kernel (0: the kernel's limit and the occupancy maximum).
 template <typename T, typename S>
 twed_status_t batch_impl(twed_handle_t h, const S* A, const S* B, const int64_t* d_pairs,
-                         int64_t npairs, int dim, T nu, T lambda, int p, T* d_out, void* stream) {
+                         int64_t npairs, int dim, T nu, T lambda, int p, T* d_out, void* stream,
+                         int order_mode = TWED_ORDER_LIST, int rmax = 0, int per_sm_req = 0) {
     if (!h) return TWED_ERR_INVALID_ARG;
     if (npairs < 0) return fail(h, TWED_ERR_INVALID_ARG, "npairs < 0");
+    if (order_mode != TWED_ORDER_LIST && order_mode != TWED_ORDER_LONGEST_FIRST)
+        return fail(h, TWED_ERR_INVALID_ARG, "unknown pair order %d", order_mode);
     if (npairs == 0) return TWED_OK;
     if (!d_pairs || !d_out) return fail(h, TWED_ERR_INVALID_ARG, "null pointer");
     twed_status_t s = check_params<T>(h, 1, 1, dim, nu, lambda, p);
@@ -1172,15 +1178,20 @@ twed_status_t batch_impl(twed_handle_t h, const S* A, const S* B, const int64_t*
     const bool same = (A->vals == B->vals && A->offs == B->offs && A->ts == B->ts);
     const int rl = twed::rec_len<T>(dim, p);
     const int threads = 128;
-    const int per_sm = std::max(1, twed::pairs_blocks_per_sm<T>(dim, p, threads));
+    const int occ = std::max(1, twed::pairs_blocks_per_sm<T>(dim, p, threads));
+    const int per_sm = per_sm_req > 0 ? std::min(per_sm_req, occ) : occ;
     const int blocks = (int)std::min<int64_t>((int64_t)per_sm * h->sms, (npairs + 3) / 4);
     const int64_t nwarps = (int64_t)blocks * (threads / 32);
     const int64_t scols = (std::max(maxa, maxb) + 2) & ~(int64_t)1;  // >= longest + 1, even
+    // a run order other than the list's, when there is a queue to order
+    const bool order = order_mode != TWED_ORDER_LIST && npairs > nwarps;
     Carver cv;
     const size_t o_ra = cv.take(sizeof(T) * rl * (size_t)tota);
     const size_t o_rb = same ? o_ra : cv.take(sizeof(T) * rl * (size_t)totb);
     const size_t o_scr = cv.take(sizeof(T) * 2 * (size_t)nwarps * (size_t)scols);
     const size_t o_cnt = cv.take(sizeof(unsigned long long));
+    const size_t o_ord = order ? cv.take(sizeof(int64_t) * (size_t)npairs) : 0;
+    const size_t o_bins = order ? cv.take(sizeof(unsigned long long) * twed::kOrderBins) : 0;
     if ((s = ensure_ws(h, cv.off)) != TWED_OK) return s;
     char* base = (char*)h->ws;
     cudaStream_t st = (cudaStream_t)stream;
@@ -1209,18 +1220,40 @@ twed_status_t batch_impl(twed_handle_t h, const S* A, const S* B, const int64_t*
     pa.nb = B->n;
     pa.dim = dim;
     pa.p = p;
-    pa.rmax = twed::pairs_rmax_limit<T>();
+    pa.rmax = rmax > 0 ? std::min(rmax, twed::pairs_rmax_limit<T>()) : twed::pairs_rmax_limit<T>();
     pa.nu = nu;
     pa.out = d_out;
     pa.counter = counter;
     pa.scratch = base + o_scr;
     pa.scratch_cols = scols;
     pa.sc = make_sync(h, nullptr);
+    if (order) {
+        int64_t* ord = (int64_t*)(base + o_ord);
+        TWED_CUDA(h, twed::launch_order_pairs(d_pairs, npairs, A->offs, B->offs, ord,
+                                              (unsigned long long*)(base + o_bins), h->sms, st));
+        pa.order = ord;
+    }
     TWED_CUDA(h, twed::launch_pairs(pa, blocks, threads, st));
     return TWED_OK;
 }
 
 }  // namespace
+
+namespace twed {
+namespace detail {
+twed_status_t batch_f32_shaped(twed_handle_t h, const twed_set_f32_t* A, const twed_set_f32_t* B,
+                               const int64_t* d_pairs, int64_t npairs, int dim, float nu,
+                               float lambda, int p, float* d_out, void* stream, int order,
+                               int rmax, int per_sm) {
+    return batch_impl<float>(h, A, B, d_pairs, npairs, dim, nu, lambda, p, d_out, stream, order,
+                             rmax, per_sm);
+}
+int batch_f32_max_blocks_per_sm(int dim, int p) {
+    return std::max(1, twed::pairs_blocks_per_sm<float>(dim, p, 128));
+}
+int batch_f32_rmax_limit() { return twed::pairs_rmax_limit<float>(); }
+}  // namespace detail
+}  // namespace twed
 
 extern "C" twed_status_t twed_batch_f64(twed_handle_t h, const twed_set_f64_t* A,
                                         const twed_set_f64_t* B, const int64_t* d_pairs,
@@ -1234,6 +1267,20 @@ extern "C" twed_status_t twed_batch_f32(twed_handle_t h, const twed_set_f32_t* A
                                         int64_t npairs, int dim, float nu, float lambda, int p,
                                         float* d_out, void* stream) {
     return batch_impl<float>(h, A, B, d_pairs, npairs, dim, nu, lambda, p, d_out, stream);
+}
+
+extern "C" twed_status_t twed_batch_f64_ex(twed_handle_t h, const twed_set_f64_t* A,
+                                           const twed_set_f64_t* B, const int64_t* d_pairs,
+                                           int64_t npairs, int dim, double nu, double lambda,
+                                           int p, int order, double* d_out, void* stream) {
+    return batch_impl<double>(h, A, B, d_pairs, npairs, dim, nu, lambda, p, d_out, stream, order);
+}
+
+extern "C" twed_status_t twed_batch_f32_ex(twed_handle_t h, const twed_set_f32_t* A,
+                                           const twed_set_f32_t* B, const int64_t* d_pairs,
+                                           int64_t npairs, int dim, float nu, float lambda, int p,
+                                           int order, float* d_out, void* stream) {
+    return batch_impl<float>(h, A, B, d_pairs, npairs, dim, nu, lambda, p, d_out, stream, order);
 }
 
 // =========================================================== host all-pairs

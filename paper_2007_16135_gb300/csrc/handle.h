@@ -9,5 +9,13 @@ namespace detail {
 twed_status_t set_error(twed_handle_t h, twed_status_t st, const char* msg);
 int handle_sms(twed_handle_t h);
 int handle_device(twed_handle_t h);
+// twed_batch_f32_ex with a chosen launch shape: rows-per-lane cap `rmax`
+// and resident blocks per SM `per_sm` (0: the defaults).
+twed_status_t batch_f32_shaped(twed_handle_t h, const twed_set_f32_t* A, const twed_set_f32_t* B,
+                               const int64_t* d_pairs, int64_t npairs, int dim, float nu,
+                               float lambda, int p, float* d_out, void* stream, int order,
+                               int rmax, int per_sm);
+int batch_f32_max_blocks_per_sm(int dim, int p);
+int batch_f32_rmax_limit();
 }  // namespace detail
 }  // namespace twed

@@ -266,9 +266,10 @@ __global__ void __launch_bounds__(128, TWED_PAIRS_MIN_BLOCKS) pairs_kernel(Pairs
         int64_t x, y;
         T *o1, *o2 = nullptr;
         if (a.mode == kExplicitPairs) {
-            x = a.pairs[2 * w];
-            y = a.pairs[2 * w + 1];
-            o1 = a.out + w;
+            const int64_t wi = a.order ? a.order[w] : (int64_t)w;
+            x = a.pairs[2 * wi];
+            y = a.pairs[2 * wi + 1];
+            o1 = a.out + wi;
         } else if (a.mode == kSymmetricSorted) {
             int64_t pp, qq;
             triangle_pos((int64_t)w, a.na, pp, qq);

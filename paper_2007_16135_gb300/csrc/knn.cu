@@ -294,6 +294,7 @@ struct twed_knn_s {
     double mean_len = 0.0;
     bool trained = false;
     bool searched = false;
+    int rr_rmax = 0, rr_per_sm = 0;  // re-rank launch shape (0: defaults)
     twed_knn_stats_t stats{};
     cudaEvent_t ev[5] = {};  // search phase boundaries
     cudaStream_t host_stream = nullptr;
@@ -316,6 +317,74 @@ twed_status_t embed_database(twed_knn_t k, cudaStream_t st) {
     KNN_CUDA(k->h, search_vectors(k->emb_db.as<float>(), k->db.n, k->scalars.as<float>() + 1,
                                   k->svec_db.as<float>(), st));
     KNN_CUDA(k->h, cudaStreamSynchronize(st));
+    return TWED_OK;
+}
+
+// The re-rank runs the many-pairs kernel on (query, candidate) pairs, longest
+// first.  Its launch shape -- rows-per-lane cap x resident blocks per SM --
+// is timed on random database pairs (the length mix of queries drawn like
+// the database; about 1e10 cells, at most 2^20 pairs) in the same order, and
+// the fastest is kept.  CUDA events on `st`: one warm-up and the best of two
+// runs per shape.
+twed_status_t tune_rerank(twed_knn_t k, cudaStream_t st) {
+    twed_handle_t h = k->h;
+    const int64_t N = k->db.n;
+    uint64_t rng = k->cfg.seed * 0xD1B54A32D192ED03ull + 0x5bd1e995ull;
+    std::vector<int64_t> pr;
+    double cells = 0.0;
+    while (cells < 1e10 && (int64_t)pr.size() < 2 * ((int64_t)1 << 20)) {
+        const int64_t i = (int64_t)below(rng, (uint64_t)N), j = (int64_t)below(rng, (uint64_t)N);
+        pr.push_back(i);
+        pr.push_back(j);
+        cells += (double)(k->db_offs[i + 1] - k->db_offs[i]) * (double)(k->db_offs[j + 1] - k->db_offs[j]);
+    }
+    const int64_t ns = (int64_t)pr.size() / 2;
+    DevBuf dpairs, dout;
+    KNN_CUDA(h, dpairs.ensure(sizeof(int64_t) * pr.size()));
+    KNN_CUDA(h, dout.ensure(sizeof(float) * ns));
+    KNN_CUDA(h, cudaMemcpyAsync(dpairs.p, pr.data(), sizeof(int64_t) * pr.size(), cudaMemcpyHostToDevice, st));
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    KNN_CUDA(h, cudaEventCreate(&e0));
+    cudaError_t ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) {
+        cudaEventDestroy(e0);
+        KNN_CUDA(h, ce);
+    }
+    struct Events {
+        cudaEvent_t a, b;
+        ~Events() { cudaEventDestroy(a); cudaEventDestroy(b); }
+    } guard{e0, e1};
+    const int lim = twed::detail::batch_f32_rmax_limit();
+    const int occ = twed::detail::batch_f32_max_blocks_per_sm(k->dim, k->p);
+    float best = 1e30f;
+    int best_r = 0, best_b = 0;
+    for (int r : {2, 4, 6, 8}) {
+        if (r > lim) continue;
+        for (int b = 1; b <= occ; ++b) {
+            float t = 1e30f;
+            for (int rep = 0; rep < 3; ++rep) {
+                KNN_CUDA(h, cudaEventRecord(e0, st));
+                twed_status_t s = twed::detail::batch_f32_shaped(
+                    h, &k->db, &k->db, dpairs.as<int64_t>(), ns, k->dim, k->nu, k->lambda, k->p,
+                    dout.as<float>(), st, TWED_ORDER_LONGEST_FIRST, r, b);
+                if (s != TWED_OK) return s;
+                KNN_CUDA(h, cudaEventRecord(e1, st));
+                KNN_CUDA(h, cudaEventSynchronize(e1));
+                float ms = 0.f;
+                KNN_CUDA(h, cudaEventElapsedTime(&ms, e0, e1));
+                if (rep > 0) t = std::min(t, ms);
+            }
+            if (t < best) {
+                best = t;
+                best_r = r;
+                best_b = b;
+            }
+        }
+    }
+    k->rr_rmax = best_r;
+    k->rr_per_sm = best_b;
+    k->stats.rerank_rows_per_lane = best_r;
+    k->stats.rerank_blocks_per_sm = best_b;
     return TWED_OK;
 }
 
@@ -698,6 +767,9 @@ extern "C" twed_status_t twed_knn_train(twed_knn_t k) {
     t0 = std::chrono::steady_clock::now();
     if ((s = embed_database(k, st)) != TWED_OK) return s;
     k->stats.embed_ms = ms_since(t0);
+    t0 = std::chrono::steady_clock::now();
+    if ((s = tune_rerank(k, st)) != TWED_OK) return s;
+    k->stats.tune_ms = ms_since(t0);
     k->trained = true;
     return TWED_OK;
 }
@@ -732,6 +804,11 @@ extern "C" twed_status_t twed_knn_set_params(twed_knn_t k, const float* in, int6
                                  k->mu.as<float>(), k->sd.as<float>(), st));
     twed_status_t s = embed_database(k, st);
     if (s != TWED_OK) return s;
+    if (k->rr_rmax == 0) {
+        const auto t0 = std::chrono::steady_clock::now();
+        if ((s = tune_rerank(k, st)) != TWED_OK) return s;
+        k->stats.tune_ms = ms_since(t0);
+    }
     k->trained = true;
     return TWED_OK;
 }
@@ -787,8 +864,9 @@ extern "C" twed_status_t twed_knn_search(twed_knn_t k, const twed_set_f32_t* Q, 
     KNN_CUDA(h, pair_cells(k->qpairs.as<int64_t>(), nq * C, Q->offs, k->db.offs,
                            k->cells.as<unsigned long long>(), st));
     KNN_CUDA(h, cudaEventRecord(k->ev[2], st));
-    s = twed_batch_f32(h, Q, &k->db, k->qpairs.as<int64_t>(), nq * C, k->dim, k->nu, k->lambda,
-                       k->p, k->rr.as<float>(), st);
+    s = twed::detail::batch_f32_shaped(h, Q, &k->db, k->qpairs.as<int64_t>(), nq * C, k->dim,
+                                       k->nu, k->lambda, k->p, k->rr.as<float>(), st,
+                                       TWED_ORDER_LONGEST_FIRST, k->rr_rmax, k->rr_per_sm);
     if (s != TWED_OK) return s;
     KNN_CUDA(h, cudaEventRecord(k->ev[3], st));
     KNN_CUDA(h, topk_rows(k->rr.as<float>(), nq, C, C, kk, k->pos.as<int64_t>(), d_dist, topk_grid, st));

@@ -74,7 +74,16 @@ struct PairsArgs {
     int64_t scratch_cols;    // >= longest series + 1, even
     SyncCtl sc;
     int64_t cut_cells = 0;   // > 0: pairs with more cells are skipped (run elsewhere)
+    const int64_t* order = nullptr;  // kExplicitPairs: run position -> pair index (nullptr: identity)
 };
+
+// Longest-first run order of an explicit pair list (order.cu): order[k] is
+// the index of the pair to run k-th, by decreasing len_a * len_b in
+// quarter-octave classes.  bins: kOrderBins device words of scratch.
+constexpr int kOrderBins = 256;
+cudaError_t launch_order_pairs(const int64_t* pairs, int64_t npairs, const int64_t* offs_a,
+                               const int64_t* offs_b, int64_t* order, unsigned long long* bins,
+                               int sms, cudaStream_t st);
 
 // Elements per point record for (dim, p) (16-byte multiple; see Rec<>).
 template <typename T>

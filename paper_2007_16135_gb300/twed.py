@@ -33,7 +33,8 @@ EXPORTS = (
     "twed_create", "twed_destroy", "twed_last_error", "twed_version", "twed_sync_status",
     "twed_f64", "twed_f32", "twed_f32_ex",
     "twed_dev_f64", "twed_dev_f32", "twed_dev_f64_ex", "twed_dev_f32_ex",
-    "twed_batch_f64", "twed_batch_f32", "twed_batch_f32_noalloc",
+    "twed_batch_f64", "twed_batch_f32", "twed_batch_f64_ex", "twed_batch_f32_ex",
+    "twed_batch_f32_noalloc",
     "twed_allpairs_plan_create_f64", "twed_allpairs_plan_create_f32", "twed_plan_execute",
     "twed_plan_cells", "twed_plan_pairs", "twed_plan_kernel_ms", "twed_plan_describe",
     "twed_plan_destroy",
@@ -105,6 +106,8 @@ def load(path: str | None = None):
             "twed_dev_f32_ex": (ci, [P, P, P, i64, P, P, i64, ci, f, f, ci, P, P, P]),
             "twed_batch_f64": (ci, [P, P, P, P, i64, ci, d, d, ci, P, P]),
             "twed_batch_f32": (ci, [P, P, P, P, i64, ci, f, f, ci, P, P]),
+            "twed_batch_f64_ex": (ci, [P, P, P, P, i64, ci, d, d, ci, ci, P, P]),
+            "twed_batch_f32_ex": (ci, [P, P, P, P, i64, ci, f, f, ci, ci, P, P]),
             "twed_batch_f32_noalloc": (ci, [P, P, P, i64, ci, f, f, ci, P, P]),
             "twed_allpairs_plan_create_f64": (ci, [P, P, P, ci, d, d, ci, P, P]),
             "twed_allpairs_plan_create_f32": (ci, [P, P, P, ci, f, f, ci, P, P]),
@@ -306,9 +309,14 @@ class DeviceSet:
                        self.offs_host.ctypes.data, self.n)
 
 
+# run orders of twed_batch (twed.h TWED_ORDER_*)
+ORDER_LIST, ORDER_LONGEST_FIRST = 0, 1
+
+
 def twed_batch(A: DeviceSet, B: DeviceSet, pairs, nu, lam, p=2, out=None, stream=None,
-               handle: Handle | None = None):
-    """TWED of listed pairs (device int64 [k, 2]) -> device tensor [k]."""
+               handle: Handle | None = None, order: int = ORDER_LIST):
+    """TWED of listed pairs (device int64 [k, 2]) -> device tensor [k].
+    `order` picks the run order (ORDER_*); out[k] is pair k's value in any."""
     import torch
     h = handle or default_handle()
     pairs = pairs.contiguous()
@@ -316,9 +324,15 @@ def twed_batch(A: DeviceSet, B: DeviceSet, pairs, nu, lam, p=2, out=None, stream
     if out is None:
         out = torch.empty(k, dtype=A.vals.dtype, device=A.vals.device)
     sa, sb = A.cstruct(), B.cstruct()
-    fn = h.lib.twed_batch_f64 if A.vals.dtype == torch.float64 else h.lib.twed_batch_f32
-    h.check(fn(h.h, ctypes.byref(sa), ctypes.byref(sb), _t_ptr(pairs), k, A.dim, float(nu),
-               float(lam), p, _t_ptr(out), _stream_ptr(stream)))
+    args = (h.h, ctypes.byref(sa), ctypes.byref(sb), _t_ptr(pairs), k, A.dim, float(nu),
+            float(lam), p)
+    f64 = A.vals.dtype == torch.float64
+    if order == ORDER_LIST:
+        fn = h.lib.twed_batch_f64 if f64 else h.lib.twed_batch_f32
+        h.check(fn(*args, _t_ptr(out), _stream_ptr(stream)))
+    else:
+        fn = h.lib.twed_batch_f64_ex if f64 else h.lib.twed_batch_f32_ex
+        h.check(fn(*args, int(order), _t_ptr(out), _stream_ptr(stream)))
     return out
 
 
@@ -455,7 +469,9 @@ class KnnStats(ctypes.Structure):
                 ("label_pairs", ctypes.c_int64), ("mined_pairs", ctypes.c_int64),
                 ("label_cells", ctypes.c_int64),
                 ("steps", ctypes.c_int64), ("label_ms", ctypes.c_double),
-                ("train_ms", ctypes.c_double), ("embed_ms", ctypes.c_double)]
+                ("train_ms", ctypes.c_double), ("embed_ms", ctypes.c_double),
+                ("rerank_rows_per_lane", ctypes.c_int32), ("rerank_blocks_per_sm", ctypes.c_int32),
+                ("tune_ms", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}

@@ -177,3 +177,53 @@ def test_plan_cutover_for_long_pairs(tw, dtype):
         if B is None:
             assert np.all(M == M.T) and np.all(np.diag(M) == 0)
         plan.close()
+
+
+@pytest.mark.parametrize("dtype,dim,p,order", [(np.float64, 1, 2, 1), (np.float64, 3, 1, 1),
+                                               (np.float32, 4, 2, 1), (np.float32, 2, 2, 1),
+                                               (np.float32, 3, 2, 0)])
+def test_explicit_pairs_run_orders(tw, dtype, dim, p, order):
+    """More pairs than resident warps, so the longest-first order goes
+    through the device counting sort; every result must still land at its
+    own pair's position (FP64: bit-exact with the oracle).  The list holds
+    repeated pairs, 1-point series and cell counts from 1 to 4e5, so many
+    size classes are populated."""
+    import torch
+    rng = np.random.default_rng(dim * 7 + p)
+
+    def series(n):
+        return np.cumsum(rng.normal(size=(n, dim)), axis=0), np.cumsum(rng.exponential(1.0, n))
+
+    # series 0 of each set has one point
+    SA = W.pack([series(1)] + [series(int(n)) for n in rng.integers(2, 641, 59)]).astype(dtype)
+    SB = W.pack([series(1)] + [series(int(n)) for n in rng.integers(2, 641, 44)]).astype(dtype)
+    tdt = torch.float64 if dtype == np.float64 else torch.float32
+    A = tw.DeviceSet.from_numpy(SA.vals, SA.ts, SA.offs, tdt)
+    B = tw.DeviceSet.from_numpy(SB.vals, SB.ts, SB.offs, tdt)
+    npairs = 9000
+    pairs = np.stack([rng.integers(0, SA.n, npairs), rng.integers(0, SB.n, npairs)], axis=1)
+    pairs[:50] = pairs[50:100]  # repeated pairs
+    pairs[100:140, 0] = 0       # 1-point rows
+    pairs[140:150] = 0          # 1 x 1
+    out = tw.twed_batch(A, B, torch.as_tensor(pairs).cuda(), 0.7, 0.3, p, order=order)
+    got = out.cpu().numpy()
+    cells = SA.lengths[pairs[:, 0]].astype(np.int64) * SB.lengths[pairs[:, 1]]
+    assert cells.min() == 1 and cells.max() > 100000
+    ref = oracle_matrix(SA, SB, 0.7, 0.3, p, pairs)
+    if dtype == np.float64:
+        if p in (1, 2):
+            assert np.array_equal(got, ref)
+        else:
+            assert rel(got, ref).max() <= 1e-12
+    else:
+        assert rel(got, ref).max() <= 1e-5
+    assert np.array_equal(got[:50], got[50:100])
+
+
+def test_explicit_pairs_unknown_order_rejected(tw):
+    import torch
+    S = ragged_set(5, 4, 3, 9, 2, np.float32)
+    D = tw.DeviceSet.from_numpy(S.vals, S.ts, S.offs, torch.float32)
+    pairs = torch.zeros((3, 2), dtype=torch.int64, device="cuda")
+    with pytest.raises(RuntimeError, match="unknown pair order"):
+        tw.twed_batch(D, D, pairs, 1.0, 1.0, 2, order=2)

@@ -286,6 +286,30 @@ def test_search_with_every_candidate_equals_exact(tw, small_index):
         assert set(idx[q][clear].tolist()) <= set(ex_idx[q].tolist())
 
 
+def test_rerank_launch_shape_is_timed(tw, small_index):
+    _, _, _, _, stats, _ = small_index
+    assert stats["rerank_rows_per_lane"] in (2, 4, 6, 8)
+    assert stats["rerank_blocks_per_sm"] >= 1
+    assert stats["tune_ms"] > 0
+
+
+def test_fresh_index_from_params_searches_alike(tw, small_index):
+    # set_params on an untrained index embeds the database and times the
+    # re-rank shape itself; the search must give the trained index's answer
+    # (the value of a pair does not depend on the launch shape)
+    index, db, _, Q, _, _ = small_index
+    cfg = tw.knn_config(group_size=16, groups_per_step=8, epochs=4, train_pairs=12000, seed=7)
+    other = tw.KnnIndex(dev_set(tw, db), 1.0, 1.0, 2, config=cfg)
+    other.set_params(index.params())
+    st = other.stats()
+    assert st["rerank_rows_per_lane"] in (2, 4, 6, 8) and st["tune_ms"] > 0
+    i0, d0 = index.search(Q, k=10, n_candidates=64)
+    i1, d1 = other.search(Q, k=10, n_candidates=64)
+    np.testing.assert_array_equal(i0.cpu().numpy(), i1.cpu().numpy())
+    np.testing.assert_allclose(d0.cpu().numpy(), d1.cpu().numpy(), rtol=1e-6)
+    other.close()
+
+
 def test_set_params_reembeds(tw, small_index):
     index, db, _, _, _, _ = small_index
     w = index.params()
