@@ -51,8 +51,8 @@ constexpr int ACOL = 64;        // first TMEM column of the A strip
 constexpr int OFF_B = 0;                               // NBB tiles of N*D floats
 constexpr int OFF_C = OFF_B + NBB * N * D * 4;         // NC tiles [N][M] costs
 constexpr int OFF_DEL = OFF_C + NC * N * M * 4;        // NC tiles of N column delete costs
-constexpr int OFF_ROW = OFF_DEL + NC * N * 4;          // MAXCOL float2 boundary row
-constexpr int OFF_BAR = OFF_ROW + MAXCOL * 8;          // mbarriers
+constexpr int OFF_ROW = OFF_DEL + NC * N * 4;          // MAXCOL + 1 float2: boundary row, spare
+constexpr int OFF_BAR = OFF_ROW + (MAXCOL + 1) * 8;    // mbarriers
 constexpr int NBAR = NB + NB + NC + NC + 1;            // mma_done, tmem_empty, cost_full, cost_empty, a_ready
 constexpr int OFF_MISC = OFF_BAR + NBAR * 8;           // tmem base, pair index
 constexpr int SMEM = OFF_MISC + 64;
@@ -376,9 +376,12 @@ __global__ void __launch_bounds__(x64::THREADS) xterm_pairs_kernel(PairsArgs<flo
                     float upD = __shfl_up_sync(kFull, botD, 1);
                     float upC = __shfl_up_sync(kFull, botC, 1);
                     // a lane before column 1 sees an infinite row above and keeps its state
-                    upD = lane == 0 ? (first ? INF : bnd.x) : upD;
-                    upC = lane == 0 ? (first ? 0.f : bnd.y) : upC;
-                    upD = j < 1 ? INF : upD;
+                    // lane 0 reads the row above the strip (for the pair's first
+                    // strip: D(0, j) = inf, c(0, j) = 0).  A lane before column 1
+                    // receives inf from the lane above, so its update keeps every
+                    // value infinite: no test of j is needed.
+                    upD = lane == 0 ? bnd.x : upD;
+                    upC = lane == 0 ? bnd.y : upC;
                     const float cc[R] = {c4.x, c4.y, c4.z, c4.w};
                     float tb_[R], tm_[R];
 #pragma unroll
@@ -399,8 +402,9 @@ __global__ void __launch_bounds__(x64::THREADS) xterm_pairs_kernel(PairsArgs<flo
                     diagC = upC;
                     botD = Dl[R - 1];
                     botC = cp[R - 1];
-                    if (!last && lane == 31 && j >= 1 && j <= m) sRow[j - 1] = make_float2(botD, botC);
-                    __syncwarp();
+                    // lane 31 hands its bottom row to the next strip; columns
+                    // outside 1..m go to the spare entry (no branch)
+                    if (lane == 31) sRow[(j >= 1 && j <= m) ? j - 1 : MAXCOL] = make_float2(botD, botC);
                 };
                 // at step s = N k - 1 lane 0's next prefetch enters tile k, and
                 // lane 31 has read tile k - 3 for the last time
@@ -419,6 +423,10 @@ __global__ void __launch_bounds__(x64::THREADS) xterm_pairs_kernel(PairsArgs<flo
                     }
                     return true;
                 };
+                if (first) {  // the row above the pair: D(0, j) = inf, c(0, j) = 0
+                    for (int c = lane; c < m; c += 32) sRow[c] = make_float2(INF, 0.f);
+                    __syncwarp();
+                }
                 {   // tile 0 must be in before the first prefetch
                     const bool w2 = xwait(&cost_full[cb0], (uint32_t)((t0 / NC) & 1), a.sc);
                     if (!__all_sync(kFull, w2)) ok = false;
