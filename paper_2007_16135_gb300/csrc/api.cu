@@ -142,13 +142,39 @@ twed::SyncCtl make_sync(twed_handle_t h, const twed_opts_t* o) {
     return sc;
 }
 
-// Rows per lane for one long pair: enough strips to give every SM several
+// Warps the FP64 one-pair schedule keeps in flight: at most 4 per SM.
+// Every FP64 operation runs on the FP64 pipe (2 DFMA per SM per clock on
+// this part), so a few warps per SM already keep it busy; more strips in
+// flight only lengthen the fill of the wavefront (each strip trails its
+// predecessor by about kCoopLag columns).
+constexpr int kCoopF64WarpsPerSm = 4;
+constexpr double kCoopLag = 110.0;
+
+// Rows per lane for one long pair.  FP64: a cost model over R in {4, 2, 1}:
+// with W = min(strips, 4 x SMs) warps, the pair takes about
+// (strips / W) x m + W x lag steps, each costing R x (warps per SM) FP64-pipe
+// slots.  FP32 (run-time dimensions): enough strips to give every SM several
 // warps, otherwise the most rows per lane (fewest shuffles per cell).
 template <typename T>
-int coop_rows_per_lane(twed_handle_t h, int64_t n, const twed_opts_t* o) {
+int coop_rows_per_lane(twed_handle_t h, int64_t n, int64_t m, const twed_opts_t* o) {
     if (o && o->rows_per_lane > 0) {
         int r = o->rows_per_lane;
         return r >= 8 ? 8 : r >= 4 ? 4 : r >= 2 ? 2 : 1;
+    }
+    if (sizeof(T) == 8) {
+        int best = 1;
+        double best_t = 1e300;
+        for (int r : {4, 2, 1}) {
+            const double strips = std::ceil((double)n / (32.0 * r));
+            const double W = std::min(strips, (double)kCoopF64WarpsPerSm * h->sms);
+            const double wps = std::ceil(W / h->sms);
+            const double t = (strips / W * (double)m + W * kCoopLag) * r * wps;
+            if (t < best_t * 0.97) {  // ties go to more rows per lane
+                best_t = t;
+                best = r;
+            }
+        }
+        return best;
     }
     const int64_t want_warps = (int64_t)h->sms * 8;
     const int cand[4] = {8, 4, 2, 1};
@@ -223,7 +249,7 @@ PairLayout pair_layout(twed_handle_t h, int64_t n, int64_t m, int dim, int p,
     PairLayout L;
     L.kahan = use_kahan<T>(n, m, dim, p, o);
     L.band = sizeof(T) == 4 && twed::compiled_layout(dim, p);
-    L.R = L.band ? band_rows_per_lane(h, n, m, dim, p, L.kahan, o) : coop_rows_per_lane<T>(h, n, o);
+    L.R = L.band ? band_rows_per_lane(h, n, m, dim, p, L.kahan, o) : coop_rows_per_lane<T>(h, n, m, o);
     L.nstrips = (n + 32 * L.R - 1) / (32 * L.R);
     const int rl = twed::rec_len<T>(dim, p);
     Carver cv;
@@ -257,9 +283,14 @@ twed_status_t launch_pair_schedule(twed_handle_t h, const PairLayout& L, const C
             return TWED_OK;
         }
     }
-    const int threads = 128;
+    // FP64: one warp per block, so the block scheduler spreads the first
+    // strips over separate SMs (a short pair's few strips each get an SM's
+    // FP64 pipe) and at most kCoopF64WarpsPerSm land on one SM
+    const bool f64 = sizeof(T) == 8;
+    const int threads = f64 ? 32 : 128;
     const int per_sm = std::max(1, twed::coop_blocks_per_sm<T>(ca.dim, ca.p, R, L.kahan, threads));
-    int64_t blocks = std::min<int64_t>((L.nstrips + 3) / 4, (int64_t)per_sm * h->sms);
+    int64_t blocks = f64 ? std::min<int64_t>(L.nstrips, (int64_t)std::min(per_sm, kCoopF64WarpsPerSm) * h->sms)
+                         : std::min<int64_t>((L.nstrips + 3) / 4, (int64_t)per_sm * h->sms);
     blocks = std::max<int64_t>(1, blocks);
     TWED_CUDA(h, twed::launch_coop(ca, R, L.kahan, (int)blocks, threads, st));
     return TWED_OK;
