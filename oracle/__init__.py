@@ -14,6 +14,8 @@ Entry points (all values float64; series are ``[len, dim]`` arrays):
 * ``delete_costs(a, ta, nu, lam, p)`` -- dA(1..n) of one series.
 * ``twed_pairs(setA, setB, pairs, dim, nu, lam, p, nthreads)`` -- rolling
   oracle over listed pairs of two packed sets, threads over pairs.
+* ``twed_path(a, ta, b, tb, nu, lam, p)`` -- TWED and an optimal edit path
+  (full matrix, walk back with a fixed tie-break), as a string of moves.
 
 Parity pins for these functions live in ``tests/test_oracle_*.py``.
 """
@@ -57,6 +59,8 @@ def _declare(lib):
         f.argtypes = [P, P, i64, P, P, i64, ci, d, d, ci, P]
     lib.oracle_delete_costs.restype = ci
     lib.oracle_delete_costs.argtypes = [P, P, i64, ci, d, d, ci, P]
+    lib.oracle_twed_path.restype = ci
+    lib.oracle_twed_path.argtypes = [P, P, i64, P, P, i64, ci, d, d, ci, P, P, P]
     lib.oracle_twed_pairs.restype = ci
     lib.oracle_twed_pairs.argtypes = [P, P, P, P, P, P, P, i64, ci, d, d, ci, ci, P]
     return lib
@@ -121,6 +125,29 @@ def twed(a, ta, b, tb, nu, lam, p=2):
 def twed_rolling(a, ta, b, tb, nu, lam, p=2):
     """TWED with two rolling rows; bit-identical to :func:`twed`."""
     return _call(_load().oracle_twed_rolling, a, ta, b, tb, nu, lam, p)
+
+
+def twed_path(a, ta, b, tb, nu, lam, p=2):
+    """TWED and one optimal edit path, ``(value, moves)``.
+
+    ``moves`` lists the steps after the forced first match (0,0) -> (1,1), in
+    order: ``'M'`` match (i+1, j+1), ``'A'`` delete in a (i+1, j), ``'B'``
+    delete in b (i, j+1).  Among optimal paths the one returned is fixed by
+    the walk back from (n,m): at each cell the first of match, delete in a,
+    delete in b whose candidate equals D(i,j)."""
+    a, ta = _series(a, ta)
+    b, tb = _series(b, tb)
+    if a.shape[1] != b.shape[1]:
+        raise ValueError("series dimensions differ")
+    out = np.zeros(1, dtype=np.float64)
+    moves = np.zeros(max(a.shape[0] + b.shape[0] - 2, 1), dtype=np.int8)
+    length = np.zeros(1, dtype=np.int64)
+    rc = _load().oracle_twed_path(_ptr(a), _ptr(ta), a.shape[0], _ptr(b), _ptr(tb), b.shape[0],
+                                  a.shape[1], float(nu), float(lam), int(p), _ptr(out),
+                                  _ptr(moves), _ptr(length))
+    if rc:
+        raise OracleError(f"oracle path failed (status {rc})")
+    return float(out[0]), "".join("MAB"[x] for x in moves[:int(length[0])])
 
 
 def delete_costs(a, ta, nu, lam, p=2):

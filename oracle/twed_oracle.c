@@ -125,16 +125,13 @@ static int bad_args(const double* a, const double* ta, int64_t n, const double* 
     return 0;
 }
 
-/* Full (n+1) x (m+1) matrix, filled in C order (step 5 of the serial TWED).
- * Returns 0 on success, 1 on invalid arguments, 2 on allocation failure. */
-int oracle_twed(const double* a, const double* ta, int64_t n, const double* b, const double* tb,
-                int64_t m, int dim, double nu, double lambda, int p, double* out)
+/* The full (n+1) x (m+1) matrix D, filled in C order (step 5 of the serial
+ * TWED), in a buffer the caller frees.  NULL on allocation failure. */
+static double* twed_matrix(const series_t* A, const series_t* B, double nu, double lambda, int p)
 {
-    if (bad_args(a, ta, n, b, tb, m, dim, nu, lambda, p) || !out) return 1;
-    double* zero = (double*)calloc((size_t)dim, sizeof(double));
+    const int64_t n = A->n, m = B->n;
     double* D = (double*)malloc((size_t)(n + 1) * (size_t)(m + 1) * sizeof(double));
-    if (!zero || !D) { free(zero); free(D); return 2; }
-    series_t A = {a, ta, n, dim, zero}, B = {b, tb, m, dim, zero};
+    if (!D) return NULL;
     const int64_t W = m + 1;
     D[0] = 0.0;
     for (int64_t j = 1; j <= m; ++j) D[j] = INFINITY;
@@ -145,14 +142,14 @@ int oracle_twed(const double* a, const double* ta, int64_t n, const double* b, c
 #endif
     for (int64_t i = 1; i <= n; ++i) {
 #if ORACLE_MUTANT == 5
-        double dA = del_cost(&A, i > 1 ? i - 1 : 1, nu, lambda, p);
+        double dA = del_cost(A, i > 1 ? i - 1 : 1, nu, lambda, p);
 #else
-        double dA = del_cost(&A, i, nu, lambda, p);
+        double dA = del_cost(A, i, nu, lambda, p);
 #endif
         for (int64_t j = 1; j <= m; ++j) {
-            double dB = del_cost(&B, j, nu, lambda, p);
-            double c_ij = cell_cost(&A, i, &B, j, nu, p);
-            double c_prev = cell_cost(&A, i - 1, &B, j - 1, nu, p);
+            double dB = del_cost(B, j, nu, lambda, p);
+            double c_ij = cell_cost(A, i, B, j, nu, p);
+            double c_prev = cell_cost(A, i - 1, B, j - 1, nu, p);
             double delete_a = D[(i - 1) * W + j] + dA;
             double delete_b = D[i * W + (j - 1)] + dB;
 #if ORACLE_MUTANT == 1
@@ -161,7 +158,7 @@ int oracle_twed(const double* a, const double* ta, int64_t n, const double* b, c
 #elif ORACLE_MUTANT == 8
             double match = (D[(i - 1) * W + (j - 1)] + c_ij) - c_prev;
 #elif ORACLE_MUTANT == 9
-            double match = (D[(i - 1) * W + (j - 1)] + c_ij) + cell_cost(&A, i - 1, &B, j, nu, p);
+            double match = (D[(i - 1) * W + (j - 1)] + c_ij) + cell_cost(A, i - 1, B, j, nu, p);
             (void)c_prev;
 #else
             double match = (D[(i - 1) * W + (j - 1)] + c_ij) + c_prev;
@@ -169,10 +166,85 @@ int oracle_twed(const double* a, const double* ta, int64_t n, const double* b, c
             D[i * W + j] = min3(delete_a, delete_b, match);
         }
     }
-    *out = D[n * W + m];
+    return D;
+}
+
+/* TWED by the full matrix.
+ * Returns 0 on success, 1 on invalid arguments, 2 on allocation failure. */
+int oracle_twed(const double* a, const double* ta, int64_t n, const double* b, const double* tb,
+                int64_t m, int dim, double nu, double lambda, int p, double* out)
+{
+    if (bad_args(a, ta, n, b, tb, m, dim, nu, lambda, p) || !out) return 1;
+    double* zero = (double*)calloc((size_t)dim, sizeof(double));
+    if (!zero) return 2;
+    series_t A = {a, ta, n, dim, zero}, B = {b, tb, m, dim, zero};
+    double* D = twed_matrix(&A, &B, nu, lambda, p);
+    if (!D) { free(zero); return 2; }
+    *out = D[n * (m + 1) + m];
     free(D);
     free(zero);
     return 0;
+}
+
+/* An optimal edit path (the alignment that the paper's introduction says a
+ * TWED solver can report): the full matrix above, then a walk back from
+ * (n,m) to (1,1).  At each cell the predecessor is the first of
+ *   match (i-1,j-1), delete in a (i-1,j), delete in b (i,j-1)
+ * whose candidate value -- recomputed with the same operations as the fill
+ * -- equals D(i,j).  Every finite path starts with the forced match
+ * (0,0) -> (1,1) (the border is infinite), so only the moves after it are
+ * returned, in forward order: moves[k] = 0 (match), 1 (delete in a),
+ * 2 (delete in b); *len receives their number (at most n + m - 2, the room
+ * `moves` must have).  *out receives D(n,m), as oracle_twed.
+ * Returns 0 on success, 1 on invalid arguments, 2 on allocation failure,
+ * 3 if no predecessor matches (cannot happen for finite inputs). */
+int oracle_twed_path(const double* a, const double* ta, int64_t n, const double* b,
+                     const double* tb, int64_t m, int dim, double nu, double lambda, int p,
+                     double* out, int8_t* moves, int64_t* len)
+{
+    if (bad_args(a, ta, n, b, tb, m, dim, nu, lambda, p) || !out || !moves || !len) return 1;
+    double* zero = (double*)calloc((size_t)dim, sizeof(double));
+    if (!zero) return 2;
+    series_t A = {a, ta, n, dim, zero}, B = {b, tb, m, dim, zero};
+    double* D = twed_matrix(&A, &B, nu, lambda, p);
+    if (!D) { free(zero); return 2; }
+    const int64_t W = m + 1;
+    int64_t i = n, j = m, k = 0;
+    int rc = 0;
+    while (i > 1 || j > 1) {
+        const double here = D[i * W + j];
+        double match = INFINITY;
+        if (i > 1 && j > 1)
+            match = (D[(i - 1) * W + (j - 1)] + cell_cost(&A, i, &B, j, nu, p)) +
+                    cell_cost(&A, i - 1, &B, j - 1, nu, p);
+        const double delete_a = i > 1 ? D[(i - 1) * W + j] + del_cost(&A, i, nu, lambda, p) : INFINITY;
+        const double delete_b = j > 1 ? D[i * W + (j - 1)] + del_cost(&B, j, nu, lambda, p) : INFINITY;
+        if (match == here) {
+            moves[k++] = 0;
+            --i;
+            --j;
+        } else if (delete_a == here) {
+            moves[k++] = 1;
+            --i;
+        } else if (delete_b == here) {
+            moves[k++] = 2;
+            --j;
+        } else {
+            rc = 3;
+            break;
+        }
+    }
+    /* the walk collected the moves backwards */
+    for (int64_t x = 0, y = k - 1; x < y; ++x, --y) {
+        const int8_t t = moves[x];
+        moves[x] = moves[y];
+        moves[y] = t;
+    }
+    *len = k;
+    *out = D[n * W + m];
+    free(D);
+    free(zero);
+    return rc;
 }
 
 /* The same operations in the same order, keeping only rows i-1 and i
