@@ -16,6 +16,9 @@ Entry points (all values float64; series are ``[len, dim]`` arrays):
   oracle over listed pairs of two packed sets, threads over pairs.
 * ``twed_path(a, ta, b, tb, nu, lam, p)`` -- TWED and an optimal edit path
   (full matrix, walk back with a fixed tie-break), as a string of moves.
+* ``lcs_length(x, y)``, ``lcs_length_rolling(x, y)``, ``lcs_pairs(x, y)`` --
+  longest common subsequence of int32 sequences (``lcs_oracle.c``): its
+  length (full matrix / two rows) and one subsequence.
 
 Parity pins for these functions live in ``tests/test_oracle_*.py``.
 """
@@ -30,6 +33,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "twed_oracle.c")
+_SRC_LCS = os.path.join(_HERE, "lcs_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
@@ -43,9 +47,10 @@ CFLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-st
 def build(force: bool = False) -> str:
     """Compile the oracle shared library with gcc (seconds)."""
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_LCS))
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm", "-lpthread"])
+        subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, _SRC, _SRC_LCS, "-lm", "-lpthread"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -61,6 +66,12 @@ def _declare(lib):
     lib.oracle_delete_costs.argtypes = [P, P, i64, ci, d, d, ci, P]
     lib.oracle_twed_path.restype = ci
     lib.oracle_twed_path.argtypes = [P, P, i64, P, P, i64, ci, d, d, ci, P, P, P]
+    for name in ("oracle_lcs_length", "oracle_lcs_length_rolling"):
+        f = getattr(lib, name)
+        f.restype = ci
+        f.argtypes = [P, i64, P, i64, P]
+    lib.oracle_lcs_pairs.restype = ci
+    lib.oracle_lcs_pairs.argtypes = [P, i64, P, i64, P, P, P]
     lib.oracle_twed_pairs.restype = ci
     lib.oracle_twed_pairs.argtypes = [P, P, P, P, P, P, P, i64, ci, d, d, ci, ci, P]
     return lib
@@ -148,6 +159,47 @@ def twed_path(a, ta, b, tb, nu, lam, p=2):
     if rc:
         raise OracleError(f"oracle path failed (status {rc})")
     return float(out[0]), "".join("MAB"[x] for x in moves[:int(length[0])])
+
+
+def _symbols(x):
+    return np.ascontiguousarray(np.asarray(x, dtype=np.int32).ravel())
+
+
+def _lcs_call(fn, x, y):
+    x, y = _symbols(x), _symbols(y)
+    out = np.zeros(1, dtype=np.int64)
+    rc = fn(_ptr(x), x.size, _ptr(y), y.size, _ptr(out))
+    if rc:
+        raise OracleError(f"LCS oracle failed (status {rc})")
+    return int(out[0])
+
+
+def lcs_length(x, y):
+    """Length of a longest common subsequence of two int32 symbol sequences
+    (full matrix)."""
+    return _lcs_call(_load().oracle_lcs_length, x, y)
+
+
+def lcs_length_rolling(x, y):
+    """As :func:`lcs_length` on two rows of memory."""
+    return _lcs_call(_load().oracle_lcs_length_rolling, x, y)
+
+
+def lcs_pairs(x, y):
+    """One longest common subsequence as matched positions ``(xi, yj)``
+    (0-based, increasing), by the textbook walk back: diagonal on a match,
+    else up when L(i-1,j) >= L(i,j-1), else left."""
+    x, y = _symbols(x), _symbols(y)
+    k = max(min(x.size, y.size), 1)
+    xi = np.zeros(k, dtype=np.int64)
+    yj = np.zeros(k, dtype=np.int64)
+    length = np.zeros(1, dtype=np.int64)
+    rc = _load().oracle_lcs_pairs(_ptr(x), x.size, _ptr(y), y.size, _ptr(xi), _ptr(yj),
+                                  _ptr(length))
+    if rc:
+        raise OracleError(f"LCS oracle failed (status {rc})")
+    n = int(length[0])
+    return xi[:n].copy(), yj[:n].copy()
 
 
 def delete_costs(a, ta, nu, lam, p=2):
