@@ -92,7 +92,7 @@ def build_variant(out_dir: str, defines: dict) -> "callable":
     tag = "_".join(f"{k}{v}" for k, v in sorted(defines.items()))
     path = os.path.join(out_dir, f"liboracle_{tag}.so")
     flags = [f"-D{k}={v}" for k, v in defines.items()]
-    subprocess.check_call(["gcc", *CFLAGS, *flags, "-o", path, _SRC, "-lm", "-lpthread"])
+    subprocess.check_call(["gcc", *CFLAGS, *flags, "-o", path, _SRC, _SRC_LCS, "-lm", "-lpthread"])
     lib = _declare(ctypes.CDLL(path))
     return lambda a, ta, b, tb, nu, lam, p=2: _call(lib.oracle_twed, a, ta, b, tb, nu, lam, p)
 
