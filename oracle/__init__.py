@@ -19,6 +19,7 @@ Entry points (all values float64; series are ``[len, dim]`` arrays):
 * ``lcs_length(x, y)``, ``lcs_length_rolling(x, y)``, ``lcs_pairs(x, y)`` --
   longest common subsequence of int32 sequences (``lcs_oracle.c``): its
   length (full matrix / two rows) and one subsequence.
+* ``dtw(a, b, p)`` -- dynamic time warping distance (``dtw_oracle.c``).
 
 Parity pins for these functions live in ``tests/test_oracle_*.py``.
 """
@@ -34,6 +35,8 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "twed_oracle.c")
 _SRC_LCS = os.path.join(_HERE, "lcs_oracle.c")
+_SRC_DTW = os.path.join(_HERE, "dtw_oracle.c")
+_SOURCES = [_SRC, _SRC_LCS, _SRC_DTW]
 _BUILD = os.path.join(_HERE, "_build")
 _LIB = os.path.join(_BUILD, "liboracle.so")
 _lock = threading.Lock()
@@ -47,10 +50,10 @@ CFLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-st
 def build(force: bool = False) -> str:
     """Compile the oracle shared library with gcc (seconds)."""
     os.makedirs(_BUILD, exist_ok=True)
-    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_LCS))
+    newest = max(os.path.getmtime(f) for f in _SOURCES)
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, _SRC, _SRC_LCS, "-lm", "-lpthread"])
+        subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, *_SOURCES, "-lm", "-lpthread"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -70,6 +73,8 @@ def _declare(lib):
         f = getattr(lib, name)
         f.restype = ci
         f.argtypes = [P, i64, P, i64, P]
+    lib.oracle_dtw.restype = ci
+    lib.oracle_dtw.argtypes = [P, i64, P, i64, ci, ci, P]
     lib.oracle_lcs_pairs.restype = ci
     lib.oracle_lcs_pairs.argtypes = [P, i64, P, i64, P, P, P]
     lib.oracle_twed_pairs.restype = ci
@@ -92,7 +97,7 @@ def build_variant(out_dir: str, defines: dict) -> "callable":
     tag = "_".join(f"{k}{v}" for k, v in sorted(defines.items()))
     path = os.path.join(out_dir, f"liboracle_{tag}.so")
     flags = [f"-D{k}={v}" for k, v in defines.items()]
-    subprocess.check_call(["gcc", *CFLAGS, *flags, "-o", path, _SRC, _SRC_LCS, "-lm", "-lpthread"])
+    subprocess.check_call(["gcc", *CFLAGS, *flags, "-o", path, *_SOURCES, "-lm", "-lpthread"])
     lib = _declare(ctypes.CDLL(path))
     return lambda a, ta, b, tb, nu, lam, p=2: _call(lib.oracle_twed, a, ta, b, tb, nu, lam, p)
 
@@ -200,6 +205,22 @@ def lcs_pairs(x, y):
         raise OracleError(f"LCS oracle failed (status {rc})")
     n = int(length[0])
     return xi[:n].copy(), yj[:n].copy()
+
+
+def dtw(a, b, p=2):
+    """Dynamic time warping distance of two ``[len, dim]`` series with the lp
+    point distance (full matrix, ``dtw_oracle.c``)."""
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    a = a[:, None] if a.ndim == 1 else a
+    b = b[:, None] if b.ndim == 1 else b
+    if a.shape[1] != b.shape[1]:
+        raise ValueError("series dimensions differ")
+    out = np.zeros(1, dtype=np.float64)
+    rc = _load().oracle_dtw(_ptr(a), a.shape[0], _ptr(b), b.shape[0], a.shape[1], int(p), _ptr(out))
+    if rc:
+        raise OracleError(f"DTW oracle rejected its arguments (status {rc})")
+    return float(out[0])
 
 
 def delete_costs(a, ta, nu, lam, p=2):
