@@ -741,6 +741,7 @@ def main():
                           "value": kn["value"], "unit": kn["unit"],
                           "ms_per_step": kn["ms_per_step"], **kn["knn"],
                           "e2e": kn.get("e2e"), "cpu_baseline": kn.get("cpu_baseline"),
+                          "error_vs_oracle": kn.get("error_vs_oracle"),
                           "roofline": kn["roofline"], "clocks": kn["clocks"],
                           "config": kn["config"]}
     elif args.workload == "w5":
