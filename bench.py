@@ -403,6 +403,43 @@ def bench_plan(args, rank, world, dev, workload):
     return res
 
 
+def pair_cpu_leg(a, ta, b, tb, nu, lam, p, dtype, result, seconds):
+    """CPU leg of a one-pair line: the FP64 rolling oracle timed on this
+    pair (whole, or its first rows when the whole would take longer than
+    about `seconds`), and the error of the GPU `result` against the oracle's
+    value of the whole pair -- computed when small, else the stored value
+    that tests/golden/make_w2_expected.py wrote for the 1e5-point w2 pair."""
+    import oracle
+    cast = (lambda x: np.asarray(x, dtype=np.float32).astype(np.float64)) if dtype == "f32" \
+        else (lambda x: np.asarray(x, dtype=np.float64))
+    a, ta, b, tb = cast(a), cast(ta), cast(b), cast(tb)
+    n, m = len(ta), len(tb)
+    # rows for about `seconds` at a first guess of 0.1 GCUPS on one core
+    rows = int(max(1, min(n, seconds * 1e8 / m)))
+    t0 = time.perf_counter()
+    part = oracle.twed_rolling(a[:rows], ta[:rows], b, tb, nu, lam, p)
+    el = time.perf_counter() - t0
+    cpu = {"value": rows * m / el / 1e9, "unit": "GCUPS", "cores": 1, "kind": "oracle",
+           "sample": (f"the whole pair ({rows} x {m} cells, {el:.2f} s)" if rows == n else
+                      f"the first {rows} of {n} rows against all {m} columns ({el:.2f} s)")
+                     + ", FP64 rolling-row oracle, one thread"}
+    want = None
+    if rows == n:
+        want, how = part, "oracle on the whole pair"
+    else:
+        with open(os.path.join(ROOT, "tests", "golden", "w2_oracle.json")) as f:
+            g = json.load(f)
+        if (g["n"], g["m"]) == (n, m):
+            want = g["f32_rounded_inputs" if dtype == "f32" else "f64_inputs"]
+            how = "stored oracle value (tests/golden/w2_oracle.json)"
+    if want is None:
+        err = {"note": f"no oracle value for a {n} x {m} pair (too large to compute here)"}
+    else:
+        err = {"rel": abs(result - want) / abs(want), "oracle": want, "how": how,
+               "bound": 1e-12 if dtype == "f64" else 1e-5}
+    return cpu, err
+
+
 def bench_pair(args, rank, world, dev, workload):
     """One long pair through twed_dev (the one-pair kernel)."""
     import torch
@@ -469,6 +506,9 @@ def bench_pair(args, rank, world, dev, workload):
                                          f"FP64 lanes x {sm_max:.0f} MHz",
                            "peak_measured": mp / 1e12,
                            "frac_of_measured": cells * opc / (ms / 1e3) / mp}
+    if rank == 0 and not args.no_cpu:
+        res["cpu_baseline"], res["error_vs_oracle"] = pair_cpu_leg(
+            a, ta, b, tb, nu, lam, p, dtype, res["result"], args.cpu_seconds)
     res["config"] = {"workload": f"{workload} one pair n=m={n}, dim {dim}, {dtype}"
                                  + (", compensated (TwoSum) FP32 running cost" if kahan else ""),
                      "n": n, "accumulation": "kahan" if kahan else dtype,
