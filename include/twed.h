@@ -171,9 +171,11 @@ twed_status_t twed_batch_f32(twed_handle_t handle, const twed_set_f32_t* A,
  *                             whatever locality the caller built into it;
  *   TWED_ORDER_LONGEST_FIRST  decreasing len_a * len_b (quarter-octave
  *                             classes), so the largest pairs do not start last.
- * Reordering is a device counting sort (workspace: 8 bytes per pair), done
- * only when there are more pairs than resident warps.  d_out[k] is always
- * pair k's value, and values do not depend on the order. */
+ * Reordering is a device counting sort (workspace: 8 bytes per pair, in the
+ * handle's workspace), done only when there are more pairs than resident
+ * warps.  d_out[k] is always pair k's value, and values do not depend on
+ * the order.  Arguments, ownership and errors as twed_batch_*; an unknown
+ * `order` returns TWED_ERR_INVALID_ARG. */
 #define TWED_ORDER_LIST 0
 #define TWED_ORDER_LONGEST_FIRST 1
 twed_status_t twed_batch_f64_ex(twed_handle_t handle, const twed_set_f64_t* A,
