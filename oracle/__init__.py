@@ -90,16 +90,26 @@ def _load():
     return _lib
 
 
-def build_variant(out_dir: str, defines: dict) -> "callable":
-    """Compile the oracle with extra -D defines into ``out_dir`` and return its
-    full-matrix ``twed`` function.  Used only by the pin-strength test, which
-    plants mistakes (``ORACLE_MUTANT``) and checks that the pins catch them."""
+def _variant_lib(out_dir: str, defines: dict):
     tag = "_".join(f"{k}{v}" for k, v in sorted(defines.items()))
     path = os.path.join(out_dir, f"liboracle_{tag}.so")
     flags = [f"-D{k}={v}" for k, v in defines.items()]
     subprocess.check_call(["gcc", *CFLAGS, *flags, "-o", path, *_SOURCES, "-lm", "-lpthread"])
-    lib = _declare(ctypes.CDLL(path))
+    return _declare(ctypes.CDLL(path))
+
+
+def build_variant(out_dir: str, defines: dict) -> "callable":
+    """Compile the oracle with extra -D defines into ``out_dir`` and return its
+    full-matrix ``twed`` function.  Used only by the pin-strength tests, which
+    plant mistakes (``ORACLE_MUTANT``) and check that the pins catch them."""
+    lib = _variant_lib(out_dir, defines)
     return lambda a, ta, b, tb, nu, lam, p=2: _call(lib.oracle_twed, a, ta, b, tb, nu, lam, p)
+
+
+def build_path_variant(out_dir: str, defines: dict) -> "callable":
+    """As :func:`build_variant`, returning the variant's ``twed_path``."""
+    lib = _variant_lib(out_dir, defines)
+    return lambda a, ta, b, tb, nu, lam, p=2: _path_call(lib, a, ta, b, tb, nu, lam, p)
 
 
 def _series(a, ta):
@@ -151,6 +161,10 @@ def twed_path(a, ta, b, tb, nu, lam, p=2):
     delete in b (i, j+1).  Among optimal paths the one returned is fixed by
     the walk back from (n,m): at each cell the first of match, delete in a,
     delete in b whose candidate equals D(i,j)."""
+    return _path_call(_load(), a, ta, b, tb, nu, lam, p)
+
+
+def _path_call(lib, a, ta, b, tb, nu, lam, p):
     a, ta = _series(a, ta)
     b, tb = _series(b, tb)
     if a.shape[1] != b.shape[1]:
@@ -158,9 +172,9 @@ def twed_path(a, ta, b, tb, nu, lam, p=2):
     out = np.zeros(1, dtype=np.float64)
     moves = np.zeros(max(a.shape[0] + b.shape[0] - 2, 1), dtype=np.int8)
     length = np.zeros(1, dtype=np.int64)
-    rc = _load().oracle_twed_path(_ptr(a), _ptr(ta), a.shape[0], _ptr(b), _ptr(tb), b.shape[0],
-                                  a.shape[1], float(nu), float(lam), int(p), _ptr(out),
-                                  _ptr(moves), _ptr(length))
+    rc = lib.oracle_twed_path(_ptr(a), _ptr(ta), a.shape[0], _ptr(b), _ptr(tb), b.shape[0],
+                              a.shape[1], float(nu), float(lam), int(p), _ptr(out),
+                              _ptr(moves), _ptr(length))
     if rc:
         raise OracleError(f"oracle path failed (status {rc})")
     return float(out[0]), "".join("MAB"[x] for x in moves[:int(length[0])])

@@ -219,6 +219,19 @@ int oracle_twed_path(const double* a, const double* ta, int64_t n, const double*
                     cell_cost(&A, i - 1, &B, j - 1, nu, p);
         const double delete_a = i > 1 ? D[(i - 1) * W + j] + del_cost(&A, i, nu, lambda, p) : INFINITY;
         const double delete_b = j > 1 ? D[i * W + (j - 1)] + del_cost(&B, j, nu, lambda, p) : INFINITY;
+#if ORACLE_MUTANT == 10
+        /* planted: delete in b tried before delete in a */
+        if (match == here) { moves[k++] = 0; --i; --j; }
+        else if (delete_b == here) { moves[k++] = 2; --j; }
+        else if (delete_a == here) { moves[k++] = 1; --i; }
+        else { rc = 3; break; }
+#elif ORACLE_MUTANT == 11
+        /* planted: delete in a tried before the match */
+        if (delete_a == here) { moves[k++] = 1; --i; }
+        else if (match == here) { moves[k++] = 0; --i; --j; }
+        else if (delete_b == here) { moves[k++] = 2; --j; }
+        else { rc = 3; break; }
+#else
         if (match == here) {
             moves[k++] = 0;
             --i;
@@ -233,8 +246,12 @@ int oracle_twed_path(const double* a, const double* ta, int64_t n, const double*
             rc = 3;
             break;
         }
+#endif
     }
     /* the walk collected the moves backwards */
+#if ORACLE_MUTANT == 12
+    if (0)  /* planted: the moves are left in walk order */
+#endif
     for (int64_t x = 0, y = k - 1; x < y; ++x, --y) {
         const int8_t t = moves[x];
         moves[x] = moves[y];

@@ -65,6 +65,26 @@ def test_tie_break_takes_delete_in_a_before_delete_in_b():
     assert moves == "BA"
 
 
+# Every cost zero (zero values, nu = lambda = 0): every path costs 0 and all
+# finite candidates tie, so the walk-back rule alone fixes the path.  By hand:
+# 2 x 2: at (2,2) the match is tried first -> "M".  4 x 2: (4,2) match from
+# (3,1); at (3,1) the match would come from the infinite border, so delete in
+# a from (2,1), then again from (1,1) -> forward "AAM".  2 x 4: (2,4) match
+# from (1,3); in row 1 only deletes in b are finite -> "BBM".
+ALL_TIES = [((2, 2), "M"), ((4, 2), "AAM"), ((2, 4), "BBM")]
+
+
+def _all_ties_path(twed_path, n, m):
+    return twed_path(np.zeros((n, 1)), np.arange(1.0, n + 1), np.zeros((m, 1)),
+                     np.arange(1.0, m + 1), 0.0, 0.0, 2)
+
+
+@pytest.mark.parametrize("shape,path", ALL_TIES)
+def test_all_ties_follow_the_walk_back_order(shape, path):
+    value, moves = _all_ties_path(oracle.twed_path, *shape)
+    assert value == 0.0 and moves == path
+
+
 def test_identical_series_align_point_to_point():
     rng = np.random.default_rng(5)
     a = np.cumsum(rng.normal(size=(17, 3)), axis=0)
@@ -113,3 +133,50 @@ def test_longer_paths_cost_the_distance(n, m, dim, p):
 def test_path_rejects_bad_arguments():
     with pytest.raises(oracle.OracleError):
         oracle.twed_path([[0.0]], [0.0], [[1.0]], [0.0], -1.0, 0.0, 2)
+
+
+# ------------------------------------------------------------ pin strength
+PATH_MUTANTS = {
+    10: "walk tries delete in b before delete in a",
+    11: "walk tries delete in a before the match",
+    12: "moves returned in walk (reverse) order",
+}
+
+
+def _path_pins(twed_path):
+    """Name of the first path pin that `twed_path` fails, or None."""
+    cases = {c["name"]: c for c in json.load(open(os.path.join(GOLDEN, "hand_worked.json")))["cases"]}
+    for p in json.load(open(os.path.join(GOLDEN, "hand_worked_paths.json")))["cases"]:
+        c = cases[p["name"]]
+        if twed_path(c["a"], c["ta"], c["b"], c["tb"], c["nu"], c["lam"], c["p"])[1] != p["path"]:
+            return "hand:" + p["name"]
+    if twed_path([[0.0], [0.0]], [1.0, 2.0], [[10.0], [10.0]], [1.0, 2.0], 0.0, 0.0, 2)[1] != "BA":
+        return "tie-break"
+    for shape, path in ALL_TIES:
+        if _all_ties_path(twed_path, *shape)[1] != path:
+            return "all-ties"
+    rng = np.random.default_rng(77)
+    for _ in range(30):
+        n, m = int(rng.integers(1, 6)), int(rng.integers(1, 6))
+        a, b = rng.normal(size=(n, 2)), rng.normal(size=(m, 2))
+        ta, tb = np.cumsum(rng.exponential(1.0, n)), np.cumsum(rng.exponential(1.0, m))
+        _, moves = twed_path(a, ta, b, tb, 0.4, 0.6, 2)
+        if not valid(moves, n, m):
+            return "validity"
+        try:
+            cost = path_cost(moves, a, ta, b, tb, 0.4, 0.6, 2)
+        except AssertionError:
+            return "validity"
+        if cost != pytest.approx(twed_bruteforce(a, ta, b, tb, 0.4, 0.6, 2), rel=1e-12):
+            return "bruteforce"
+    return None
+
+
+def test_real_path_oracle_passes_every_path_pin():
+    assert _path_pins(oracle.twed_path) is None
+
+
+@pytest.mark.parametrize("k", sorted(PATH_MUTANTS), ids=lambda k: PATH_MUTANTS[k])
+def test_planted_path_mistake_is_caught(k, tmp_path):
+    mutant = oracle.build_path_variant(str(tmp_path), {"ORACLE_MUTANT": k})
+    assert _path_pins(mutant) is not None, f"no pin rejects: {PATH_MUTANTS[k]}"
