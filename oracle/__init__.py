@@ -106,6 +106,12 @@ def build_variant(out_dir: str, defines: dict) -> "callable":
     return lambda a, ta, b, tb, nu, lam, p=2: _call(lib.oracle_twed, a, ta, b, tb, nu, lam, p)
 
 
+def build_lib_variant(out_dir: str, defines: dict):
+    """The whole variant library (every entry point declared), for the
+    pin-strength tests of the LCS and DTW oracles."""
+    return _variant_lib(out_dir, defines)
+
+
 def build_path_variant(out_dir: str, defines: dict) -> "callable":
     """As :func:`build_variant`, returning the variant's ``twed_path``."""
     lib = _variant_lib(out_dir, defines)
@@ -193,37 +199,38 @@ def _lcs_call(fn, x, y):
     return int(out[0])
 
 
-def lcs_length(x, y):
+def lcs_length(x, y, lib=None):
     """Length of a longest common subsequence of two int32 symbol sequences
-    (full matrix)."""
-    return _lcs_call(_load().oracle_lcs_length, x, y)
+    (full matrix).  `lib`: a variant library (pin-strength tests only)."""
+    return _lcs_call((lib or _load()).oracle_lcs_length, x, y)
 
 
-def lcs_length_rolling(x, y):
+def lcs_length_rolling(x, y, lib=None):
     """As :func:`lcs_length` on two rows of memory."""
-    return _lcs_call(_load().oracle_lcs_length_rolling, x, y)
+    return _lcs_call((lib or _load()).oracle_lcs_length_rolling, x, y)
 
 
-def lcs_pairs(x, y):
+def lcs_pairs(x, y, lib=None):
     """One longest common subsequence as matched positions ``(xi, yj)``
     (0-based, increasing), by the textbook walk back: diagonal on a match,
     else up when L(i-1,j) >= L(i,j-1), else left."""
+    lib = lib or _load()
     x, y = _symbols(x), _symbols(y)
     k = max(min(x.size, y.size), 1)
     xi = np.zeros(k, dtype=np.int64)
     yj = np.zeros(k, dtype=np.int64)
     length = np.zeros(1, dtype=np.int64)
-    rc = _load().oracle_lcs_pairs(_ptr(x), x.size, _ptr(y), y.size, _ptr(xi), _ptr(yj),
-                                  _ptr(length))
+    rc = lib.oracle_lcs_pairs(_ptr(x), x.size, _ptr(y), y.size, _ptr(xi), _ptr(yj), _ptr(length))
     if rc:
         raise OracleError(f"LCS oracle failed (status {rc})")
     n = int(length[0])
     return xi[:n].copy(), yj[:n].copy()
 
 
-def dtw(a, b, p=2):
+def dtw(a, b, p=2, lib=None):
     """Dynamic time warping distance of two ``[len, dim]`` series with the lp
-    point distance (full matrix, ``dtw_oracle.c``)."""
+    point distance (full matrix, ``dtw_oracle.c``).  `lib`: a variant
+    library (pin-strength tests only)."""
     a = np.ascontiguousarray(a, dtype=np.float64)
     b = np.ascontiguousarray(b, dtype=np.float64)
     a = a[:, None] if a.ndim == 1 else a
@@ -231,7 +238,8 @@ def dtw(a, b, p=2):
     if a.shape[1] != b.shape[1]:
         raise ValueError("series dimensions differ")
     out = np.zeros(1, dtype=np.float64)
-    rc = _load().oracle_dtw(_ptr(a), a.shape[0], _ptr(b), b.shape[0], a.shape[1], int(p), _ptr(out))
+    rc = (lib or _load()).oracle_dtw(_ptr(a), a.shape[0], _ptr(b), b.shape[0], a.shape[1], int(p),
+                                     _ptr(out))
     if rc:
         raise OracleError(f"DTW oracle rejected its arguments (status {rc})")
     return float(out[0])

@@ -57,3 +57,35 @@ def test_closed_forms():
     assert oracle.dtw(np.full(7, 1.5), np.full(4, -0.5)) == pytest.approx(7 * 2.0)
     # a stretched copy: repeating points costs nothing
     assert oracle.dtw(np.repeat(a, 2, axis=0), a) == 0.0
+
+
+# ------------------------------------------------------------ pin strength
+DTW_MUTANTS = {
+    30: "the left neighbour is left out of the minimum",
+    31: "the best predecessor is halved",
+    32: "the 1-D point distance is squared",
+}
+
+
+def _dtw_pins(lib):
+    """Name of the first DTW pin that the variant `lib` fails, or None."""
+    if oracle.dtw([0.0, 1.0, 2.0], [0.0, 2.0], lib=lib) != 1.0:
+        return "hand"
+    rng = np.random.default_rng(321)
+    for _ in range(30):
+        n, m = int(rng.integers(1, 6)), int(rng.integers(1, 6))
+        dim, p = int(rng.integers(1, 3)), int(rng.choice([1, 2]))
+        a, b = rng.normal(size=(n, dim)), rng.normal(size=(m, dim))
+        if oracle.dtw(a, b, p, lib=lib) != pytest.approx(brute_dtw(a, b, p), rel=1e-12):
+            return "bruteforce"
+    return None
+
+
+def test_real_dtw_oracle_passes_every_pin(tmp_path):
+    assert _dtw_pins(oracle.build_lib_variant(str(tmp_path), {"ORACLE_MUTANT": 0})) is None
+
+
+@pytest.mark.parametrize("k", sorted(DTW_MUTANTS), ids=lambda k: DTW_MUTANTS[k])
+def test_planted_dtw_mistake_is_caught(k, tmp_path):
+    lib = oracle.build_lib_variant(str(tmp_path), {"ORACLE_MUTANT": k})
+    assert _dtw_pins(lib) is not None, f"no pin rejects: {DTW_MUTANTS[k]}"

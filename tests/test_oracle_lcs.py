@@ -83,3 +83,41 @@ def test_rolling_equals_full(n, m, alphabet):
     assert oracle.lcs_length_rolling(x, y) == full
     xi, yj = oracle.lcs_pairs(x, y)
     assert len(xi) == full and np.array_equal(x[xi], y[yj])
+
+
+# ------------------------------------------------------------ pin strength
+LCS_MUTANTS = {
+    20: "walk goes left on ties",
+    21: "equal symbols extend the cell above instead of the diagonal",
+    22: "rolling rows read the up-left cell for the up cell",
+}
+
+
+def _lcs_pins(lib):
+    """Name of the first LCS pin that the variant `lib` fails, or None."""
+    for c in json.load(open(os.path.join(GOLDEN, "lcs_hand_worked.json")))["cases"]:
+        x, y = codes(c["x"]), codes(c["y"])
+        if oracle.lcs_length(x, y, lib) != c["length"] or \
+                oracle.lcs_length_rolling(x, y, lib) != c["length"]:
+            return "hand-length:" + c["name"]
+        xi, yj = oracle.lcs_pairs(x, y, lib)
+        if xi.tolist() != c["xi"] or yj.tolist() != c["yj"]:
+            return "hand-walk:" + c["name"]
+    rng = np.random.default_rng(123)
+    for _ in range(40):
+        x = rng.integers(0, 3, int(rng.integers(0, 9))).tolist()
+        y = rng.integers(0, 3, int(rng.integers(0, 9))).tolist()
+        want = brute_lcs(x, y)
+        if oracle.lcs_length(x, y, lib) != want or oracle.lcs_length_rolling(x, y, lib) != want:
+            return "bruteforce"
+    return None
+
+
+def test_real_lcs_oracle_passes_every_pin(tmp_path):
+    assert _lcs_pins(oracle.build_lib_variant(str(tmp_path), {"ORACLE_MUTANT": 0})) is None
+
+
+@pytest.mark.parametrize("k", sorted(LCS_MUTANTS), ids=lambda k: LCS_MUTANTS[k])
+def test_planted_lcs_mistake_is_caught(k, tmp_path):
+    lib = oracle.build_lib_variant(str(tmp_path), {"ORACLE_MUTANT": k})
+    assert _lcs_pins(lib) is not None, f"no pin rejects: {LCS_MUTANTS[k]}"
