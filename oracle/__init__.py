@@ -90,31 +90,26 @@ def _load():
     return _lib
 
 
-def _variant_lib(out_dir: str, defines: dict):
-    tag = "_".join(f"{k}{v}" for k, v in sorted(defines.items()))
-    path = os.path.join(out_dir, f"liboracle_{tag}.so")
-    flags = [f"-D{k}={v}" for k, v in defines.items()]
-    subprocess.check_call(["gcc", *CFLAGS, *flags, "-o", path, *_SOURCES, "-lm", "-lpthread"])
-    return _declare(ctypes.CDLL(path))
+def compile_library(out_path: str, sources) -> ctypes.CDLL:
+    """Compile the given oracle sources (the files of ``SOURCE_FILES``,
+    possibly from another directory) with the oracle's own flags into
+    ``out_path`` and load them.  Used by the pin-strength tests, which build
+    private copies with planted mistakes."""
+    subprocess.check_call(["gcc", *CFLAGS, "-o", out_path, *sources, "-lm", "-lpthread"])
+    return _declare(ctypes.CDLL(out_path))
 
 
-def build_variant(out_dir: str, defines: dict) -> "callable":
-    """Compile the oracle with extra -D defines into ``out_dir`` and return its
-    full-matrix ``twed`` function.  Used only by the pin-strength tests, which
-    plant mistakes (``ORACLE_MUTANT``) and check that the pins catch them."""
-    lib = _variant_lib(out_dir, defines)
+SOURCE_FILES = [os.path.basename(f) for f in _SOURCES]
+SOURCE_DIR = _HERE
+
+
+def twed_of(lib) -> "callable":
+    """The full-matrix ``twed`` of a library from :func:`compile_library`."""
     return lambda a, ta, b, tb, nu, lam, p=2: _call(lib.oracle_twed, a, ta, b, tb, nu, lam, p)
 
 
-def build_lib_variant(out_dir: str, defines: dict):
-    """The whole variant library (every entry point declared), for the
-    pin-strength tests of the LCS and DTW oracles."""
-    return _variant_lib(out_dir, defines)
-
-
-def build_path_variant(out_dir: str, defines: dict) -> "callable":
-    """As :func:`build_variant`, returning the variant's ``twed_path``."""
-    lib = _variant_lib(out_dir, defines)
+def twed_path_of(lib) -> "callable":
+    """As :func:`twed_of`, for ``twed_path``."""
     return lambda a, ta, b, tb, nu, lam, p=2: _path_call(lib, a, ta, b, tb, nu, lam, p)
 
 

@@ -21,19 +21,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 
-/* Planted mistakes for the pin-strength test (tests/test_oracle_dtw.py
- * builds private copies with -DORACLE_MUTANT=k); 0 = the oracle itself. */
-#ifndef ORACLE_MUTANT
-#define ORACLE_MUTANT 0
-#endif
-
 static double dtw_dist(const double* x, const double* y, int dim, int p)
 {
-#if ORACLE_MUTANT == 32
-    if (dim == 1) return (x[0] - y[0]) * (x[0] - y[0]);  /* planted: squared 1-D distance */
-#else
     if (dim == 1) return fabs(x[0] - y[0]);
-#endif
     double s = 0.0;
     if (p == 1) {
         for (int k = 0; k < dim; ++k) s = s + fabs(x[k] - y[k]);
@@ -65,13 +55,7 @@ int oracle_dtw(const double* a, int64_t n, const double* b, int64_t m, int dim, 
         D[i * W] = INFINITY;
         for (int64_t j = 1; j <= m; ++j) {
             const double d = dtw_dist(a + (i - 1) * dim, b + (j - 1) * dim, dim, p);
-#if ORACLE_MUTANT == 30
-            const double best = fmin(D[(i - 1) * W + (j - 1)], D[(i - 1) * W + j]);  /* planted: no left */
-#elif ORACLE_MUTANT == 31
-            const double best = fmin(fmin(D[(i - 1) * W + (j - 1)], D[(i - 1) * W + j]), D[i * W + (j - 1)]) * 0.5;  /* planted: halved */
-#else
             const double best = fmin(fmin(D[(i - 1) * W + (j - 1)], D[(i - 1) * W + j]), D[i * W + (j - 1)]);
-#endif
             D[i * W + j] = d + best;
         }
     }

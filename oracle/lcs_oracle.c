@@ -18,12 +18,6 @@
 #include <stdint.h>
 #include <stdlib.h>
 
-/* Planted mistakes for the pin-strength test (tests/test_oracle_lcs.py
- * builds private copies with -DORACLE_MUTANT=k); 0 = the oracle itself. */
-#ifndef ORACLE_MUTANT
-#define ORACLE_MUTANT 0
-#endif
-
 static int lcs_bad(const int32_t* x, int64_t n, const int32_t* y, int64_t m)
 {
     return !x || !y || n < 0 || m < 0;
@@ -40,11 +34,7 @@ static int64_t* lcs_matrix(const int32_t* x, int64_t n, const int32_t* y, int64_
         L[i * W] = 0;
         for (int64_t j = 1; j <= m; ++j) {
             if (x[i - 1] == y[j - 1]) {
-#if ORACLE_MUTANT == 21
-                L[i * W + j] = L[(i - 1) * W + j] + 1;  /* planted: up instead of diagonal */
-#else
                 L[i * W + j] = L[(i - 1) * W + (j - 1)] + 1;
-#endif
             } else {
                 const int64_t up = L[(i - 1) * W + j], left = L[i * W + (j - 1)];
                 L[i * W + j] = up >= left ? up : left;
@@ -80,11 +70,7 @@ int oracle_lcs_length_rolling(const int32_t* x, int64_t n, const int32_t* y, int
             if (x[i - 1] == y[j - 1]) {
                 cur[j] = prev[j - 1] + 1;
             } else {
-#if ORACLE_MUTANT == 22
-                cur[j] = prev[j - 1] >= cur[j - 1] ? prev[j - 1] : cur[j - 1];  /* planted: up-left for up */
-#else
                 cur[j] = prev[j] >= cur[j - 1] ? prev[j] : cur[j - 1];
-#endif
             }
         }
         int64_t* t = prev;
@@ -119,11 +105,7 @@ int oracle_lcs_pairs(const int32_t* x, int64_t n, const int32_t* y, int64_t m, i
             yj[k] = j - 1;
             --i;
             --j;
-#if ORACLE_MUTANT == 20
-        } else if (L[(i - 1) * W + j] > L[i * W + (j - 1)]) {  /* planted: left on ties */
-#else
         } else if (L[(i - 1) * W + j] >= L[i * W + (j - 1)]) {
-#endif
             --i;
         } else {
             --j;

@@ -45,13 +45,6 @@
 #include <stdlib.h>
 #include <string.h>
 
-/* Planted mistakes, compiled in only by the pin-strength test
- * (tests/test_oracle_mutants.py builds the oracle with -DORACLE_MUTANT=k and
- * checks that the pins reject every such build).  0 = the oracle itself. */
-#ifndef ORACLE_MUTANT
-#define ORACLE_MUTANT 0
-#endif
-
 /* lp distance between two points of `dim` components. */
 static double oracle_dist(const double* x, const double* y, int dim, int p)
 {
@@ -66,11 +59,7 @@ static double oracle_dist(const double* x, const double* y, int dim, int p)
             double t = x[k] - y[k];
             s = s + t * t;
         }
-#if ORACLE_MUTANT == 6
-        return s;
-#else
         return sqrt(s);
-#endif
     }
     for (int k = 0; k < dim; ++k) s = s + pow(fabs(x[k] - y[k]), (double)p);
     return pow(s, 1.0 / (double)p);
@@ -92,13 +81,7 @@ static double tm(const series_t* s, int64_t i) { return i == 0 ? 0.0 : s->t[i - 
 static double cell_cost(const series_t* a, int64_t i, const series_t* b, int64_t j, double nu, int p)
 {
     double d = oracle_dist(pt(a, i), pt(b, j), a->dim, p);
-#if ORACLE_MUTANT == 2
-    double w = nu * fabs(tm(a, i) - tm(b, i <= b->n ? i : b->n));
-#elif ORACLE_MUTANT == 7
-    double w = fabs(tm(a, i) - tm(b, j));
-#else
     double w = nu * fabs(tm(a, i) - tm(b, j));
-#endif
     return d + w;
 }
 
@@ -107,11 +90,7 @@ static double del_cost(const series_t* s, int64_t i, double nu, double lambda, i
 {
     double d = oracle_dist(pt(s, i), pt(s, i - 1), s->dim, p);
     double w = nu * fabs(tm(s, i) - tm(s, i - 1));
-#if ORACLE_MUTANT == 3
-    return d + w;
-#else
     return (d + w) + lambda;
-#endif
 }
 
 static double min3(double x, double y, double z) { return fmin(fmin(x, y), z); }
@@ -135,34 +114,16 @@ static double* twed_matrix(const series_t* A, const series_t* B, double nu, doub
     const int64_t W = m + 1;
     D[0] = 0.0;
     for (int64_t j = 1; j <= m; ++j) D[j] = INFINITY;
-#if ORACLE_MUTANT == 4
-    for (int64_t i = 1; i <= n; ++i) D[i * W] = 0.0;
-#else
     for (int64_t i = 1; i <= n; ++i) D[i * W] = INFINITY;
-#endif
     for (int64_t i = 1; i <= n; ++i) {
-#if ORACLE_MUTANT == 5
-        double dA = del_cost(A, i > 1 ? i - 1 : 1, nu, lambda, p);
-#else
         double dA = del_cost(A, i, nu, lambda, p);
-#endif
         for (int64_t j = 1; j <= m; ++j) {
             double dB = del_cost(B, j, nu, lambda, p);
             double c_ij = cell_cost(A, i, B, j, nu, p);
             double c_prev = cell_cost(A, i - 1, B, j - 1, nu, p);
             double delete_a = D[(i - 1) * W + j] + dA;
             double delete_b = D[i * W + (j - 1)] + dB;
-#if ORACLE_MUTANT == 1
-            double match = D[(i - 1) * W + (j - 1)] + c_ij;
-            (void)c_prev;
-#elif ORACLE_MUTANT == 8
-            double match = (D[(i - 1) * W + (j - 1)] + c_ij) - c_prev;
-#elif ORACLE_MUTANT == 9
-            double match = (D[(i - 1) * W + (j - 1)] + c_ij) + cell_cost(A, i - 1, B, j, nu, p);
-            (void)c_prev;
-#else
             double match = (D[(i - 1) * W + (j - 1)] + c_ij) + c_prev;
-#endif
             D[i * W + j] = min3(delete_a, delete_b, match);
         }
     }
@@ -219,19 +180,6 @@ int oracle_twed_path(const double* a, const double* ta, int64_t n, const double*
                     cell_cost(&A, i - 1, &B, j - 1, nu, p);
         const double delete_a = i > 1 ? D[(i - 1) * W + j] + del_cost(&A, i, nu, lambda, p) : INFINITY;
         const double delete_b = j > 1 ? D[i * W + (j - 1)] + del_cost(&B, j, nu, lambda, p) : INFINITY;
-#if ORACLE_MUTANT == 10
-        /* planted: delete in b tried before delete in a */
-        if (match == here) { moves[k++] = 0; --i; --j; }
-        else if (delete_b == here) { moves[k++] = 2; --j; }
-        else if (delete_a == here) { moves[k++] = 1; --i; }
-        else { rc = 3; break; }
-#elif ORACLE_MUTANT == 11
-        /* planted: delete in a tried before the match */
-        if (delete_a == here) { moves[k++] = 1; --i; }
-        else if (match == here) { moves[k++] = 0; --i; --j; }
-        else if (delete_b == here) { moves[k++] = 2; --j; }
-        else { rc = 3; break; }
-#else
         if (match == here) {
             moves[k++] = 0;
             --i;
@@ -246,12 +194,8 @@ int oracle_twed_path(const double* a, const double* ta, int64_t n, const double*
             rc = 3;
             break;
         }
-#endif
     }
     /* the walk collected the moves backwards */
-#if ORACLE_MUTANT == 12
-    if (0)  /* planted: the moves are left in walk order */
-#endif
     for (int64_t x = 0, y = k - 1; x < y; ++x, --y) {
         const int8_t t = moves[x];
         moves[x] = moves[y];

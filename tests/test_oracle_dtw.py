@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 import oracle
+from tests import mutants
 from bruteforce import all_paths, lp
 
 
@@ -82,10 +83,10 @@ def _dtw_pins(lib):
 
 
 def test_real_dtw_oracle_passes_every_pin(tmp_path):
-    assert _dtw_pins(oracle.build_lib_variant(str(tmp_path), {"ORACLE_MUTANT": 0})) is None
+    assert _dtw_pins(mutants.build(str(tmp_path), 0)) is None
 
 
 @pytest.mark.parametrize("k", sorted(DTW_MUTANTS), ids=lambda k: DTW_MUTANTS[k])
 def test_planted_dtw_mistake_is_caught(k, tmp_path):
-    lib = oracle.build_lib_variant(str(tmp_path), {"ORACLE_MUTANT": k})
+    lib = mutants.build(str(tmp_path), k)
     assert _dtw_pins(lib) is not None, f"no pin rejects: {DTW_MUTANTS[k]}"

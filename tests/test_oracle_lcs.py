@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 import oracle
+from tests import mutants
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 
@@ -114,10 +115,10 @@ def _lcs_pins(lib):
 
 
 def test_real_lcs_oracle_passes_every_pin(tmp_path):
-    assert _lcs_pins(oracle.build_lib_variant(str(tmp_path), {"ORACLE_MUTANT": 0})) is None
+    assert _lcs_pins(mutants.build(str(tmp_path), 0)) is None
 
 
 @pytest.mark.parametrize("k", sorted(LCS_MUTANTS), ids=lambda k: LCS_MUTANTS[k])
 def test_planted_lcs_mistake_is_caught(k, tmp_path):
-    lib = oracle.build_lib_variant(str(tmp_path), {"ORACLE_MUTANT": k})
+    lib = mutants.build(str(tmp_path), k)
     assert _lcs_pins(lib) is not None, f"no pin rejects: {LCS_MUTANTS[k]}"

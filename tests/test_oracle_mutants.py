@@ -1,9 +1,9 @@
 """Pin strength: the oracle's pins must reject plausible mistakes.
 
-Each planted mistake is compiled into a private copy of the oracle
-(``-DORACLE_MUTANT=k``; the planted lines sit under that macro in
-``oracle/twed_oracle.c``) and run through the same independent pins that
-``test_oracle.py`` applies to the real oracle.  A mistake that no pin rejects
+Each planted mistake is compiled into a private copy of the oracle (a
+textual patch of ``oracle/twed_oracle.c`` from ``tests/mutants.py``) and run
+through the same independent pins that ``test_oracle.py`` applies to the
+real oracle.  A mistake that no pin rejects
 would mean the pins do not pin that part of the definition.
 """
 import json
@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 
 import oracle
+from tests import mutants
 from tests.bruteforce import lp, twed_bruteforce
 
 MUTANTS = {
@@ -64,5 +65,5 @@ def test_real_oracle_passes_every_pin():
 
 @pytest.mark.parametrize("k", sorted(MUTANTS), ids=lambda k: MUTANTS[k])
 def test_planted_mistake_is_caught(k, tmp_path):
-    mutant = oracle.build_variant(str(tmp_path), {"ORACLE_MUTANT": k})
+    mutant = oracle.twed_of(mutants.build(str(tmp_path), k))
     assert _pins(mutant) is not None, f"no pin rejects: {MUTANTS[k]}"

@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 
 import oracle
+from tests import mutants
 from bruteforce import all_paths, step_costs, twed_bruteforce
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -178,5 +179,5 @@ def test_real_path_oracle_passes_every_path_pin():
 
 @pytest.mark.parametrize("k", sorted(PATH_MUTANTS), ids=lambda k: PATH_MUTANTS[k])
 def test_planted_path_mistake_is_caught(k, tmp_path):
-    mutant = oracle.build_path_variant(str(tmp_path), {"ORACLE_MUTANT": k})
+    mutant = oracle.twed_path_of(mutants.build(str(tmp_path), k))
     assert _path_pins(mutant) is not None, f"no pin rejects: {PATH_MUTANTS[k]}"
