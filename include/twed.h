@@ -60,7 +60,10 @@ typedef struct twed_plan_s* twed_plan_t;
 /* Accumulation of the running cost D for single-precision entry points. */
 typedef enum {
     TWED_ACCUM_AUTO = 0,  /* FP32, or compensated FP32 once n + m > 100000 */
-    TWED_ACCUM_F32 = 1,   /* plain FP32 sums */
+    TWED_ACCUM_F32 = 1,   /* plain FP32 sums: within 1e-5 relative of FP64
+                             only while n + m <= 100000; longer pairs drift
+                             (measured 1.4e-5 at n = m = 1e5, 2.3e-5 at
+                             1e6), outside the single-precision contract */
     TWED_ACCUM_KAHAN = 2  /* compensated (TwoSum) FP32 running cost */
 } twed_accum_t;
 
@@ -114,8 +117,10 @@ void twed_destroy(twed_handle_t handle);
 const char* twed_last_error(twed_handle_t handle);
 /* Library version string. */
 const char* twed_version(void);
-/* Waits for `stream`, then reports (and clears) any TWED_ERR_TIMEOUT that a
- * device entry point enqueued on this handle raised.  TWED_OK otherwise. */
+/* Waits for `stream`, then reports (and clears) the first error that a
+ * device entry point enqueued on this handle raised on the GPU:
+ * TWED_ERR_TIMEOUT (a bounded wait expired) or TWED_ERR_INVALID_ARG (a batch
+ * pair index outside its set).  TWED_OK otherwise. */
 twed_status_t twed_sync_status(twed_handle_t handle, void* stream);
 
 /* ---- one pair ------------------------------------------------------------
@@ -157,8 +162,10 @@ twed_status_t twed_dev_f32_ex(twed_handle_t handle, const float* d_a, const floa
  * an arbitrary list of pairs: d_pairs[2k], d_pairs[2k+1] (device int64) index
  * series of A and B; d_out[k] (device) receives TWED(A[d_pairs[2k]],
  * B[d_pairs[2k+1]]).  One persistent launch, one warp per pair, pairs taken
- * in list order.  Pair indices are not range-checked on the device:
- * out-of-range indices are undefined.  B may equal A. */
+ * in list order.  The host does not read d_pairs; the kernel checks every
+ * index against its set before reading any point of it: a pair with an index
+ * outside [0, A->n) x [0, B->n) gets NaN in d_out[k], and the launch reports
+ * TWED_ERR_INVALID_ARG through twed_sync_status.  B may equal A. */
 twed_status_t twed_batch_f64(twed_handle_t handle, const twed_set_f64_t* A,
                              const twed_set_f64_t* B, const int64_t* d_pairs, int64_t npairs,
                              int dim, double nu, double lambda, int p, double* d_out, void* stream);
@@ -199,15 +206,26 @@ twed_status_t twed_batch_f32_ex(twed_handle_t handle, const twed_set_f32_t* A,
  * working memory is one static device array of TWED_NOALLOC_SCRATCH_BYTES
  * inside the library, which every GPU that loads the library keeps until
  * the process exits.  The caller still passes (and owns) all inputs and
- * outputs.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls share the one array and it keeps
- * the last call's contents (the call clears what must start at zero): two
- * calls whose work overlaps on the GPU -- on different streams, or from
- * different threads -- race and give undefined results.  Requests whose
- * per-point records plus one boundary row need more than the array return
- * TWED_ERR_UNSUPPORTED before enqueuing anything.  No error text is kept
- * (there is no handle); the status code is the whole report. */
+ * outputs.
+ *
+ * Set-up: the first call on each device, with that device current, looks up
+ * the array's device address (cudaGetSymbolAddress), reads the SM count, and
+ * loads and sizes every kernel this call can launch (attribute and occupancy
+ * queries), so that later calls on that device do no lazy kernel loading.
+ * Make that first call before any stream capture.  The set-up belongs to the
+ * device's primary context: after cudaDeviceReset of that device this entry
+ * point must not be called again in the process.
+ *
+ * All calls share the one array and it keeps the last call's contents (the
+ * call clears what must start at zero): two calls whose work overlaps on the
+ * GPU -- on different streams, or from different threads -- race and give
+ * undefined results.  Size limit: the per-point records (A's, plus B's
+ * unless B is A; 16 to 80 bytes per point, by dim) plus four boundary rows
+ * of 8 x (longest series + 2) bytes must fit in the array after 256 bytes of
+ * control words; larger requests return TWED_ERR_UNSUPPORTED before
+ * enqueuing anything.  No error text is kept (there is no handle); the
+ * status code is the whole report, and a pair index outside its set leaves
+ * NaN in that pair's output. */
 #define TWED_NOALLOC_SCRATCH_BYTES (32u * 1024u * 1024u)
 twed_status_t twed_batch_f32_noalloc(const twed_set_f32_t* A, const twed_set_f32_t* B,
                                      const int64_t* d_pairs, int64_t npairs, int dim, float nu,

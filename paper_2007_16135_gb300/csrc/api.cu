@@ -68,6 +68,15 @@ twed_status_t cuda_fail(twed_handle_t h, cudaError_t e, const char* what) {
     return fail(h, TWED_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+// Text of an error word a kernel left in the launch's control words.
+const char* device_error_text(unsigned code) {
+    switch (code) {
+        case TWED_ERR_INVALID_ARG: return "a pair index lies outside its set (the pair's result is NaN)";
+        case TWED_ERR_TIMEOUT: return "a bounded inter-warp wait expired";
+        default: return "a kernel reported an error";
+    }
+}
+
 #define TWED_CUDA(h, call)                                          \
     do {                                                            \
         cudaError_t e_ = (call);                                    \
@@ -393,7 +402,7 @@ twed_status_t run_pair_host(twed_handle_t h, const T* a, const T* ta, int64_t la
     if (err != 0) {
         unsigned zero = 0;
         cudaMemcpy(h->ctl + 1, &zero, sizeof zero, cudaMemcpyHostToDevice);
-        return fail(h, (twed_status_t)err, "a bounded inter-warp wait expired");
+        return fail(h, (twed_status_t)err, "%s", device_error_text(err));
     }
     return TWED_OK;
 }
@@ -474,7 +483,7 @@ extern "C" twed_status_t twed_sync_status(twed_handle_t h, void* stream) {
     TWED_CUDA(h, cudaMemcpy(&sticky, h->ctl + 1, sizeof sticky, cudaMemcpyDeviceToHost));
     if (sticky) {
         TWED_CUDA(h, cudaMemcpy(h->ctl + 1, &zero, sizeof zero, cudaMemcpyHostToDevice));
-        return fail(h, (twed_status_t)sticky, "a bounded inter-warp wait expired");
+        return fail(h, (twed_status_t)sticky, "%s", device_error_text(sticky));
     }
     return TWED_OK;
 }
@@ -1376,7 +1385,7 @@ extern "C" twed_status_t twed_allpairs_host_f32(twed_handle_t h, const float* a_
         if (e != cudaSuccess) { s = cuda_fail(h, e, "device to host copy"); break; }
         unsigned err = 0;
         cudaMemcpy(&err, pl->ctl, sizeof err, cudaMemcpyDeviceToHost);
-        if (err) s = fail(h, (twed_status_t)err, "a bounded wait expired");
+        if (err) s = fail(h, (twed_status_t)err, "%s", device_error_text(err));
     } while (0);
     if (pl) twed_plan_destroy(pl);
     cudaStreamSynchronize(st);

@@ -234,6 +234,18 @@ __global__ void __launch_bounds__(256) band_kernel(CoopArgs<float> a) {
 }
 
 // ------------------------------------------------------------- many pairs
+// Explicit pair lists come from the caller: an index outside [0, na) x
+// [0, nb) is rejected on the device before any record is read.
+__device__ __forceinline__ bool pair_in_range(int64_t x, int64_t y, int64_t na, int64_t nb) {
+    return (uint64_t)x < (uint64_t)na && (uint64_t)y < (uint64_t)nb;
+}
+template <typename T>
+__device__ __forceinline__ void flag_bad_pair(T* out, const SyncCtl& sc) {
+    *out = (T)__int_as_float(0x7fc00000);  // quiet NaN
+    atomicCAS(sc.err, 0u, 1u /* TWED_ERR_INVALID_ARG */);
+    atomicCAS(sc.sticky, 0u, 1u);
+}
+
 __device__ __forceinline__ void triangle_pos(int64_t w, int64_t n, int64_t& p, int64_t& q) {
     // row-major enumeration of {(p, q): 0 <= p < q < n}; row p starts at
     // p*(2n - p - 1)/2
@@ -270,6 +282,12 @@ __global__ void __launch_bounds__(128, TWED_PAIRS_MIN_BLOCKS) pairs_kernel(Pairs
             x = a.pairs[2 * wi];
             y = a.pairs[2 * wi + 1];
             o1 = a.out + wi;
+            // a caller's index outside its set is never dereferenced: the
+            // pair's result is NaN and the launch reports TWED_ERR_INVALID_ARG
+            if (!pair_in_range(x, y, a.na, a.nb)) {
+                if (lane == 0) flag_bad_pair(o1, a.sc);
+                continue;
+            }
         } else if (a.mode == kSymmetricSorted) {
             int64_t pp, qq;
             triangle_pos((int64_t)w, a.na, pp, qq);

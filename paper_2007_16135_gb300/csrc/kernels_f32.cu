@@ -42,6 +42,12 @@ int band_blocks_per_sm(int dim, int p, int R, bool kahan, int warps) {
     return kahan ? band_blocks_per_sm_kh<true>(dim, p, R, warps)
                  : band_blocks_per_sm_kh<false>(dim, p, R, warps);
 }
+cudaError_t records_preload_f32(int dim, int p) {
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaSuccess;
+    TWED_DISPATCH(dim, p, (e = cudaFuncGetAttributes(&fa, records_kernel<float, DIM_, P_>)));
+    return e;
+}
 bool compiled_layout(int dim, int p) {
     int d = 0;
     TWED_DISPATCH(dim, p, (d = DIM_));

@@ -91,6 +91,9 @@ int rec_len(int dim, int p);
 
 cudaError_t launch_records(const RecordsArgs<float>& a, cudaStream_t st);
 cudaError_t launch_records(const RecordsArgs<double>& a, cudaStream_t st);
+// Loads the FP32 records kernel that (dim, p) dispatches to (a function
+// attribute query), so that its first launch does no lazy module loading.
+cudaError_t records_preload_f32(int dim, int p);
 
 // R (rows of the DP per lane) in {1, 2, 4, 8}.  kahan: compensated FP32
 // running cost (float, dims with a compiled point layout only; ring entries

@@ -26,22 +26,64 @@ constexpr int kMaxDevices = 64;
 // cudaGetSymbolAddress returns for the current device.
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
+// Every (dim, p) the many-pairs dispatch can pick: dim 1 (any p); dims 2,
+// 3, 4 and 8 (5-7 use the dim-8 layout) with p = 1 or 2; everything else on
+// the run-time-dimension kernels.
+constexpr int kVariants = 10;
+int variant_of(int dim, int p) {
+    if (dim == 1) return 0;
+    const int d = dim <= 4 ? dim : (dim <= 8 ? 8 : 0);
+    if (d == 0 || (p != 1 && p != 2)) return kVariants - 1;
+    const int di = d == 2 ? 0 : d == 3 ? 1 : d == 4 ? 2 : 3;
+    return 1 + 2 * di + (p - 1);
+}
+void variant_rep(int v, int* dim, int* p) {
+    static const int dims[4] = {2, 3, 4, 8};
+    if (v == 0) { *dim = 1; *p = 2; }
+    else if (v == kVariants - 1) { *dim = 9; *p = 2; }
+    else { *dim = dims[(v - 1) / 2]; *p = (v - 1) % 2 + 1; }
+}
+
+// What the first call on a device sets up, with that device current.
+struct DeviceSetup {
+    bool ready = false;
+    unsigned char* scratch = nullptr;  // device address of g_scratch
+    int sms = 0;
+    int per_sm[kVariants] = {};        // resident many-pairs blocks per SM
+};
 std::mutex g_mu;
-void* g_scratch_addr[kMaxDevices] = {};
+DeviceSetup g_dev[kMaxDevices];
 
 size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 
-// Device address of g_scratch on device `dev` (looked up once per device,
-// with that device current).
-cudaError_t scratch_address(int dev, unsigned char** out) {
+// Once per device: the device address of g_scratch (cudaGetSymbolAddress),
+// the SM count, and every records / many-pairs kernel variant this entry
+// point can launch loaded and sized (function attribute and occupancy
+// queries), so that later calls do no lazy module loading.
+cudaError_t device_setup(int dev, const DeviceSetup** out) {
     std::lock_guard<std::mutex> lock(g_mu);
-    if (g_scratch_addr[dev] == nullptr) {
+    DeviceSetup& d = g_dev[dev];
+    if (!d.ready) {
         void* p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_addr[dev] = p;
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev);
+        for (int v = 0; v < kVariants && e == cudaSuccess; ++v) {
+            int vd = 0, vp = 0;
+            variant_rep(v, &vd, &vp);
+            e = twed::records_preload_f32(vd, vp);
+            if (e == cudaSuccess) {
+                d.per_sm[v] = twed::pairs_blocks_per_sm<float>(vd, vp, kThreads);
+                if (d.per_sm[v] < 1) e = cudaErrorInvalidConfiguration;
+            }
+        }
+        if (e != cudaSuccess) {
+            (void)cudaGetLastError();
+            return e;  // not marked ready: the next call tries again
+        }
+        d.scratch = static_cast<unsigned char*>(p);
+        d.ready = true;
     }
-    *out = static_cast<unsigned char*>(g_scratch_addr[dev]);
+    *out = &d;
     return cudaSuccess;
 }
 
@@ -86,15 +128,14 @@ extern "C" twed_status_t twed_batch_f32_noalloc(const twed_set_f32_t* A, const t
     const int64_t fit_warps = (int64_t)((kScratchBytes - o_rows) / row_bytes);
     if (fit_warps < kWarpsPerBlock) return TWED_ERR_UNSUPPORTED;
 
-    int dev = 0, sms = 0;
+    int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return TWED_ERR_CUDA;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-        return TWED_ERR_CUDA;
-    unsigned char* base = nullptr;
-    if (scratch_address(dev, &base) != cudaSuccess) return TWED_ERR_CUDA;
+    const DeviceSetup* ds = nullptr;
+    if (device_setup(dev, &ds) != cudaSuccess) return TWED_ERR_CUDA;
+    unsigned char* base = ds->scratch;
 
-    const int per_sm = std::max(1, twed::pairs_blocks_per_sm<float>(dim, p, kThreads));
-    int64_t blocks = std::min<int64_t>((int64_t)per_sm * sms, (npairs + kWarpsPerBlock - 1) / kWarpsPerBlock);
+    const int per_sm = ds->per_sm[variant_of(dim, p)];
+    int64_t blocks = std::min<int64_t>((int64_t)per_sm * ds->sms, (npairs + kWarpsPerBlock - 1) / kWarpsPerBlock);
     blocks = std::min<int64_t>(blocks, fit_warps / kWarpsPerBlock);
     blocks = std::max<int64_t>(blocks, 1);
 

@@ -184,6 +184,10 @@ __global__ void __launch_bounds__(x64::THREADS) xterm_pairs_kernel(PairsArgs<flo
             x = a.pairs[2 * w];
             y = a.pairs[2 * w + 1];
             o1 = a.out + w;
+            if (!pair_in_range(x, y, a.na, a.nb)) {  // block-uniform
+                if (threadIdx.x == 0) flag_bad_pair(o1, a.sc);
+                continue;
+            }
         } else if (a.mode == kSymmetricSorted) {
             int64_t pp, qq;
             triangle_pos((int64_t)w, a.na, pp, qq);
