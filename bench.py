@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["w3", "w4", "w2", "w1", "w5", "u1", "u2"], default="w3")
     ap.add_argument("--no-knn", action="store_true", help="w3: skip the appended w5 result")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="w3: skip the appended w1, w2 and w4 results")
     ap.add_argument("--knn-epochs", type=int, default=40)
     ap.add_argument("--knn-pairs", type=int, default=1_000_000)
     ap.add_argument("--knn-db", type=int, default=100_000)
@@ -278,7 +280,10 @@ def bench_plan(args, rank, world, dev, workload):
     peaks = measured_peaks()
     sm_max = float(peaks.get("sm_max_mhz", FALLBACK_SM_MAX_MHZ))
     peak_ops = props.multi_processor_count * FP32_LANES_PER_SM * sm_max * 1e6
-    opc = 7 if xterm else ops_per_cell(dim, p)
+    # tensor-core path: per cell after the contraction, 11 operations (cost:
+    # norm sum, -2X FMA, clamp, square root, time difference, nu FMA; update:
+    # four additions and the three-way minimum)
+    opc = 11 if xterm else ops_per_cell(dim, p)
     kern_s = res["kernel_ms"] / 1e3
     if workload in ("u1", "u2"):
         # pairs above the cut-over run after the timed persistent launch:
@@ -294,7 +299,7 @@ def bench_plan(args, rank, world, dev, workload):
             tj = json.load(f)
         if tj.get("src_hash") == kernel_src_hash():
             traffic = tj.get("dram_bytes_per_launch")
-    kname = "xterm_pairs_kernel (tcgen05 tf32)" if xterm else f"pairs_kernel<float,{dim if dim in (1,2,3,4,8) else 0},2,8>"
+    kname = "xterm_sweep_kernel (tcgen05 tf32)" if xterm else f"pairs_kernel<float,{dim if dim in (1,2,3,4,8) else 0},2,8>"
     lanes = FP64_LANES_PER_SM if dtype == "f64" else FP32_LANES_PER_SM
     if workload in ("u1", "u2"):
         kname = f"whole step ({'double' if dtype == 'f64' else 'float'}; pairs kernel + one-pair schedule)"
@@ -509,11 +514,72 @@ def bench_pair(args, rank, world, dev, workload):
     if rank == 0 and not args.no_cpu:
         res["cpu_baseline"], res["error_vs_oracle"] = pair_cpu_leg(
             a, ta, b, tb, nu, lam, p, dtype, res["result"], args.cpu_seconds)
+    if dtype == "f32" and getattr(args, "check_f64", False):
+        # the FP32 result against the FP64 GPU path on the same FP32-rounded
+        # inputs (too large for the oracle): one untimed-in-`value` FP64 run
+        up = lambda x: torch.as_tensor(np.ascontiguousarray(x)).to(torch.float32).to(torch.float64).to(dev)
+        A64, TA64, B64, TB64 = up(a), up(ta), up(b), up(tb)
+        o64 = torch.empty(1, dtype=torch.float64, device=dev)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        twed.twed_dev(A64, TA64, B64, TB64, nu, lam, p, out=o64, stream=stream)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        twed.default_handle().sync_status(stream)
+        f64 = float(o64.item())
+        ms64 = ev0.elapsed_time(ev1)
+        res["error_vs_f64_gpu"] = {"rel": abs(res["result"] - f64) / abs(f64), "f64_gpu": f64,
+                                   "bound": 1e-5, "f64_ms": ms64,
+                                   "f64_gcups": cells / (ms64 / 1e3) / 1e9,
+                                   "how": "twed_dev_f64 on the same FP32-rounded inputs upcast"}
     res["config"] = {"workload": f"{workload} one pair n=m={n}, dim {dim}, {dtype}"
                                  + (", compensated (TwoSum) FP32 running cost" if kahan else ""),
                      "n": n, "accumulation": "kahan" if kahan else dtype,
                      "l2": "one pair per step; records stream through L2"}
     return res
+
+
+def _sub(args, **kw):
+    d = dict(vars(args))
+    d.update(kw)
+    return argparse.Namespace(**d)
+
+
+EXTRA_KEYS = ("value", "unit", "ms_per_step", "steps", "warmup", "config", "dtype", "roofline",
+              "tensor", "cpu_baseline", "error_vs_oracle", "error_vs_f64_gpu", "clocks", "result",
+              "cells_per_step", "kernel_ms", "plan")
+
+
+def _extra_line(res, steps, warmup):
+    out = {k: res[k] for k in EXTRA_KEYS if k in res}
+    out.setdefault("unit", UNIT)
+    out["steps"], out["warmup"] = steps, warmup
+    return out
+
+
+def bench_extra(args, rank, world, dev):
+    """The other configurations of the metric, appended to the default run
+    with fixed, small step counts: the 1000-point FP64 pair (w1), the long
+    3-D pair (w2: 1e5 FP64 against the stored oracle value; 1e6 compensated
+    FP32 against the FP64 GPU path on the same inputs) and the dim-64 block
+    on the tensor cores (w4)."""
+    out = {}
+    a1 = _sub(args, workload="w1", dtype="f64", n=None, steps=20, warmup=5, accum="auto",
+              rows_per_lane=0, cpu_seconds=min(args.cpu_seconds, 6.0))
+    out["w1"] = _extra_line(bench_pair(a1, rank, world, dev, "w1"), 20, 5)
+    w2 = {}
+    a2 = _sub(args, workload="w2", dtype="f64", n=100_000, steps=3, warmup=2, accum="auto",
+              rows_per_lane=0, cpu_seconds=min(args.cpu_seconds, 6.0))
+    w2["f64_1e5"] = _extra_line(bench_pair(a2, rank, world, dev, "w2"), 3, 2)
+    a2 = _sub(a2, dtype="f32")
+    w2["f32_1e5"] = _extra_line(bench_pair(a2, rank, world, dev, "w2"), 3, 2)
+    a2 = _sub(a2, dtype="f32", n=1_000_000, check_f64=True)
+    w2["f32_1e6"] = _extra_line(bench_pair(a2, rank, world, dev, "w2"), 3, 2)
+    out["w2"] = w2
+    a4 = _sub(args, workload="w4", xterm="tf32", steps=3, warmup=3, no_e2e=True,
+              cpu_seconds=min(args.cpu_seconds, 6.0))
+    out["w4"] = _extra_line(bench_plan(a4, rank, world, dev, "w4"), 3, 3)
+    return out
 
 
 def bench_knn(args, rank, world, dev, steps, warmup):
@@ -528,8 +594,12 @@ def bench_knn(args, rank, world, dev, steps, warmup):
     nu, lam, p, k = 1.0, 1.0, 2, 10
     db = W.set_w5(args.knn_db, stream=1 if rank == 0 else 20 + rank).astype(np.float32)
     qs = W.set_w5(args.knn_queries, stream=0 if rank == 0 else 10 + rank).astype(np.float32)
+    # a separate query stream on which the candidate count is chosen; the
+    # reported recall is measured on the other queries (no selection on them)
+    qt = W.set_w5(args.knn_queries, stream=5 if rank == 0 else 30 + rank).astype(np.float32)
     D = twed.DeviceSet.from_numpy(db.vals, db.ts, db.offs, torch.float32, device=dev)
     Q = twed.DeviceSet.from_numpy(qs.vals, qs.ts, qs.offs, torch.float32, device=dev)
+    QT = twed.DeviceSet.from_numpy(qt.vals, qt.ts, qt.offs, torch.float32, device=dev)
     cfg = twed.knn_config(train_pairs=args.knn_pairs, epochs=args.knn_epochs)
     index = twed.KnnIndex(D, nu, lam, p, config=cfg)
     train = index.train()
@@ -544,31 +614,36 @@ def bench_knn(args, rank, world, dev, steps, warmup):
     exact_s = ev0.elapsed_time(ev1) / 1e3
     exact_cells = int(qs.lengths.sum()) * int(db.lengths.sum())
     kth = ex_dist.cpu().numpy()[:, k - 1]
+    _, ext_dist = index.exact(QT, k=k, stream=stream)
+    kth_t = ext_dist.cpu().numpy()[:, k - 1]
 
-    def recall(dist):
+    def recall(dist, kk=kth):
         d = dist.cpu().numpy()
-        return float(np.minimum((d <= kth[:, None]).sum(axis=1), k).mean() / k)
+        return float(np.minimum((d <= kk[:, None]).sum(axis=1), k).mean() / k)
 
+    def recall_t(C):
+        _, dist = index.search(QT, k=k, n_candidates=C, stream=stream)
+        return recall(dist, kth_t)
+
+    # the smallest candidate count (to within 100) whose recall@10 on the
+    # tuning queries reaches 0.99
     sweep, c_op = {}, None
     for C in (200, 400, 800, 1600, 3200, 4096):
         if C > db.n:
             break
-        _, dist = index.search(Q, k=k, n_candidates=C, stream=stream)
-        sweep[C] = recall(dist)
+        sweep[C] = recall_t(C)
         if sweep[C] >= 0.99:
             c_op = C
             break
     if c_op is None:
         c_op = max(sweep)
     else:
-        # bisect between the last count below 0.99 and c_op, to within 100
         lo = max([c for c in sweep if sweep[c] < 0.99], default=None)
         while lo is not None and c_op - lo > 100:
             mid = ((lo + c_op) // 2 + 99) // 100 * 100
             if mid >= c_op:
                 break
-            _, dist = index.search(Q, k=k, n_candidates=mid, stream=stream)
-            sweep[mid] = recall(dist)
+            sweep[mid] = recall_t(mid)
             if sweep[mid] >= 0.99:
                 c_op = mid
             else:
@@ -598,7 +673,9 @@ def bench_knn(args, rank, world, dev, steps, warmup):
     res = {"value": value, "unit": "queries/s", "ms_per_step": ms_step, "clocks": clk.summary(),
            "dtype": "f32",
            "knn": {"recall_at_10": rec_op, "n_candidates": c_op, "k": k,
-                   "recall_sweep": {str(c): r for c, r in sweep.items()},
+                   "n_candidates_chosen_on": f"{qt.n} separate tuning queries (seed stream 5); "
+                                             "recall_at_10 is measured on the reported queries",
+                   "recall_sweep_tuning_queries": {str(c): r for c, r in sweep.items()},
                    "exact_queries_per_s": qs.n / exact_s, "exact_s": exact_s,
                    "exact_gcups": exact_cells / exact_s / 1e9,
                    "speedup_vs_exact": value / world / (qs.n / exact_s),
@@ -697,11 +774,16 @@ def bench_reference(args, rank, world):
     L = S.lengths.astype(np.int64)
     cores = os.cpu_count() or 1
     pairs = W.sample_upper_pairs(S.n, 200000, 3)
-    # size one step to about args.cpu_seconds / 2 of CPU time from a calibration slice
+    # One step is a bounded sample sized from the oracle's measured cells/s:
+    # about min(cpu_seconds / 2, 150 s / steps) of CPU time, so that the whole
+    # --steps K --warmup W run ends within a few minutes.
+    cal = pairs[:4 * cores]
     t0 = time.perf_counter()
-    oracle.twed_pairs(S64.as_tuple(), S64.as_tuple(), pairs[:cores], nu, lam, p, nthreads=cores)
-    per = (time.perf_counter() - t0) / cores
-    k = int(max(cores, min(len(pairs), (args.cpu_seconds / 2) / max(per, 1e-6) * cores)))
+    oracle.twed_pairs(S64.as_tuple(), S64.as_tuple(), cal, nu, lam, p, nthreads=cores)
+    rate = float((L[cal[:, 0]] * L[cal[:, 1]]).sum()) / max(time.perf_counter() - t0, 1e-6)
+    budget = min(args.cpu_seconds / 2, 150.0 / max(args.steps, 1))
+    csum = np.cumsum(L[pairs[:, 0]] * L[pairs[:, 1]])
+    k = int(max(cores, min(len(pairs), np.searchsorted(csum, budget * rate) + 1)))
     step_pairs = pairs[:k]
     cells = int((L[step_pairs[:, 0]] * L[step_pairs[:, 1]]).sum())
     for _ in range(args.warmup):
@@ -775,6 +857,8 @@ def main():
     twed.load()
     if args.workload in ("w3", "w4", "u1", "u2"):
         res = bench_plan(args, rank, world, dev, args.workload)
+        if args.workload == "w3" and not args.no_extra:
+            res.update(bench_extra(args, rank, world, dev))
         if args.workload == "w3" and not args.no_knn:
             kn = bench_knn(args, rank, world, dev, steps=10, warmup=3)
             res["knn"] = {"metric": "k-NN queries/s at recall@10>=0.99 vs exact batched",
@@ -795,7 +879,8 @@ def main():
                 "dtype": res.get("dtype", "f32"), "data": "synthetic (seeded generators)",
                 "config": res["config"]}
         for k in ("roofline", "tensor", "cpu_baseline", "e2e", "gpu_launches", "clocks",
-                  "error_vs_oracle", "kernel_ms", "plan", "cells_per_step", "result", "knn"):
+                  "error_vs_oracle", "error_vs_f64_gpu", "kernel_ms", "plan", "cells_per_step", "result",
+                  "knn", "w1", "w2", "w4"):
             if k in res:
                 line[k] = res[k]
         print(json.dumps(line), flush=True)

@@ -256,6 +256,12 @@ twed_status_t twed_allpairs_plan_create_f32(twed_handle_t handle, const twed_set
                                             twed_plan_t* plan);
 /* d_out: device float[NA*NB] (f32 plans) or double[NA*NB] (f64 plans). */
 twed_status_t twed_plan_execute(twed_plan_t plan, void* d_out, void* stream);
+/* Waits for `stream`, then reports (and clears) the first error the plan's
+ * kernels raised on the GPU since the last call: TWED_ERR_TIMEOUT (a bounded
+ * wait expired; that execute's output is invalid) or TWED_ERR_UNSUPPORTED
+ * (the tensor-core kernel found its shared memory misaligned and computed
+ * nothing).  TWED_OK otherwise. */
+twed_status_t twed_plan_status(twed_plan_t plan, void* stream);
 /* Interior cells (sum of la*lb over computed pairs) one execute evaluates. */
 int64_t twed_plan_cells(twed_plan_t plan);
 /* Number of pairs one execute evaluates. */

@@ -73,6 +73,7 @@ const char* device_error_text(unsigned code) {
     switch (code) {
         case TWED_ERR_INVALID_ARG: return "a pair index lies outside its set (the pair's result is NaN)";
         case TWED_ERR_TIMEOUT: return "a bounded inter-warp wait expired";
+        case TWED_ERR_UNSUPPORTED: return "the kernel's shared memory window is not 1024-byte aligned";
         default: return "a kernel reported an error";
     }
 }
@@ -583,6 +584,8 @@ struct twed_plan_s {
     unsigned* ctl = nullptr;  // plan's own [live err, sticky err]
     unsigned long long* counter = nullptr;
     bool xterm = false;  // tensor-core cross-term kernel (dim 64, FP32)
+    twed::XtermArgs xa{};                 // its argument block (out filled in at launch)
+    alignas(64) unsigned char tmap[128];  // its TMA descriptor of the column set's values
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around the pairs launch
     std::string desc;
     // pairs above the cut-over run one at a time on the one-pair schedule;
@@ -637,7 +640,11 @@ cudaError_t launch_plan_records(twed_plan_t pl, const RecordsArgs<T>& r, cudaStr
 template <typename T>
 cudaError_t launch_plan_pairs(twed_plan_t pl, const PairsArgs<T>& pa, cudaStream_t st) {
     if constexpr (sizeof(T) == 4) {
-        if (pl->xterm) return twed::launch_xterm_pairs(pa, pl->blocks, st);
+        if (pl->xterm) {
+            twed::XtermArgs xa = pl->xa;
+            xa.out = pa.out;
+            return twed::launch_xterm(pl->tmap, xa, pl->blocks, st);
+        }
     }
     return twed::launch_pairs(pa, pl->blocks, pl->threads, st);
 }
@@ -728,6 +735,10 @@ twed_status_t autotune_plan(twed_handle_t h, twed_plan_t pl, const std::vector<i
                             const std::vector<int32_t>& perm_b, const int64_t* offs_a,
                             const int64_t* offs_b, int max_per_sm, std::string& report) {
     PairsArgs<T>& pa = plan_pairs<T>(pl);
+    if (pl->xterm) {  // the tensor-core kernel has one launch shape (2 blocks per SM)
+        report = "; autotune: not applicable to the tensor-core kernel (fixed launch shape)";
+        return TWED_OK;
+    }
     const double target = 2e10;
     const int64_t stride = std::max<int64_t>(1, (int64_t)((double)pl->cells / target));
     std::vector<int64_t> sample;
@@ -765,15 +776,13 @@ twed_status_t autotune_plan(twed_handle_t h, twed_plan_t pl, const std::vector<i
         float ms;
     };
     std::vector<Cand> cands;
-    if (pl->xterm) {
-        for (int b = 1; b <= max_per_sm; ++b) cands.push_back({0, b, 0.f});
-    } else {
+    {
         const int lim = twed::pairs_rmax_limit<T>();
         for (int r : {2, 4, 6, 8})
             if (r <= lim)
                 for (int b = 1; b <= max_per_sm; ++b) cands.push_back({r, b, 0.f});
     }
-    const int64_t per_block_pairs = pl->xterm ? 1 : 4;
+    const int64_t per_block_pairs = 4;
     const int64_t cap_blocks = std::max<int64_t>(1, std::min<int64_t>(pl->blocks, (ns + per_block_pairs - 1) / per_block_pairs));
     PairsArgs<T> q = pa;
     q.mode = twed::kExplicitPairs;
@@ -782,19 +791,14 @@ twed_status_t autotune_plan(twed_handle_t h, twed_plan_t pl, const std::vector<i
     q.out = (T*)((char*)mem + sizeof(int64_t) * 2 * ns);
     for (Cand& c : cands) {
         if (e != cudaSuccess) break;
-        if (!pl->xterm) q.rmax = c.rmax;
+        q.rmax = c.rmax;
         const int blocks = (int)std::min<int64_t>((int64_t)c.per_sm * h->sms, cap_blocks);
         float best = 1e30f;
         for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
             e = cudaMemsetAsync(pl->counter, 0, sizeof(unsigned long long), st);
             if (e == cudaSuccess) e = cudaEventRecord(e0, st);
             if (e == cudaSuccess) {
-                if constexpr (sizeof(T) == 4) {
-                    if (pl->xterm) e = twed::launch_xterm_pairs(q, blocks, st);
-                    else e = twed::launch_pairs(q, blocks, pl->threads, st);
-                } else {
-                    e = twed::launch_pairs(q, blocks, pl->threads, st);
-                }
+                e = twed::launch_pairs(q, blocks, pl->threads, st);
             }
             if (e == cudaSuccess) e = cudaEventRecord(e1, st);
             if (e == cudaSuccess) e = cudaEventSynchronize(e1);
@@ -818,7 +822,7 @@ twed_status_t autotune_plan(twed_handle_t h, twed_plan_t pl, const std::vector<i
     const Cand* best = &cands[0];
     for (const Cand& c : cands)
         if (c.ms < best->ms) best = &c;
-    if (!pl->xterm) pa.rmax = best->rmax;
+    pa.rmax = best->rmax;
     pl->blocks = (int)std::min<int64_t>((int64_t)best->per_sm * h->sms, pl->blocks);
     char buf[160];
     snprintf(buf, sizeof buf, "; autotuned on %lld sampled pairs (%.2e cells): rows_per_lane<=%d, %d blocks/SM, %.3f ms [",
@@ -893,12 +897,9 @@ twed_status_t plan_create(twed_handle_t h, const S* A, const S* B, int dim, T nu
         delete pl;
         return fail(h, TWED_ERR_INVALID_ARG, "unknown xterm mode %d", o->xterm);
     }
-    if (want_x && (sizeof(T) != 4 || dim != 64 || p != 2 ||
-                   std::max(maxa, maxb) > twed::xterm_max_cols())) {
+    if (want_x && (sizeof(T) != 4 || dim != 64 || p != 2)) {
         delete pl;
-        return fail(h, TWED_ERR_UNSUPPORTED,
-                    "tensor-core cross term: FP32, dim 64, p 2 and series of <= %d points only",
-                    twed::xterm_max_cols());
+        return fail(h, TWED_ERR_UNSUPPORTED, "tensor-core cross term: FP32, dim 64 and p 2 only");
     }
     if (want_x && (((uintptr_t)A->vals & 15) || (!sym && ((uintptr_t)B->vals & 15)))) {
         delete pl;
@@ -906,21 +907,36 @@ twed_status_t plan_create(twed_handle_t h, const S* A, const S* B, int dim, T nu
     }
     pl->xterm = want_x;
     const int rl = pl->xterm ? 4 : twed::rec_len<T>(dim, p);
-    const int threads = pl->xterm ? 192 : 128;
+    const int threads = pl->xterm ? twed::xterm_threads() : 128;
     const int per_sm_raw = pl->xterm ? twed::xterm_blocks_per_sm()
                                      : twed::pairs_blocks_per_sm<T>(dim, p, threads);
     int per_sm = std::max(1, per_sm_raw);
+    // tensor-core plans: work items = one column series x up to CH row series
+    // (sorted order); symmetric plans count them per chunk of rows
+    std::vector<int64_t> chunk_start;
+    int64_t nitems = 0;
     if (pl->xterm) {
-        // The occupancy query reports one block per SM for this kernel although
-        // three fit (shared memory, registers and tensor memory all allow it;
-        // measured: three resident blocks run 2.5x faster than one).  The
-        // persistent kernel claims pairs dynamically, so blocks beyond the
-        // resident ones would only queue: size the grid from the resources.
+        // the persistent kernel claims items dynamically, so blocks beyond the
+        // resident ones would only queue: size the grid from the resources
+        // (shared memory, registers, tensor memory), which the occupancy
+        // query does not see in full
         per_sm = std::max(per_sm, twed::xterm_resident_blocks());
         if (const char* v = getenv("TWED_XTERM_BLOCKS_PER_SM")) per_sm = std::max(1, atoi(v));
+        const int64_t CH = twed::xterm_rows_per_item();
+        const int64_t nch = (A->n + CH - 1) / CH;
+        if (!sym) {
+            nitems = nch * B->n;
+        } else {
+            chunk_start.resize((size_t)nch + 1);
+            for (int64_t c = 0; c < nch; ++c) {
+                chunk_start[(size_t)c] = nitems;
+                nitems += std::min((c + 1) * CH, A->n) - 1;
+            }
+            chunk_start[(size_t)nch] = nitems;
+        }
     }
     const int64_t want_blocks = (int64_t)per_sm * h->sms;
-    const int64_t need_blocks = pl->xterm ? std::max<int64_t>(1, pl->npairs)
+    const int64_t need_blocks = pl->xterm ? std::max<int64_t>(1, nitems)
                                           : std::max<int64_t>(1, (pl->npairs + 3) / 4);
     pl->blocks = (int)std::min(want_blocks, need_blocks);
     pl->threads = threads;
@@ -933,6 +949,10 @@ twed_status_t plan_create(twed_handle_t h, const S* A, const S* B, int dim, T nu
     const size_t o_pa = cv.take(sizeof(int32_t) * perm_a.size());
     const size_t o_pb = sym ? 0 : cv.take(sizeof(int32_t) * perm_b.size());
     const size_t o_scr = cv.take(sizeof(T) * 2 * (size_t)nwarps * (size_t)scols);
+    const int64_t xbnd = pl->xterm ? twed::xterm_bnd_stride(std::max(maxa, maxb)) : 0;
+    const size_t o_xb = pl->xterm ? cv.take(sizeof(float) * 2 * (size_t)pl->blocks *
+                                            (size_t)twed::xterm_warps_per_block() * (size_t)xbnd) : 0;
+    const size_t o_cs = chunk_start.empty() ? 0 : cv.take(sizeof(int64_t) * chunk_start.size());
     const size_t o_ctl = cv.take(64);
     pl->mem_bytes = cv.off;
     cudaError_t e = cudaMalloc(&pl->mem, pl->mem_bytes);
@@ -947,7 +967,12 @@ twed_status_t plan_create(twed_handle_t h, const S* A, const S* B, int dim, T nu
     e = cudaMemcpy(base + o_pa, perm_a.data(), sizeof(int32_t) * perm_a.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !sym)
         e = cudaMemcpy(base + o_pb, perm_b.data(), sizeof(int32_t) * perm_b.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !chunk_start.empty())
+        e = cudaMemcpy(base + o_cs, chunk_start.data(), sizeof(int64_t) * chunk_start.size(),
+                       cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(pl->ctl, 0, 64);
+    if (e == cudaSuccess && pl->xterm)
+        e = twed::xterm_tensor_map(pl->tmap, (const float*)(sym ? A->vals : B->vals), sym ? tota : totb);
     if (e != cudaSuccess) {
         cudaGetLastError();
         cudaFree(pl->mem);
@@ -987,6 +1012,30 @@ twed_status_t plan_create(twed_handle_t h, const S* A, const S* B, int dim, T nu
     pa.sc.timeout_ns = timeout_ns(o);
     pa.sc.stall_strip = -1;
     pa.sc.sleep_ns = h->sleep_ns;
+    if constexpr (sizeof(T) == 4) {
+        if (pl->xterm) {
+            twed::XtermArgs& xa = pl->xa;
+            xa.vals_a = A->vals;
+            xa.rec_a = (const float4*)rec_a;
+            xa.rec_b = (const float4*)rec_b;
+            xa.offs_a = A->offs;
+            xa.offs_b = sym ? A->offs : B->offs;
+            xa.perm_a = pa.perm_a;
+            xa.perm_b = pa.perm_b;
+            xa.na = pl->na;
+            xa.nb = pl->nb;
+            xa.symmetric = sym ? 1 : 0;
+            xa.nitems = nitems;
+            xa.chunk_start = chunk_start.empty() ? nullptr : (const int64_t*)(base + o_cs);
+            xa.nchunks = chunk_start.empty() ? 0 : (int64_t)chunk_start.size() - 1;
+            xa.nu = nu;
+            xa.out = nullptr;
+            xa.bnd = (float2*)(base + o_xb);
+            xa.bnd_stride = xbnd;
+            xa.counter = pl->counter;
+            xa.sc = pa.sc;
+        }
+    }
 
     // Schedule cut-over: a pair with more cells than the plan's average work
     // per warp would leave one warp running long after the others finish;
@@ -1093,9 +1142,10 @@ twed_status_t plan_create(twed_handle_t h, const S* A, const S* B, int dim, T nu
         char r[200];
         twed::xterm_resources(r, sizeof r);
         snprintf(d, sizeof d,
-                 "f32 tensor-core cross term (tf32) pairs=%lld blocks=%d x %d threads "
+                 "f32 tensor-core cross term (tf32) pairs=%lld items=%lld blocks=%d x %d threads "
                  "(%d resident per SM by shared memory, registers and TMEM; occupancy query %d; %s)",
-                 (long long)pl->npairs, pl->blocks, threads, twed::xterm_resident_blocks(), per_sm_raw, r);
+                 (long long)pl->npairs, (long long)nitems, pl->blocks, threads, twed::xterm_resident_blocks(),
+                 per_sm_raw, r);
     }
     else
         snprintf(d, sizeof d, "%s pairs=%lld warps=%lld rows_per_lane<=%d blocks=%d x %d threads",
@@ -1163,6 +1213,19 @@ extern "C" twed_status_t twed_plan_execute(twed_plan_t pl, void* d_out, void* st
         if (s != TWED_OK) return s;
     }
     TWED_CUDA(pl->h, cudaGraphLaunch(pl->exec, (cudaStream_t)stream));
+    return TWED_OK;
+}
+
+extern "C" twed_status_t twed_plan_status(twed_plan_t pl, void* stream) {
+    if (!pl) return TWED_ERR_INVALID_ARG;
+    twed_handle_t h = pl->h;
+    TWED_CUDA(h, cudaStreamSynchronize((cudaStream_t)stream));
+    unsigned sticky = 0, zero = 0;
+    TWED_CUDA(h, cudaMemcpy(&sticky, pl->ctl + 1, sizeof sticky, cudaMemcpyDeviceToHost));
+    if (sticky) {
+        TWED_CUDA(h, cudaMemcpy(pl->ctl + 1, &zero, sizeof zero, cudaMemcpyHostToDevice));
+        return fail(h, (twed_status_t)sticky, "plan: %s", device_error_text(sticky));
+    }
     return TWED_OK;
 }
 

@@ -122,13 +122,41 @@ template <typename T>
 int pairs_rmax_limit();
 
 // Tensor-core cross-term path (xterm.cu): dim 64, p = 2, FP32.
-// Records are float4 (t, delete cost, |x|^2, 0) per point.
+// Records are float4 (t, delete cost, |x|^2, 0) per point.  Work items pair
+// one column series with up to xterm_rows_per_item() row series taken in
+// the sorted (longest-first) order; rows come from set A, columns from set
+// B (set A again when symmetric).
+struct XtermArgs {
+    const float* vals_a;          // row set values [total_a][64], 16-byte aligned
+    const float4* rec_a;          // row set records
+    const float4* rec_b;          // column set records
+    const int64_t* offs_a;
+    const int64_t* offs_b;
+    const int32_t* perm_a;        // sorted position -> series (longest first)
+    const int32_t* perm_b;
+    int64_t na, nb;
+    int symmetric;                // 1: out[x][y] and out[y][x] for row x < column y in sorted order
+    int64_t nitems;
+    const int64_t* chunk_start;   // symmetric: first item of each chunk of rows [nchunks + 1]
+    int64_t nchunks;
+    float nu;
+    float* out;
+    float2* bnd;                  // per consumer warp: bnd_stride (D, c) of a strip's bottom row
+    int64_t bnd_stride;           // xterm_bnd_stride(longest column series)
+    unsigned long long* counter;  // work item counter, zero before the launch
+    SyncCtl sc;
+};
 cudaError_t launch_xrecords(const RecordsArgs<float>& a, cudaStream_t st);
-cudaError_t launch_xterm_pairs(const PairsArgs<float>& a, int blocks, cudaStream_t st);
+// tmap: 128-byte CUtensorMap of the column set's values (xterm_tensor_map)
+cudaError_t xterm_tensor_map(void* tmap, const float* vals, int64_t total);
+cudaError_t launch_xterm(const void* tmap, const XtermArgs& a, int blocks, cudaStream_t st);
 int xterm_blocks_per_sm();
-int xterm_max_cols();
 int xterm_resident_blocks();
 void xterm_resources(char* buf, int len);
+int xterm_rows_per_item();
+int xterm_warps_per_block();  // consumer warps
+int xterm_threads();
+int64_t xterm_bnd_stride(int64_t max_len);
 
 // Writes 0 to out[i*n + i], i < n.
 cudaError_t launch_zero_diag(void* out, bool f64, int64_t n, cudaStream_t st);

@@ -1,33 +1,42 @@
 // Tensor-core cross term for 64-dimensional FP32 series (p = 2).
 //
-// For p = 2, d(a_i, b_j)^2 = |a_i|^2 + |b_j|^2 - 2 a_i . b_j; the dot products
-// of a 128-row strip of series a against a 16-column tile of series b form a
-// dense 128 x 16 x 64 contraction.  It runs on the 5th-generation tensor cores
-// (tcgen05.mma, TF32 inputs, FP32 accumulation in tensor memory); the norms
-// stay FP32 on CUDA cores, and the cell cost c(i,j) = sqrt(max(d^2, 0)) +
-// nu |t_i - t'_j| is formed in FP32 before the wavefront consumes it.  The
-// recurrence itself (paper, section "Time Warp Edit Distance", step 5) is the
-// same as everywhere else in this library.
+// For p = 2, d(a_i, b_j)^2 = |a_i|^2 + |b_j|^2 - 2 a_i . b_j, and the dot
+// products of a block of rows of series a against a tile of columns of
+// series b form a dense contraction with K = 64.  It runs on the
+// 5th-generation tensor cores (tcgen05.mma, TF32 inputs, FP32 accumulation in
+// tensor memory); the norms stay FP32, and the cell cost c(i,j) =
+// sqrt(max(d^2, 0)) + nu |t_i - t'_j| is formed in FP32 before the wavefront
+// consumes it.  The recurrence itself (paper, section "Time Warp Edit
+// Distance", step 5) is the same as everywhere else in this library.
 //
-// One persistent block handles one pair at a time (pairs from an atomic
-// counter, longest series first); four blocks share an SM (shared memory
-// 54 KB and 128 TMEM columns each).  Warp roles:
-//   warp 0      producer: cp.async of the column tiles (B) into a 3-deep
-//               shared-memory ring in the K-major core-matrix layout, two
-//               tiles ahead; tcgen05.mma issue (A from tensor memory),
-//               tcgen05.commit to an mbarrier.  Also owns the TMEM.
-//   warps 1..4  epilogue: at each strip, load the strip's 128 points (one
-//               per thread) into tensor memory with tcgen05.st (A operand);
-//               per tile, tcgen05.ld of their TMEM lane quarter, cost
-//               formation, store into a 4-tile ring of cost tiles [col][row]
-//               with the tile's column delete costs beside it.
-//   warp 5      wavefront: 32 lanes x 4 rows = the strip's 128 rows, lane L
-//               on column s - L at step s, costs read from the ring, in
-//               branch-free blocks of 16 steps (one tile of lane 0).
+// Work item: one column series y and up to CH row series (consecutive in the
+// longest-first order).  A block holds four consumer warps; warp q owns TMEM
+// lane quadrant q, and in every "sweep" each consumer runs one strip of 64
+// rows (2 per lane) of its current row series against all of y's columns.
+// The four strips of a sweep share every B tile (y's points): the MMA of one
+// 16-column tile is 2 x (128 x 16 x 64), A = the four strips' rows in TMEM
+// (row 2L + r of warp q's strip on lane 32q + L of row tile r), written there
+// by the consumers themselves with tcgen05.st.  Roles:
+//   warps 0..3  consumers: per 16-step block, tcgen05.ld of their own lanes'
+//               accumulators of the next tile, cost formation for it
+//               interleaved with the 16 wavefront steps of the current tile
+//               (lane L on column s - L + 1 at step s), costs through a
+//               private skewed shared-memory ring; the bottom rows of a strip
+//               go to a per-warp boundary row in global memory, read back by
+//               the warp's next strip of the same series.
+//   warp 4      TMA (cp.async.bulk.tensor) of the B tiles into a 4-stage
+//               ring, as far ahead as the ring allows.
+//   warp 5      tcgen05.mma issue and tcgen05.commit (to the consumers'
+//               accumulator barrier and to the B stage's free barrier).
+// Columns past m get cost +inf and column delete cost 0, which freezes every
+// row at its column-m value, so all lanes can run the same number of steps.
 // Every wait is bounded (%globaltimer, then the launch's error word).
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <cstdio>
+#include <utility>
 
 #include "kernels.cuh"
 #include "tc.cuh"
@@ -35,27 +44,43 @@
 namespace twed {
 
 namespace x64 {
-constexpr int D = 64;         // point dimension (MMA K)
-constexpr int M = 128;        // rows per strip (MMA M)
-constexpr int N = 16;         // columns per tile (MMA N)
-constexpr int R = 4;          // wavefront rows per lane
-constexpr int NB = 2;         // TMEM accumulators in flight
-constexpr int NBB = 3;        // B tiles in the shared-memory ring
-constexpr int PREF = 2;       // B tiles loaded ahead of the MMA
-constexpr int NC = 4;         // cost tiles in the ring (wavefront span 3 + lead 1)
-constexpr int MAXCOL = 1024;  // longest column series (boundary row kept in smem)
-constexpr int THREADS = 192;
-constexpr int TMEM_COLS = 128;  // NB*N accumulator columns + D columns of A
-constexpr int ACOL = 64;        // first TMEM column of the A strip
+constexpr int D = 64;            // point dimension (MMA K)
+constexpr int RT = 2;            // row tiles per block = DP rows per lane
+constexpr int N = 16;            // columns per tile = wavefront steps per block
+constexpr int NS = 4;            // accumulator stages in TMEM
+constexpr int NBS = 4;           // B tile stages in shared memory (== NS)
+constexpr int CW = 4;            // consumer warps (one per TMEM lane quadrant)
+constexpr int TMA_WARP = CW;     // B tile loads
+constexpr int MMA_WARP = CW + 1; // tcgen05.mma issue
+constexpr int THREADS = 32 * (CW + 2);
+constexpr int STRIP = 32 * RT;   // rows per consumer strip
+constexpr int CRING = 128;       // columns in a consumer's column-record ring (staged 32 at a time)
+constexpr int RING = 64;         // columns in a consumer's cost ring
+constexpr int RMIR = RING + N;   // ring slots incl. a mirror of slots 0..N-1 (no wrap inside a block)
+constexpr int RS = 2 * (RMIR + 2); // floats per lane: 82 float2, == 2 mod 4 (conflict-free v2 reads, v4 writes)
+constexpr int CH = 64;           // row series per work item
+constexpr int TMEM_COLS = 256;
+constexpr int ACC_COL = RT * D;  // accumulators follow the A tiles
+constexpr int BOXES = D / 4;     // TMA boxes per B tile: 4 values x N points each
+constexpr uint32_t TILE_BYTES = N * D * 4;
+constexpr int BND_PAD = 32;      // boundary rows start 32 entries in (lane 31 writes from column -30)
 
-constexpr int OFF_B = 0;                               // NBB tiles of N*D floats
-constexpr int OFF_C = OFF_B + NBB * N * D * 4;         // NC tiles [N][M] costs
-constexpr int OFF_DEL = OFF_C + NC * N * M * 4;        // NC tiles of N column delete costs
-constexpr int OFF_ROW = OFF_DEL + NC * N * 4;          // MAXCOL + 1 float2: boundary row, spare
-constexpr int OFF_BAR = OFF_ROW + (MAXCOL + 1) * 8;    // mbarriers
-constexpr int NBAR = NB + NB + NC + NC + 1;            // mma_done, tmem_empty, cost_full, cost_empty, a_ready
-constexpr int OFF_MISC = OFF_BAR + NBAR * 8;           // tmem base, pair index
+constexpr int OFF_B = 0;
+constexpr int OFF_RING = OFF_B + NBS * (int)TILE_BYTES;
+constexpr int RING_WARP = 32 * RS * 4;
+constexpr int OFF_CTIME = OFF_RING + CW * RING_WARP;  // per warp: CRING column times t'
+constexpr int OFF_CNORM = OFF_CTIME + CW * CRING * 4; // per warp: CRING column norms |b|^2
+constexpr int DMIR = CRING + N;                       // column delete costs incl. a mirror of slots 0..N-1
+constexpr int OFF_DELB = OFF_CNORM + CW * CRING * 4;  // per warp: DMIR column delete costs
+constexpr int OFF_BND = OFF_DELB + CW * DMIR * 4;     // per warp: 64 staged (D, c) of the row above
+constexpr int OFF_BAR = OFF_BND + CW * 64 * 8;
+constexpr int NBAR = NBS + NBS + NS + NS + 1;         // b_full, b_empty, acc_full, acc_empty, a_ready
+constexpr int OFF_SCHED = OFF_BAR + NBAR * 8;         // per warp: its copy of the strip schedule
+constexpr int SCHED_BYTES = 128;
+constexpr int OFF_MISC = OFF_SCHED + (CW + 2) * SCHED_BYTES;  // tmem base, item index
 constexpr int SMEM = OFF_MISC + 64;
+static_assert((OFF_RING % 16) == 0 && (RING_WARP % 16) == 0, "vector access alignment");
+static_assert((OFF_SCHED % 8) == 0, "schedule alignment");
 }  // namespace x64
 
 // Point records for the tensor-core path: (t, delete cost, |x|^2, 0).
@@ -91,394 +116,536 @@ __global__ void __launch_bounds__(256) xrecords_kernel(RecordsArgs<float> a) {
 
 namespace {
 
-__device__ __forceinline__ void cp_async16_zfill(void* smem, const void* gmem, bool valid) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    const int n = valid ? 16 : 0;
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(s), "l"(gmem), "r"(n) : "memory");
-}
-
 // Bounded wait on an mbarrier phase: false (and the error word set) after
 // sc.timeout_ns of %globaltimer, or as soon as another role has failed.
-__device__ __forceinline__ bool xwait(uint64_t* bar, uint32_t parity, const SyncCtl& sc) {
-    if (tc::mbar_try_wait(bar, parity)) return true;
+// Bounded waits on an mbarrier phase: false (and the error word set) after
+// sc.timeout_ns of %globaltimer, or as soon as another role has failed.
+// They poll with the non-blocking test_wait and back off with nanosleep in
+// between (try_wait would wait inside the instruction, and a warp waiting
+// there keeps taking issue slots from the consumers' wavefront).  Consumers'
+// waits are rare and short (16 ns back-off); the TMA and MMA warps run
+// ahead and wait most of the time (longer back-off).
+__device__ __forceinline__ bool xwait_fail(const SyncCtl& sc, unsigned long long t0) {
+    if (*(volatile unsigned*)sc.err != 0u) return true;
+    if (globaltimer() - t0 > sc.timeout_ns) {
+        atomicCAS(sc.err, 0u, 4u);
+        atomicCAS(sc.sticky, 0u, 4u);
+        return true;
+    }
+    return false;
+}
+__device__ __forceinline__ bool xwait_sleep(uint64_t* bar, uint32_t parity, const SyncCtl& sc,
+                                            unsigned ns = 128) {
+    if (tc::mbar_test_wait(bar, parity)) return true;
     const unsigned long long t0 = globaltimer();
-    uint32_t spins = 0;
-    while (!tc::mbar_try_wait(bar, parity)) {
-        if ((++spins & 15u) == 0) {
-            if (*(volatile unsigned*)sc.err != 0u) return false;
-            if (globaltimer() - t0 > sc.timeout_ns) {
-                atomicCAS(sc.err, 0u, 4u);
-                atomicCAS(sc.sticky, 0u, 4u);
-                return false;
-            }
-        }
+    uint32_t k = 0;
+    while (!tc::mbar_test_wait(bar, parity)) {
+        __nanosleep(ns);
+        if ((++k & 15u) == 0 && xwait_fail(sc, t0)) return false;
     }
     return true;
+}
+__device__ __forceinline__ bool xwait(uint64_t* bar, uint32_t parity, const SyncCtl& sc) {
+    return xwait_sleep(bar, parity, sc, 16);
+}
+
+// Predicated 8-byte global store at p + OFF bytes (no branch around it).
+template <int OFF>
+__device__ __forceinline__ void st_global_pred(float2* p, float a, float b, int pred) {
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %3, 0;\n\t@q st.global.v2.f32 [%0+%4], {%1, %2};\n\t}" ::"l"(p),
+                 "f"(a), "f"(b), "r"(pred), "n"(OFF)
+                 : "memory");
+}
+
+// f(integral_constant<int, 0>) .. f(integral_constant<int, N-1>): a loop whose
+// index is a constant expression in the body.
+template <typename F, int... I>
+__device__ __forceinline__ void unroll_seq(F&& f, std::integer_sequence<int, I...>) {
+    (f(std::integral_constant<int, I>{}), ...);
+}
+
+// One work item: column series y, row series at sorted positions [r_lo, r_hi).
+struct XItem {
+    int64_t y, yb;
+    int m;
+    int64_t r_lo, r_hi;
+};
+
+__device__ __forceinline__ XItem decode_item(const XtermArgs& a, int64_t w) {
+    XItem it;
+    if (!a.symmetric) {
+        const int64_t c = w / a.nb, q = w % a.nb;
+        it.y = a.perm_b[q];
+        it.r_lo = c * x64::CH;
+        it.r_hi = min(it.r_lo + (int64_t)x64::CH, a.na);
+    } else {
+        // chunk c holds items chunk_start[c] .. chunk_start[c+1]-1; item p of
+        // chunk c is column series p against rows max(p+1, c*CH) .. hi-1
+        int64_t lo = 0, hi = a.nchunks;
+        while (hi - lo > 1) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (a.chunk_start[mid] <= w) lo = mid; else hi = mid;
+        }
+        const int64_t p = w - a.chunk_start[lo];
+        it.y = a.perm_b[p];
+        it.r_lo = max(p + 1, lo * (int64_t)x64::CH);
+        it.r_hi = min((lo + 1) * (int64_t)x64::CH, a.na);
+    }
+    it.yb = a.offs_b[it.y];
+    it.m = (int)(a.offs_b[it.y + 1] - it.yb);
+    return it;
+}
+
+// Which strip each consumer runs in a sweep: a warp whose series is done
+// takes the next row series of the item.  Every warp of the block runs the
+// same bookkeeping, so they agree without communicating.
+struct XSched {  // 72 bytes
+    int64_t next;
+    int64_t pos[x64::CW];  // sorted row position of each warp's series (-1: idle)
+    int rem[x64::CW];      // strips left, the current one included
+    int k[x64::CW];        // current strip index
+};
+
+__device__ __forceinline__ int series_len(const XtermArgs& a, int64_t pos) {
+    const int64_t x = a.perm_a[pos];
+    return (int)(a.offs_a[x + 1] - a.offs_a[x]);
+}
+
+__device__ __forceinline__ void sched_init(XSched& s, const XItem& it) {
+    s.next = it.r_lo;
+#pragma unroll
+    for (int w = 0; w < x64::CW; ++w) {
+        s.pos[w] = -1;
+        s.rem[w] = 0;
+        s.k[w] = 0;
+    }
+}
+// Assignments of the next sweep; false when the item is finished.
+__device__ __forceinline__ bool sched_begin(XSched& s, const XtermArgs& a, const XItem& it) {
+    bool any = false;
+#pragma unroll
+    for (int w = 0; w < x64::CW; ++w) {
+        if (s.rem[w] == 0) {
+            if (s.next < it.r_hi) {
+                s.pos[w] = s.next++;
+                s.rem[w] = (series_len(a, s.pos[w]) + x64::STRIP - 1) / x64::STRIP;
+                s.k[w] = 0;
+            } else {
+                s.pos[w] = -1;
+            }
+        }
+        any |= s.rem[w] > 0;
+    }
+    return any;
+}
+__device__ __forceinline__ void sched_end(XSched& s) {
+#pragma unroll
+    for (int w = 0; w < x64::CW; ++w) {
+        if (s.rem[w] > 0) {
+            --s.rem[w];
+            ++s.k[w];
+        }
+    }
+}
+
+__device__ __forceinline__ void st_shared_v4(float* p, float a, float b, float c, float d) {
+    *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
 }
 
 }  // namespace
 
-// cp.async.wait_group needs an immediate: wait until at most `pending`
-// groups of this thread are still in flight (pending <= PREF).
-__device__ __forceinline__ void cp_async_wait_pending(int pending) {
-    if (pending <= 0) asm volatile("cp.async.wait_group 0;" ::: "memory");
-    else if (pending == 1) asm volatile("cp.async.wait_group 1;" ::: "memory");
-    else asm volatile("cp.async.wait_group 2;" ::: "memory");
-}
-
-// PairsArgs as for pairs_kernel; rec_a / rec_b hold x64 records (float4 per
-// point) and vals_a / vals_b the raw 64-dimensional points (16-byte aligned).
-__global__ void __launch_bounds__(x64::THREADS) xterm_pairs_kernel(PairsArgs<float> a) {
+__global__ void __launch_bounds__(x64::THREADS, 2) xterm_sweep_kernel(const __grid_constant__ CUtensorMap tmap_b,
+                                                                   XtermArgs a) {
     using namespace x64;
-    static_assert(PREF <= 2 && PREF < NBB, "cp_async_wait_pending covers PREF <= 2");
     extern __shared__ __align__(1024) unsigned char sm[];
-    float* sC = reinterpret_cast<float*>(sm + OFF_C);
-    float* sDel = reinterpret_cast<float*>(sm + OFF_DEL);
-    float2* sRow = reinterpret_cast<float2*>(sm + OFF_ROW);
     uint64_t* bar = reinterpret_cast<uint64_t*>(sm + OFF_BAR);
-    uint64_t* mma_done = bar;
-    uint64_t* tmem_empty = bar + NB;
-    uint64_t* cost_full = bar + 2 * NB;
-    uint64_t* cost_empty = bar + 2 * NB + NC;
-    uint64_t* a_ready = bar + 2 * NB + 2 * NC;
+    uint64_t* b_full = bar;
+    uint64_t* b_empty = bar + NBS;
+    uint64_t* acc_full = bar + 2 * NBS;
+    uint64_t* acc_empty = bar + 2 * NBS + NS;
+    uint64_t* a_ready = bar + 2 * NBS + 2 * NS;
     uint32_t* misc = reinterpret_cast<uint32_t*>(sm + OFF_MISC);
-    volatile long long* pair_sh = reinterpret_cast<volatile long long*>(misc + 2);
+    volatile long long* item_sh = reinterpret_cast<volatile long long*>(misc + 2);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const float INF = __int_as_float(0x7f800000);
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < NB; ++i) {
-            tc::mbar_init(&mma_done[i], 1);
-            tc::mbar_init(&tmem_empty[i], 4);
+        for (int i = 0; i < NBS; ++i) {
+            tc::mbar_init(&b_full[i], 1);
+            tc::mbar_init(&b_empty[i], 1);
         }
-        for (int i = 0; i < NC; ++i) {
-            tc::mbar_init(&cost_full[i], 4);
-            tc::mbar_init(&cost_empty[i], 1);
+        for (int i = 0; i < NS; ++i) {
+            tc::mbar_init(&acc_full[i], 1);
+            tc::mbar_init(&acc_empty[i], CW);
         }
-        tc::mbar_init(a_ready, 4);
+        tc::mbar_init(a_ready, CW);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) tc::tmem_alloc(misc, TMEM_COLS);
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = misc[0];
-    const uint32_t idesc = tc::idesc_tf32(M, N);
+    const uint32_t idesc = tc::idesc_tf32(128, N);
+    // the TMA destinations need a 1024-byte aligned shared window
+    const bool aligned = (tc::smem_u32(sm) & 1023u) == 0;
 
-    // per-role running counters (identical sequences in every role)
-    long long t_prod = 0, t_epi = 0, t_dp = 0;  // tiles
-    long long s_prod = 0, s_epi = 0;            // strips
-    bool ok = true;
+    // running counters, identical in every role
+    uint32_t Lp = 0;               // TMA warp: B tiles loaded
+    uint32_t Tp = 0, sweep_p = 0;  // MMA warp: tiles issued, sweeps
+    uint32_t Tc = 0;               // consumers: accumulator tiles read
+    bool ok = aligned;
+    if (!aligned && threadIdx.x == 0) {
+        atomicCAS(a.sc.err, 0u, 5u);
+        atomicCAS(a.sc.sticky, 0u, 5u);
+    }
     while (true) {
         __syncthreads();
         if (threadIdx.x == 0) {
             const bool failed = *(volatile unsigned*)a.sc.err != 0u;
-            *pair_sh = failed ? a.npairs : (long long)atomicAdd(a.counter, 1ull);
+            *item_sh = failed ? a.nitems : (long long)atomicAdd(a.counter, 1ull);
         }
         __syncthreads();
-        const long long w = *pair_sh;  // block-uniform: every role stops together
-        if (w >= a.npairs) break;
-        // ---- the pair (same mapping as pairs_kernel)
-        int64_t x, y;
-        float *o1, *o2 = nullptr;
-        if (a.mode == kExplicitPairs) {
-            x = a.pairs[2 * w];
-            y = a.pairs[2 * w + 1];
-            o1 = a.out + w;
-            if (!pair_in_range(x, y, a.na, a.nb)) {  // block-uniform
-                if (threadIdx.x == 0) flag_bad_pair(o1, a.sc);
-                continue;
-            }
-        } else if (a.mode == kSymmetricSorted) {
-            int64_t pp, qq;
-            triangle_pos((int64_t)w, a.na, pp, qq);
-            x = a.perm_a[pp];
-            y = a.perm_a[qq];
-            o1 = a.out + x * a.na + y;
-            o2 = a.out + y * a.na + x;
-        } else {
-            const int64_t pp = (int64_t)w / a.nb, qq = (int64_t)w % a.nb;
-            x = a.perm_a[pp];
-            y = a.perm_b[qq];
-            o1 = a.out + x * a.nb + y;
-        }
-        const int64_t xa = a.offs_a[x], nx = a.offs_a[x + 1] - xa;
-        const int64_t yb = a.offs_b[y], ny = a.offs_b[y + 1] - yb;
-        const bool swap = nx > ny;  // rows = shorter series
-        const float* rvals = swap ? a.vals_b + yb * D : a.vals_a + xa * D;
-        const float* cvals = swap ? a.vals_a + xa * D : a.vals_b + yb * D;
-        const float4* rrec = reinterpret_cast<const float4*>(swap ? a.rec_b : a.rec_a) + (swap ? yb : xa);
-        const float4* crec = reinterpret_cast<const float4*>(swap ? a.rec_a : a.rec_b) + (swap ? xa : yb);
-        const int n = (int)(swap ? ny : nx), m = (int)(swap ? nx : ny);
-        const int nstrips = (n + M - 1) / M, ntiles = (m + N - 1) / N;
-        const int K = nstrips * ntiles;  // tiles of this pair, strip-major
+        const long long w = *item_sh;  // block-uniform
+        if (w >= a.nitems || !ok) break;
+        const XItem it = decode_item(a, w);
+        const int m = it.m;
+        const int ntiles = (m + N - 1) / N;
+        // each warp keeps its copy of the schedule in shared memory (every lane
+        // computes the same values)
+        XSched& sch = *reinterpret_cast<XSched*>(sm + OFF_SCHED + warp * SCHED_BYTES);
+        sched_init(sch, it);
+        __syncwarp();
 
-        if (warp == 0) {
-            // ================= producer
-            const long long t_base = t_prod;
-            int issued = 0;  // B tiles of this pair whose copies were issued
-            // B tile k of this pair (column tile k % ntiles) into ring slot (t_base + k) % NBB;
-            // the slot was last read by the MMA of tile t_base + k - NBB.  Tiles of
-            // earlier pairs are all complete (every role finished them before the
-            // block moved on), and waiting on their phases could alias a later
-            // phase of the same barrier, so only this pair's tiles are waited for.
-            auto issue_load = [&](int k) -> bool {
-                const long long t = t_base + k;
-                if (k >= NBB) {
-                    const long long tp = t - NBB;
-                    if (!xwait(&mma_done[tp % NB], (uint32_t)((tp / NB) & 1), a.sc)) return false;
+        if (warp >= CW) {
+            uint32_t total = 0;
+            {
+                uint32_t nsw = 0;
+                while (sched_begin(sch, a, it)) {
+                    ++nsw;
+                    sched_end(sch);
                 }
-                unsigned char* sB = sm + OFF_B + (int)(t % NBB) * N * D * 4;
-                const int c0 = (k % ntiles) * N;
-                for (int c = lane; c < N * (D / 4); c += 32) {
-                    const int col = c / (D / 4), kq = c % (D / 4);
-                    const bool v = c0 + col < m;
-                    const float* src = cvals + (int64_t)(v ? c0 + col : 0) * D + kq * 4;
-                    cp_async16_zfill(sB + tc::kmajor_offset(col, kq * 4, D), src, v);
-                }
-                cp_async_commit();
-                return true;
-            };
-            for (int k = 0; k < K && ok; ++k) {
-                while (issued < K && issued <= k + PREF && ok) {
-                    ok = __all_sync(kFull, issue_load(issued));
-                    ++issued;
-                }
-                if (!ok) break;
-                cp_async_wait_pending(issued - k - 1);  // tile k's copies are in
-                tc::fence_proxy_async_smem();
-                __syncwarp();
-                const long long t = t_prod;
-                const int b = (int)(t % NB);
-                bool w2 = true;
-                if (k % ntiles == 0) w2 = xwait(a_ready, (uint32_t)(s_prod & 1), a.sc);  // strip's A in TMEM
-                if (w2 && t >= NB) w2 = xwait(&tmem_empty[b], (uint32_t)(((t - NB) / NB) & 1), a.sc);
-                if (!__all_sync(kFull, w2)) { ok = false; break; }
-                tc::fence_after_sync();
-                if (lane == 0) {
-                    const uint32_t bad = tc::smem_u32(sm + OFF_B + (int)(t % NBB) * N * D * 4);
-#pragma unroll
-                    for (int ks = 0; ks < D / 8; ++ks) {
-                        const uint64_t bd = tc::smem_desc(bad + ks * 2 * tc::kmajor_lbo(), tc::kmajor_lbo(), tc::kmajor_sbo(D));
-                        tc::mma_tf32_tmem_a(tmem + (uint32_t)(b * N), tmem + (uint32_t)(ACOL + ks * 8), bd, idesc, ks > 0);
-                    }
-                    tc::mma_commit(&mma_done[b]);
-                }
-                __syncwarp();
-                ++t_prod;
-                if (k % ntiles == ntiles - 1) ++s_prod;
+                total = nsw * (uint32_t)ntiles;
             }
-            cp_async_wait_all();
-        } else if (warp <= 4) {
-            // ================= epilogue: TMEM lane quarter q = warp % 4
-            const int q = warp & 3;
-            for (int st = 0; st < nstrips && ok; ++st) {
-                const int row = st * M + 32 * q + lane;  // 0-based row of the pair
-                const int rowc = row < n ? row : n - 1;
-                const float4 ri = __ldg(rrec + rowc);
-                const float na = ri.z, ti = ri.x;
-                {   // this strip's A: every MMA of the previous strip has completed
-                    // (this warp waited for each of them), so TMEM columns ACOL.. are free
-                    const float4* src = reinterpret_cast<const float4*>(rvals + (int64_t)rowc * D);
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        float v[32];
-#pragma unroll
-                        for (int u = 0; u < 8; ++u) {
-                            const float4 f = __ldg(src + h * 8 + u);
-                            v[4 * u] = f.x;
-                            v[4 * u + 1] = f.y;
-                            v[4 * u + 2] = f.z;
-                            v[4 * u + 3] = f.w;
-                        }
-                        tc::tmem_st32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(ACOL + 32 * h), v);
-                    }
-                    tc::tmem_wait_st();
-                    tc::fence_before_sync();
+            if (warp == TMA_WARP) {
+                // ======================= B tiles by TMA, up to NBS ahead of the MMA
+                for (uint32_t idx = 0; idx < total; ++idx) {
+                    const int st = (int)(Lp % NBS);
+                    bool w2 = true;
+                    if (Lp >= NBS) w2 = xwait_sleep(&b_empty[st], ((Lp / NBS) - 1) & 1, a.sc, 512);
+                    if (!__all_sync(kFull, w2)) { ok = false; break; }
+                    const int t = (int)(idx % (uint32_t)ntiles);
+                    unsigned char* dst = sm + OFF_B + st * TILE_BYTES;
+                    if (lane == 0) tc::mbar_arrive_expect_tx(&b_full[st], TILE_BYTES);
                     __syncwarp();
-                    if (lane == 0) tc::mbar_arrive(a_ready);
-                    ++s_epi;
+                    if (lane < BOXES)
+                        tc::tma_load_2d(dst + lane * (N * 16), &tmap_b, 4 * lane, (int)(it.yb + (int64_t)N * t),
+                                        &b_full[st]);
+                    __syncwarp();
+                    ++Lp;
                 }
-                for (int tt = 0; tt < ntiles; ++tt, ++t_epi) {
-                    const int b = (int)(t_epi % NB), cb = (int)(t_epi % NC);
-                    bool w2 = xwait(&mma_done[b], (uint32_t)((t_epi / NB) & 1), a.sc);
-                    if (w2 && t_epi >= NC) w2 = xwait(&cost_empty[cb], (uint32_t)(((t_epi - NC) / NC) & 1), a.sc);
+            } else {
+                // ======================= MMA issue
+                for (uint32_t idx = 0; idx < total; ++idx) {
+                    const int st = (int)(Tp % NBS), s = (int)(Tp % NS);
+                    const int t = (int)(idx % (uint32_t)ntiles);
+                    bool w2 = xwait_sleep(&b_full[st], (Tp / NBS) & 1, a.sc, 128);
+                    if (w2 && t == 0) w2 = xwait_sleep(a_ready, sweep_p & 1, a.sc, 32);
+                    if (w2 && Tp >= NS) w2 = xwait_sleep(&acc_empty[s], ((Tp / NS) - 1) & 1, a.sc, 256);
                     if (!__all_sync(kFull, w2)) { ok = false; break; }
                     tc::fence_after_sync();
-                    uint32_t r[16];
-                    asm volatile(
-                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-                          "=r"(r[14]), "=r"(r[15])
-                        : "r"(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(b * N))
-                        : "memory");
-                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-                    tc::fence_before_sync();
-                    __syncwarp();
-                    if (lane == 0) tc::mbar_arrive(&tmem_empty[b]);
-                    float* ct = sC + (size_t)cb * N * M;
-                    const int c0 = tt * N;
+                    if (lane == 0) {
+                        const uint32_t bad = tc::smem_u32(sm + OFF_B + st * TILE_BYTES);
 #pragma unroll
-                    for (int c = 0; c < N; ++c) {
-                        const float4 ci = __ldg(crec + min(c0 + c, m - 1));  // (t', delB, |b|^2, 0)
-                        const float d2 = fmaf(-2.f, __uint_as_float(r[c]), na + ci.z);
-                        const float dd = Arith<float>::root(fmaxf(d2, 0.f));
-                        ct[c * M + 32 * q + lane] = fmaf(a.nu, fabsf(ti - ci.x), dd);
+                        for (int r = 0; r < RT; ++r) {
+#pragma unroll
+                            for (int ks = 0; ks < D / 8; ++ks) {
+                                // K step ks covers k-groups 2ks, 2ks+1 (boxes 256 bytes apart);
+                                // points 8..15 of the tile sit 128 bytes after points 0..7
+                                const uint64_t bd = tc::smem_desc(bad + ks * 2 * (N * 16), N * 16, 128);
+                                tc::mma_tf32_tmem_a(tmem + (uint32_t)(ACC_COL + s * (RT * N) + r * N),
+                                                    tmem + (uint32_t)(r * D + ks * 8), bd, idesc, ks > 0);
+                            }
+                        }
+                        tc::mma_commit(&acc_full[s]);
+                        tc::mma_commit(&b_empty[st]);
                     }
-                    // the tile's column delete costs, next to its costs: the
-                    // wavefront step then reads only shared memory
-                    if (q == 0 && lane < N) sDel[cb * N + lane] = __ldg(crec + min(c0 + lane, m - 1)).y;
                     __syncwarp();
-                    if (lane == 0) tc::mbar_arrive(&cost_full[cb]);
+                    ++Tp;
+                    if (t == ntiles - 1) ++sweep_p;
                 }
             }
         } else {
-            // ================= wavefront (warp 5)
-            // Steps run in blocks of N (= one cost tile of lane 0's columns):
-            // the tile wait and release happen once per block, so the steps in
-            // between are one stretch of code without branches.
-            static_assert((NC * N & (NC * N - 1)) == 0, "the cost ring index wraps with a mask");
-            for (int st = 0; st < nstrips && ok; ++st) {
-                const int r0 = st * M + 1;  // 1-based first row of the strip
-                const int rows = min(M, n - st * M);
-                const int lanes_used = (rows + R - 1) / R;
-                const bool first = (st == 0), last = (st == nstrips - 1);
-                float rdel[R], Dl[R], cp[R];
+            const int q = warp;
+            const uint32_t tlane = (uint32_t)(32 * q) << 16;
+            float* ring = reinterpret_cast<float*>(sm + OFF_RING + q * RING_WARP);
+            float* myring = ring + lane * RS;
+            float* ctime = reinterpret_cast<float*>(sm + OFF_CTIME) + q * CRING;
+            float* cnorm = reinterpret_cast<float*>(sm + OFF_CNORM) + q * CRING;
+            float* delb_r = reinterpret_cast<float*>(sm + OFF_DELB) + q * DMIR;
+            float2* bnd_r = reinterpret_cast<float2*>(sm + OFF_BND) + q * 64;
+            float2* bnd_g = a.bnd + (int64_t)(blockIdx.x * CW + q) * a.bnd_stride + BND_PAD;
+            const float4* rec_y = a.rec_b + it.yb;
+            const float nu = a.nu;
+            while (ok && sched_begin(sch, a, it)) {
+                int64_t pos = -1;
+                int kq = 0, remq = 0;
 #pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    const int i = r0 + lane * R + r;
-                    rdel[r] = __ldg(rrec + ((i <= n ? i : n) - 1)).y;
-                    Dl[r] = INF;
-                    cp[r] = 0.f;
+                for (int w = 0; w < CW; ++w) {
+                    if (w == q) {
+                        pos = sch.pos[w];
+                        kq = sch.k[w];
+                        remq = sch.rem[w];
+                    }
                 }
-                float diagD = (first && lane == 0) ? 0.f : INF, diagC = 0.f;
+                const bool idle = pos < 0;
+                const int64_t x = a.perm_a[idle ? it.r_lo : pos];
+                const int64_t xa = a.offs_a[x];
+                const int n = (int)(a.offs_a[x + 1] - xa);
+                const int r0 = STRIP * kq + 1;
+                const bool first = idle || kq == 0;
+                const bool last = !idle && remq == 1;
+                const int i0 = min(r0 + 2 * lane, n), i1 = min(r0 + 2 * lane + 1, n);
+                const float4 ra0 = __ldg(a.rec_a + xa + i0 - 1);
+                const float4 ra1 = __ldg(a.rec_a + xa + i1 - 1);
+                // ---- this strip's rows into the A tiles (every MMA of the previous
+                // sweep has completed: this warp read all of its accumulators)
+                if (!idle) {
+#pragma unroll
+                    for (int r = 0; r < RT; ++r) {
+                        const float4* src = reinterpret_cast<const float4*>(a.vals_a + (xa + (r ? i1 : i0) - 1) * D);
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            float v[32];
+#pragma unroll
+                            for (int u = 0; u < 8; ++u) {
+                                const float4 f = __ldg(src + h * 8 + u);
+                                v[4 * u] = f.x;
+                                v[4 * u + 1] = f.y;
+                                v[4 * u + 2] = f.z;
+                                v[4 * u + 3] = f.w;
+                            }
+                            tc::tmem_st32(tmem + tlane + (uint32_t)(r * D + 32 * h), v);
+                        }
+                    }
+                    tc::tmem_wait_st();
+                }
+                tc::fence_before_sync();
+                __syncwarp();
+                if (lane == 0) tc::mbar_arrive(a_ready);
+                // the TMA warp keeps the B loads four tiles ahead of its own use; the
+                // MMA warp, once every warp's rows are in, issues tiles 0..2
+
+                // ---- rings.  Cost ring: columns <= 0 cost +inf (slots 32..63).  Column
+                // delete costs: 0 for columns <= 0 (slots 96..127).
+#pragma unroll
+                for (int u = 0; u < RING / 2; u += 2) st_shared_v4(myring + 2 * (RING / 2 + u), INF, INF, INF, INF);
+                delb_r[CRING - 32 + lane] = 0.f;
+                // column record of column j (1-based) of y: (t', dB, |b|^2, 0); past m the
+                // norm is +inf (cost +inf) and the delete cost 0, which freezes the rows
+                auto colrec = [&](int j) -> float4 {
+                    float4 v = __ldg(rec_y + (min(j, m) - 1));  // j >= 1
+                    const bool in = j <= m;
+                    v.x = in ? v.x : 0.f;
+                    v.y = in ? v.y : 0.f;
+                    v.z = in ? v.z : INF;
+                    return v;
+                };
+                // the row above the strip at column j (1-based): (inf, 0) above a
+                // series' first strip and past m
+                auto rowabove = [&](int j) -> float2 {
+                    const float2 v = __ldcg(bnd_g + min(j, m));
+                    return (first || j > m) ? make_float2(INF, 0.f) : v;
+                };
+                // tile 0's records (lanes 16..31 write the same values again), then the
+                // staged inputs of the first two blocks: records of tiles 1 and 2, the
+                // row above for steps 0..31
+                {
+                    const float4 c0 = colrec((lane & (N - 1)) + 1);
+                    ctime[lane & (N - 1)] = c0.x;
+                    cnorm[lane & (N - 1)] = c0.z;
+                    delb_r[lane & (N - 1)] = c0.y;
+                    delb_r[CRING + (lane & (N - 1))] = c0.y;  // mirror
+                }
+                float4 cr_st = colrec(N + 1 + lane);
+                float2 bd_st = rowabove(1 + lane);
+                __syncwarp();
+                // ---- costs of tile 0
+                const float na0 = ra0.z, na1 = ra1.z, ti0 = ra0.x, ti1 = ra1.x;
+                const float rdel0 = ra0.y, rdel1 = ra1.y;
+                float X0[N], X1[N];
+                {
+                    const int s = (int)(Tc % NS);
+                    const bool w2 = xwait(&acc_full[s], (Tc / NS) & 1, a.sc);
+                    if (!__all_sync(kFull, w2)) { ok = false; break; }
+                    tc::fence_after_sync();
+                    tc::tmem_ld16x2(tmem + tlane + (uint32_t)(ACC_COL + s * (RT * N)),
+                                    tmem + tlane + (uint32_t)(ACC_COL + s * (RT * N) + N), X0, X1);
+                    tc::fence_before_sync();
+                    __syncwarp();
+                    if (lane == 0) tc::mbar_arrive(&acc_empty[s]);
+                    ++Tc;
+                }
+                // c(i, j) = sqrt(max(|a_i|^2 + |b_j|^2 - 2 X, 0)) + nu |t_i - t'_j|
+                auto cost = [&](float x, float na, float ti, float nb, float tj) -> float {
+                    const float d2 = fmaf(-2.f, x, na + nb);
+                    return fmaf(nu, fabsf(ti - tj), Arith<float>::root(fmaxf(d2, 0.f)));
+                };
+                // the costs of 4 columns (u0 .. u0+3 of a tile) into the cost ring at
+                // `dst`, and also at `dst` + the mirror offset when `mirror`
+                auto cost4 = [&](int u0, const float4& tj, const float4& nb, float* dst, bool mirror) {
+                    const float e0 = cost(X0[u0], na0, ti0, nb.x, tj.x), e1 = cost(X1[u0], na1, ti1, nb.x, tj.x);
+                    const float e2 = cost(X0[u0 + 1], na0, ti0, nb.y, tj.y), e3 = cost(X1[u0 + 1], na1, ti1, nb.y, tj.y);
+                    const float e4 = cost(X0[u0 + 2], na0, ti0, nb.z, tj.z), e5 = cost(X1[u0 + 2], na1, ti1, nb.z, tj.z);
+                    const float e6 = cost(X0[u0 + 3], na0, ti0, nb.w, tj.w), e7 = cost(X1[u0 + 3], na1, ti1, nb.w, tj.w);
+                    st_shared_v4(dst, e0, e1, e2, e3);
+                    st_shared_v4(dst + 4, e4, e5, e6, e7);
+                    if (mirror) {
+                        st_shared_v4(dst + 2 * RING, e0, e1, e2, e3);
+                        st_shared_v4(dst + 2 * RING + 4, e4, e5, e6, e7);
+                    }
+                };
+#pragma unroll
+                for (int u = 0; u < N; u += 4)  // tile 0 sits in slots 0..N-1: mirrored
+                    cost4(u, *reinterpret_cast<const float4*>(ctime + u), *reinterpret_cast<const float4*>(cnorm + u),
+                          myring + 2 * u, true);
+                __syncwarp();
+
+                // ---- the wavefront: lane L on column s - L + 1 at step s
+                float Dl0 = INF, Dl1 = INF, cp0 = 0.f;
+                float diagD = (r0 == 1 && lane == 0) ? 0.f : INF, diagC = 0.f;
                 float botD = INF, botC = 0.f;
-                const long long t0 = t_dp;
-                const int cb0 = (int)(t0 % NC);  // ring slot of this strip's tile 0
-                int released = 0;                // tiles of this strip handed back
-                const int steps = m + lanes_used - 1;
-                // column jc (1-based) of this strip sits in ring column
-                // (cb0 * N + jc - 1) mod (NC * N): tiles are consecutive slots
-                const int gbase = cb0 * N;
-                float4 c4n = make_float4(0.f, 0.f, 0.f, 0.f);
-                float delbn = 0.f;
-                float2 bndn = make_float2(0.f, 0.f);
-                auto prefetch = [&](int jn) {
-                    const int jc = jn < 1 ? 1 : (jn > m ? m : jn);
-                    const int g = (gbase + jc - 1) & (NC * N - 1);
-                    c4n = *reinterpret_cast<const float4*>(sC + (size_t)g * M + lane * R);
-                    delbn = sDel[g];
-                    bndn = sRow[jc - 1];
-                };
-                // one step: lane L on column j = s - L + 1; the next column's
-                // costs, delete cost and boundary entry are fetched during it
-                auto step = [&](int j) {
-                    const float4 c4 = c4n;
-                    const float delb = delbn;
-                    const float2 bnd = bndn;
-                    prefetch(j + 1);
-                    float upD = __shfl_up_sync(kFull, botD, 1);
-                    float upC = __shfl_up_sync(kFull, botC, 1);
-                    // a lane before column 1 sees an infinite row above and keeps its state
-                    // lane 0 reads the row above the strip (for the pair's first
-                    // strip: D(0, j) = inf, c(0, j) = 0).  A lane before column 1
-                    // receives inf from the lane above, so its update keeps every
-                    // value infinite: no test of j is needed.
-                    upD = lane == 0 ? bnd.x : upD;
-                    upC = lane == 0 ? bnd.y : upC;
-                    const float cc[R] = {c4.x, c4.y, c4.z, c4.w};
-                    float tb_[R], tm_[R];
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        const float dg = r == 0 ? diagD : Dl[r - 1];
-                        const float cd = r == 0 ? diagC : cp[r - 1];
-                        tb_[r] = Dl[r] + delb;
-                        tm_[r] = (dg + cc[r]) + cd;
-                    }
-                    float d_up = upD;
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        d_up = min3f(d_up + rdel[r], tb_[r], tm_[r]);
-                        Dl[r] = d_up;
-                        cp[r] = cc[r];
-                    }
-                    diagD = upD;
-                    diagC = upC;
-                    botD = Dl[R - 1];
-                    botC = cp[R - 1];
-                    // lane 31 hands its bottom row to the next strip; columns
-                    // outside 1..m go to the spare entry (no branch)
-                    if (lane == 31) sRow[(j >= 1 && j <= m) ? j - 1 : MAXCOL] = make_float2(botD, botC);
-                };
-                // at step s = N k - 1 lane 0's next prefetch enters tile k, and
-                // lane 31 has read tile k - 3 for the last time
-                auto boundary = [&](int s) -> bool {
-                    const int k = (s + 1) / N;
-                    if (k < ntiles) {
-                        const long long tt = t0 + k;
-                        const bool w2 = xwait(&cost_full[(cb0 + k) % NC], (uint32_t)((tt / NC) & 1), a.sc);
-                        if (!__all_sync(kFull, w2)) return false;
-                    }
-                    const int kr = k - 3;
-                    if (kr >= 0 && kr == released && kr < ntiles) {
+                const int nblk = (m + 31 + N - 1) / N;
+                const int is31 = lane == 31;
+                for (int b = 0; b < nblk; ++b) {
+                    const int sb = N * b;
+                    if ((b & 1) == 0) {
+                        // every 32 steps, all lanes: the staged records of tiles b+1,
+                        // b+2 (columns 16b+17 ..) and the row above for steps sb ..
+                        // sb+31 go to shared memory; then those of the next 32 steps
+                        // are loaded (used 32 steps later)
+                        const int slot = (N * (b + 1) + lane) & (CRING - 1);
+                        ctime[slot] = cr_st.x;
+                        cnorm[slot] = cr_st.z;
+                        delb_r[slot] = cr_st.y;
+                        if (slot < N) delb_r[CRING + slot] = cr_st.y;  // mirror
+                        bnd_r[(sb + lane) & 63] = bd_st;
                         __syncwarp();
-                        if (lane == 0) tc::mbar_arrive(&cost_empty[(cb0 + kr) % NC]);
-                        ++released;
+                        cr_st = colrec(N * (b + 3) + 1 + lane);
+                        bd_st = rowabove(sb + 32 + 1 + lane);
                     }
-                    return true;
-                };
-                if (first) {  // the row above the pair: D(0, j) = inf, c(0, j) = 0
-                    for (int c = lane; c < m; c += 32) sRow[c] = make_float2(INF, 0.f);
+                    // accumulators of tile b+1: the load is issued here and waited for
+                    // three steps later, just before the costs first use them
+                    const bool xload = b + 1 < ntiles;
+                    const int xs = (int)(Tc % NS);
+                    if (xload) {
+                        const bool w2 = xwait(&acc_full[xs], (Tc / NS) & 1, a.sc);
+                        if (!__all_sync(kFull, w2)) { ok = false; break; }
+                        tc::fence_after_sync();
+                        tc::tmem_ld16x2_async(tmem + tlane + (uint32_t)(ACC_COL + xs * (RT * N)),
+                                              tmem + tlane + (uint32_t)(ACC_COL + xs * (RT * N) + N), X0, X1);
+                        ++Tc;
+                    }
+                    const int cslot = (N * (b + 1)) & (RING - 1);  // cost-ring slot of tile b+1's first column
+                    const int rslot = (N * (b + 1)) & (CRING - 1);  // record-ring slot of the same column
+                    float* cst = myring + 2 * cslot;
+                    // lane 31's bottom row at column s - 30 (the other lanes' addresses are
+                    // never stored to)
+                    float2* bst = bnd_g + (sb - 30) + (lane - 31);
+                    // this block's reads: slot (s - L) mod the ring for s = sb .. sb+15,
+                    // which the mirrors keep contiguous from the block's first slot
+                    const float2* rp = reinterpret_cast<const float2*>(myring) + ((sb - lane) & (RING - 1));
+                    const float* dp = delb_r + ((sb - lane) & (CRING - 1));
+                    const float2* bp = bnd_r + (sb & 63);
+                    float2 cn = rp[0];
+                    float dbn = dp[0];
+                    float2 bn = bp[0];
+                    auto block = [&](auto MC) {
+                      constexpr bool kMirror = decltype(MC)::value;
+                      unroll_seq(
+                        [&](auto UC) {
+                            constexpr int u = decltype(UC)::value;
+                            const float c0 = cn.x, c1 = cn.y, delb = dbn;
+                            const float2 bnd = bn;
+                            if constexpr (u + 1 < N) {
+                                cn = rp[u + 1];
+                                dbn = dp[u + 1];
+                                bn = bp[u + 1];
+                            }
+                            float upD = __shfl_up_sync(kFull, botD, 1);
+                            float upC = __shfl_up_sync(kFull, botC, 1);
+                            upD = lane == 0 ? bnd.x : upD;
+                            upC = lane == 0 ? bnd.y : upC;
+                            const float tb0 = Dl0 + delb, tm0 = (diagD + c0) + diagC;
+                            const float tb1 = Dl1 + delb, tm1 = (Dl0 + c1) + cp0;
+                            const float D0 = min3f(upD + rdel0, tb0, tm0);
+                            const float D1 = min3f(D0 + rdel1, tb1, tm1);
+                            diagD = upD;
+                            diagC = upC;
+                            cp0 = c0;
+                            Dl0 = D0;
+                            Dl1 = D1;
+                            botD = D1;
+                            botC = c1;
+                            st_global_pred<8 * u>(bst, D1, c1, is31);
+                            if constexpr (u == 2) {
+                                // the accumulators have landed: release the stage
+                                if (xload) {
+                                    tc::tmem_wait_ld_tied(X0, X1);
+                                    tc::fence_before_sync();
+                                    __syncwarp();
+                                    if (lane == 0) tc::mbar_arrive(&acc_empty[xs]);
+                                }
+                            }
+                            // costs of tile b+1, 4 columns every 4 steps (not read in this
+                            // block); cost slots 0..N-1 are mirrored at RING.. for the lanes
+                            // whose window wraps
+                            if constexpr ((u & 3) == 3)
+                                cost4(u - 3, *reinterpret_cast<const float4*>(ctime + rslot + u - 3),
+                                      *reinterpret_cast<const float4*>(cnorm + rslot + u - 3), cst + 2 * (u - 3),
+                                      kMirror);
+                        },
+                        std::make_integer_sequence<int, N>{});
+                    };
+                    if (cslot == 0) block(std::true_type{});
+                    else block(std::false_type{});
                     __syncwarp();
                 }
-                {   // tile 0 must be in before the first prefetch
-                    const bool w2 = xwait(&cost_full[cb0], (uint32_t)((t0 / NC) & 1), a.sc);
-                    if (!__all_sync(kFull, w2)) ok = false;
-                }
-                if (ok) {
-                    prefetch(1 - lane);
-                    int s = 0;
-                    const int head = min(steps, N - 1);
-                    for (; s < head; ++s) step(s - lane + 1);
-                    while (ok && s + N <= steps) {
-                        if (!boundary(s)) { ok = false; break; }
-#pragma unroll
-                        for (int u = 0; u < N; ++u) step(s + u - lane + 1);
-                        s += N;
-                    }
-                    if (ok && s < steps) {
-                        if (!boundary(s)) ok = false;
-                        for (; ok && s < steps; ++s) step(s - lane + 1);
-                    }
-                }
-                // hand back the tiles not yet released
-                __syncwarp();
-                for (int k = released; k < ntiles; ++k)
-                    if (lane == 0) tc::mbar_arrive(&cost_empty[(cb0 + k) % NC]);
-                // the lane holding row n ends its last step on column m, so
-                // its final state holds D(n, m)
-                if (ok && last && lane == lanes_used - 1) {
-                    const int rr = n - r0 - lane * R;
-#pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        if (r == rr) {
-                            *o1 = Dl[r];
-                            if (o2) *o2 = Dl[r];
+                if (!ok) break;
+                // every lane ran past column m with frozen rows: Dl = D(row, m)
+                if (last) {
+                    const int rr = n - r0;  // 0 .. 63
+                    if (lane == (rr >> 1)) {
+                        const float v = (rr & 1) ? Dl1 : Dl0;
+                        if (!a.symmetric) {
+                            a.out[x * a.nb + it.y] = v;
+                        } else {
+                            a.out[x * a.na + it.y] = v;
+                            a.out[it.y * a.na + x] = v;
                         }
                     }
                 }
-                t_dp = t0 + ntiles;
+                sched_end(sch);
             }
         }
-        // a failed role stops the block at the next pair boundary
-        if (!ok && lane == 0) atomicCAS(a.sc.err, 0u, 4u);
+        if (!ok && lane == 0) {
+            atomicCAS(a.sc.err, 0u, 4u);
+            atomicCAS(a.sc.sticky, 0u, 4u);
+        }
     }
-    // drain: the producer's last MMAs must finish before TMEM is freed
-    // (bounded by the same timeout as every other wait)
-    (void)s_epi;
-    if (warp == 0 && t_prod > 0) {
+    // drain (bounded): B loads and MMAs in flight must land before the shared
+    // memory and the TMEM are released.  Only the last NBS loads (one per
+    // stage) and the last MMA group can still be pending.
+    if (warp == TMA_WARP) {
         const unsigned long long t0 = globaltimer();
-        while (!tc::mbar_try_wait(&mma_done[(t_prod - 1) % NB], (uint32_t)(((t_prod - 1) / NB) & 1)) &&
+        for (long long l = (Lp > NBS ? Lp - NBS : 0); l < Lp; ++l)
+            while (!tc::mbar_try_wait(&b_full[l % NBS], (uint32_t)((l / NBS) & 1)) &&
+                   globaltimer() - t0 < a.sc.timeout_ns) {
+            }
+    }
+    if (warp == MMA_WARP && Tp > 0) {
+        const unsigned long long t0 = globaltimer();
+        while (!tc::mbar_try_wait(&acc_full[(Tp - 1) % NS], (uint32_t)(((Tp - 1) / NS) & 1)) &&
                globaltimer() - t0 < a.sc.timeout_ns) {
         }
     }
@@ -497,22 +664,45 @@ cudaError_t launch_xrecords(const RecordsArgs<float>& a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-// Opt in to the shared memory the kernel needs and ask for the largest
-// shared-memory carve-out, so that three blocks fit on one SM.
 static cudaError_t xterm_attributes() {
-    cudaError_t e = cudaFuncSetAttribute(xterm_pairs_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, x64::SMEM);
+    cudaError_t e = cudaFuncSetAttribute(xterm_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, x64::SMEM);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(xterm_pairs_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+        e = cudaFuncSetAttribute(xterm_sweep_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  cudaSharedmemCarveoutMaxShared);
     return e;
 }
 
-cudaError_t launch_xterm_pairs(const PairsArgs<float>& a, int blocks, cudaStream_t st) {
-    if (a.npairs <= 0) return cudaSuccess;
+// Tensor map of a set's 64-dimensional values for the B tiles: [total][64]
+// FP32, rows 256 bytes apart; a box is 4 values (16 bytes) of 16 points, so
+// one tile is 16 boxes at x = 0, 4, .., 60.  Points past the end read 0.
+cudaError_t xterm_tensor_map(void* tmap, const float* vals, int64_t total) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult q;
+        void* fn = nullptr;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                         cudaEnableDefault, &q);
+        if (e != cudaSuccess) return e;
+        if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const cuuint64_t dims[2] = {(cuuint64_t)x64::D, (cuuint64_t)total};
+    const cuuint64_t strides[1] = {(cuuint64_t)x64::D * sizeof(float)};
+    const cuuint32_t box[2] = {4, (cuuint32_t)x64::N};
+    const cuuint32_t estr[2] = {1, 1};
+    CUresult r = encode(reinterpret_cast<CUtensorMap*>(tmap), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                        const_cast<float*>(vals), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t launch_xterm(const void* tmap, const XtermArgs& a, int blocks, cudaStream_t st) {
+    if (a.nitems <= 0) return cudaSuccess;
     cudaError_t e = xterm_attributes();
     if (e != cudaSuccess) return e;
     (void)cudaGetLastError();
-    xterm_pairs_kernel<<<blocks, x64::THREADS, x64::SMEM, st>>>(a);
+    xterm_sweep_kernel<<<blocks, x64::THREADS, x64::SMEM, st>>>(*reinterpret_cast<const CUtensorMap*>(tmap), a);
     return cudaGetLastError();
 }
 
@@ -520,7 +710,7 @@ int xterm_blocks_per_sm() {
     cudaError_t e = xterm_attributes();
     int nb = 0;
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, xterm_pairs_kernel, x64::THREADS, x64::SMEM);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, xterm_sweep_kernel, x64::THREADS, x64::SMEM);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         return -(int)e;  // negative: the CUDA error code, for diagnostics
@@ -528,14 +718,12 @@ int xterm_blocks_per_sm() {
     return nb;
 }
 
-int xterm_max_cols() { return x64::MAXCOL; }
-
 // Blocks per SM allowed by shared memory (1 KB reserved per block), tensor
 // memory columns and registers.
 int xterm_resident_blocks() {
     cudaFuncAttributes fa{};
     int dev = 0, smem_sm = 0, regs_sm = 0;
-    if (xterm_attributes() != cudaSuccess || cudaFuncGetAttributes(&fa, xterm_pairs_kernel) != cudaSuccess ||
+    if (xterm_attributes() != cudaSuccess || cudaFuncGetAttributes(&fa, xterm_sweep_kernel) != cudaSuccess ||
         cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess) {
@@ -556,7 +744,7 @@ void xterm_resources(char* buf, int len) {
     cudaFuncAttributes fa{};
     int dev = 0, smem_sm = 0, smem_blk = 0;
     (void)xterm_attributes();
-    cudaFuncGetAttributes(&fa, xterm_pairs_kernel);
+    cudaFuncGetAttributes(&fa, xterm_sweep_kernel);
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     cudaDeviceGetAttribute(&smem_blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
@@ -564,5 +752,10 @@ void xterm_resources(char* buf, int len) {
     snprintf(buf, len, "regs %d static %zu dyn %d max_dyn %d smem/SM %d smem/block %d", fa.numRegs,
              fa.sharedSizeBytes, x64::SMEM, fa.maxDynamicSharedSizeBytes, smem_sm, smem_blk);
 }
+
+int xterm_rows_per_item() { return x64::CH; }
+int xterm_warps_per_block() { return x64::CW; }
+int xterm_threads() { return x64::THREADS; }
+int64_t xterm_bnd_stride(int64_t max_len) { return max_len + 64 + x64::BND_PAD; }
 
 }  // namespace twed

@@ -36,7 +36,7 @@ EXPORTS = (
     "twed_batch_f64", "twed_batch_f32", "twed_batch_f64_ex", "twed_batch_f32_ex",
     "twed_batch_f32_noalloc",
     "twed_allpairs_plan_create_f64", "twed_allpairs_plan_create_f32", "twed_plan_execute",
-    "twed_plan_cells", "twed_plan_pairs", "twed_plan_kernel_ms", "twed_plan_describe",
+    "twed_plan_cells", "twed_plan_pairs", "twed_plan_kernel_ms", "twed_plan_describe", "twed_plan_status",
     "twed_plan_destroy",
     "twed_allpairs_host_f32",
     "twed_knn_config_default", "twed_knn_create", "twed_knn_train", "twed_knn_search",
@@ -115,6 +115,7 @@ def load(path: str | None = None):
             "twed_plan_cells": (i64, [P]),
             "twed_plan_pairs": (i64, [P]),
             "twed_plan_kernel_ms": (ci, [P, P]),
+            "twed_plan_status": (ci, [P, P]),
             "twed_plan_describe": (ctypes.c_char_p, [P]),
             "twed_plan_destroy": (None, [P]),
             "twed_allpairs_host_f32": (ci, [P, P, P, P, i64, P, P, P, i64, ci, f, f, ci, P]),
@@ -398,6 +399,11 @@ class Plan:
 
     def describe(self) -> str:
         return self.handle.lib.twed_plan_describe(self.plan).decode()
+
+    def status(self, stream=None):
+        """Wait for `stream`; raise TwedError if a kernel of this plan failed
+        (a bounded wait expired) since the last call."""
+        self.handle.check(self.handle.lib.twed_plan_status(self.plan, _stream_ptr(stream)))
 
     def new_output(self):
         import torch

@@ -4,8 +4,11 @@ The cell cost uses |a_i - b_j|^2 = |a_i|^2 + |b_j|^2 - 2 a_i . b_j with the
 dot products on the tensor cores.  TF32 keeps 10 mantissa bits of each
 input, so every cost carries about 1e-4 relative error; the test bounds the
 TWED error at 2e-3 relative and checks that the CUDA-core FP32 path on the
-same inputs stays within the 1e-5 FP32 bound.  Lengths straddle the 128-row
-strips and 16-column tiles (1, 15, 16, 17, 127, 128, 129, ...).
+same inputs stays within the 1e-5 FP32 bound.  Lengths straddle the 64-row
+strips (two rows per lane) and the 16-column tiles (1, 15, 16, 17, 63, 64,
+65, 127, 128, 129, ...); further cases cover more row series than one work
+item holds (64), the symmetric plan's per-chunk items, and column series
+longer than 1024 points (the boundary rows stream through global memory).
 """
 import numpy as np
 import pytest
@@ -15,7 +18,7 @@ from paper_2007_16135_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 
-LENGTHS_A = [1, 15, 16, 17, 127, 128, 129, 300, 257, 64]
+LENGTHS_A = [1, 15, 16, 17, 63, 64, 65, 127, 128, 129, 300, 257]
 LENGTHS_B = [1, 16, 33, 128, 200, 255, 256, 513]
 
 
@@ -45,8 +48,7 @@ def matrix(tw, SA, SB, xterm, nu=1.0, lam=1.0):
     B = tw.DeviceSet.from_numpy(SB.vals, SB.ts, SB.offs, torch.float32) if SB is not None else None
     plan = tw.Plan(A, B, nu, lam, 2, opts=tw.make_opts(xterm=xterm))
     M = plan.execute().cpu().numpy()
-    torch.cuda.synchronize()
-    tw.default_handle().sync_status()
+    plan.status()
     return M, plan.describe()
 
 
@@ -97,8 +99,7 @@ def test_w4_full_size_sampled(tw):
     B = tw.DeviceSet.from_numpy(SB.vals, SB.ts, SB.offs, torch.float32)
     plan = tw.Plan(A, B, 1.0, 1.0, 2, opts=tw.make_opts(xterm=tw.XTERM_TF32))
     M = plan.execute()
-    torch.cuda.synchronize()
-    tw.default_handle().sync_status()
+    plan.status()
     pairs = W.sample_block_pairs(SA.n, SB.n, 64, 4)
     got = M[torch.as_tensor(pairs[:, 0]).cuda(), torch.as_tensor(pairs[:, 1]).cuda()].cpu().numpy()
     A64, B64 = SA.astype(np.float64), SB.astype(np.float64)
@@ -106,3 +107,45 @@ def test_w4_full_size_sampled(tw):
     rel = np.abs(got - ref) / ref
     print(f"w4 full size, 64 sampled pairs: max rel err {rel.max():.3e}")
     assert rel.max() <= 2e-3
+
+
+def test_tensor_core_many_rows_long_columns(tw):
+    # 150 row series (three work items per column series, uneven strip
+    # counts per consumer warp) against columns of 1 .. 2100 points
+    rng = np.random.default_rng(11)
+    SA = smoothed_set(5, [int(v) for v in rng.integers(1, 200, 150)])
+    SB = smoothed_set(6, [1, 17, 1100, 2100, 64, 1025])
+    ref = oracle_block(SA, SB)
+    Mx, _ = matrix(tw, SA, SB, tw.XTERM_TF32)
+    rel = np.abs(Mx - ref) / ref
+    print(f"many rows, long columns: max rel err {rel.max():.3e}")
+    assert np.all(np.isfinite(Mx)) and rel.max() <= 2e-3
+
+
+def test_tensor_core_symmetric_several_chunks(tw):
+    # 140 series: three chunks of rows, including the items on the diagonal
+    # of the triangle whose rows are only part of a chunk
+    rng = np.random.default_rng(12)
+    S = smoothed_set(7, [int(v) for v in rng.integers(1, 160, 140)])
+    Mx, _ = matrix(tw, S, None, tw.XTERM_TF32)
+    ref = oracle_block(S, S)
+    iu = np.triu_indices(S.n, 1)
+    rel = np.abs(Mx[iu] - ref[iu]) / ref[iu]
+    print(f"symmetric, 140 series: max rel err {rel.max():.3e}")
+    assert rel.max() <= 2e-3
+    assert np.array_equal(Mx, Mx.T) and np.all(np.diag(Mx) == 0)
+
+
+def test_tensor_core_reexecute_is_stable(tw):
+    # the kernel keeps no state between executes: the same plan twice gives
+    # the same matrix bit for bit
+    import torch
+    SA, SB = smoothed_set(8, [90, 33, 200]), smoothed_set(9, [70, 5, 400])
+    A = tw.DeviceSet.from_numpy(SA.vals, SA.ts, SA.offs, torch.float32)
+    B = tw.DeviceSet.from_numpy(SB.vals, SB.ts, SB.offs, torch.float32)
+    plan = tw.Plan(A, B, 1.0, 1.0, 2, opts=tw.make_opts(xterm=tw.XTERM_TF32))
+    M1 = plan.execute().cpu().numpy()
+    plan.status()
+    M2 = plan.execute().cpu().numpy()
+    plan.status()
+    assert np.array_equal(M1, M2)
