@@ -231,6 +231,91 @@ twed_status_t twed_batch_f32_noalloc(const twed_set_f32_t* A, const twed_set_f32
                                      const int64_t* d_pairs, int64_t npairs, int dim, float nu,
                                      float lambda, int p, float* d_out, void* stream);
 
+/* ---- edit paths ----------------------------------------------------------
+ * The alignment behind a TWED value, which the paper's introduction names
+ * as readily obtainable from the same dynamic program (and its conclusion
+ * as an extension).  A path is the list of moves after the forced first
+ * match (0,0) -> (1,1): 0 = match (i+1, j+1), 1 = delete in a (i+1, j),
+ * 2 = delete in b (i, j+1), ending at (la, lb).  Among optimal paths the one
+ * returned is fixed by a walk back from (la, lb) that takes, at each cell,
+ * the first of match, delete in a, delete in b whose candidate equals
+ * D(i,j) (the forward pass records that choice per cell: 2 bits, la*lb/4
+ * bytes of device memory per pair in flight, at most 8 GiB in all; a pair
+ * needing more returns TWED_ERR_UNSUPPORTED).  The distance itself is the
+ * same as twed_f64 / twed_f32 computes (FP64: bit for bit for p = 1, 2).
+ *
+ * twed_path_*: one pair, host pointers, blocking; moves (host) needs room
+ * for max(la + lb - 2, 1) entries; *len receives their number and *out
+ * TWED(a, b).  It runs on one warp (about la*lb / 1e8 seconds in FP64). */
+twed_status_t twed_path_f64(twed_handle_t handle, const double* a, const double* ta, int64_t la,
+                            const double* b, const double* tb, int64_t lb, int dim, double nu,
+                            double lambda, int p, double* out, int8_t* moves, int64_t* len);
+twed_status_t twed_path_f32(twed_handle_t handle, const float* a, const float* ta, int64_t la,
+                            const float* b, const float* tb, int64_t lb, int dim, float nu,
+                            float lambda, int p, float* out, int8_t* moves, int64_t* len);
+/* Explicit pairs of two packed sets (device pointers, enqueued on `stream`):
+ * pair k's distance goes to d_dist[k], its moves to d_moves[d_move_offs[k]
+ * ..] (room for len_a + len_b - 2 entries, caller-allocated) and their
+ * number to d_len[k].  A pair index outside its set gives NaN, d_len[k] = -1
+ * and TWED_ERR_INVALID_ARG through twed_sync_status. */
+twed_status_t twed_path_batch_f64(twed_handle_t handle, const twed_set_f64_t* A,
+                                  const twed_set_f64_t* B, const int64_t* d_pairs, int64_t npairs,
+                                  int dim, double nu, double lambda, int p, double* d_dist,
+                                  int8_t* d_moves, const int64_t* d_move_offs, int64_t* d_len,
+                                  void* stream);
+twed_status_t twed_path_batch_f32(twed_handle_t handle, const twed_set_f32_t* A,
+                                  const twed_set_f32_t* B, const int64_t* d_pairs, int64_t npairs,
+                                  int dim, float nu, float lambda, int p, float* d_dist,
+                                  int8_t* d_moves, const int64_t* d_move_offs, int64_t* d_len,
+                                  void* stream);
+
+/* ---- LCS and DTW on the same wavefront ------------------------------------
+ * The paper's section "Generalized Dynamic Programming Extensions" carries
+ * its diagonal band over to other dynamic programs, first the longest common
+ * subsequence ("Direct Extension: LCS"):
+ *   L(i,0) = L(0,j) = 0;  L(i,j) = L(i-1,j-1) + 1 if x_i == y_j,
+ *                                 max(L(i-1,j), L(i,j-1)) otherwise,
+ * and dynamic time warping, the related distance of its introduction:
+ *   D(0,0) = 0, D(i,0) = D(0,j) = inf,
+ *   D(i,j) = d(a_i,b_j) + min(min(D(i-1,j-1), D(i-1,j)), D(i,j-1)),
+ * with the lp point distance d of TWED (no warping window).  Integer LCS
+ * results are exact; FP64 DTW follows that evaluation order (bit for bit
+ * against a sequential evaluation for p = 1, 2).
+ *
+ * A packed set of int32 symbol sequences: sym[offs[n]], offs[n+1] (device,
+ * int64, offs[0] = 0), offs_host a host copy; sequences may be empty. */
+typedef struct {
+    const int32_t* sym;
+    const int64_t* offs;
+    const int64_t* offs_host;
+    int64_t n;
+} twed_seq_t;
+/* LCS lengths of explicit pairs (device, enqueued on `stream`): d_len[k] =
+ * LCS(X[d_pairs[2k]], Y[d_pairs[2k+1]]); an index outside its set gives -1
+ * and TWED_ERR_INVALID_ARG through twed_sync_status. */
+twed_status_t twed_lcs_batch(twed_handle_t handle, const twed_seq_t* X, const twed_seq_t* Y,
+                             const int64_t* d_pairs, int64_t npairs, int32_t* d_len, void* stream);
+/* One longest common subsequence of x[n], y[m] (host, blocking): xi[k],
+ * yj[k] (room for min(n, m) entries) receive the matched 0-based positions
+ * in increasing order, *len their number (the LCS length).  The walk back
+ * takes the diagonal on equal symbols, else goes up when L(i-1,j) >=
+ * L(i,j-1), else left.  Choice bits as for edit paths (n*m/4 bytes). */
+twed_status_t twed_lcs_pairs(twed_handle_t handle, const int32_t* x, int64_t n, const int32_t* y,
+                             int64_t m, int64_t* xi, int64_t* yj, int64_t* len);
+/* DTW of explicit pairs over two packed sets (timestamps are not read and
+ * may be NULL); arguments, ownership and errors as twed_batch_*. */
+twed_status_t twed_dtw_batch_f64(twed_handle_t handle, const twed_set_f64_t* A,
+                                 const twed_set_f64_t* B, const int64_t* d_pairs, int64_t npairs,
+                                 int dim, int p, double* d_out, void* stream);
+twed_status_t twed_dtw_batch_f32(twed_handle_t handle, const twed_set_f32_t* A,
+                                 const twed_set_f32_t* B, const int64_t* d_pairs, int64_t npairs,
+                                 int dim, int p, float* d_out, void* stream);
+/* DTW of one pair from host memory (a[la][dim], b[lb][dim]), blocking. */
+twed_status_t twed_dtw_f64(twed_handle_t handle, const double* a, int64_t la, const double* b,
+                           int64_t lb, int dim, int p, double* out);
+twed_status_t twed_dtw_f32(twed_handle_t handle, const float* a, int64_t la, const float* b,
+                           int64_t lb, int dim, int p, float* out);
+
 /* ---- all-pairs distance matrix (plan + CUDA graph) -----------------------
  * The paper's batch mode returning a distance matrix, with its suggested
  * upper-triangle saving for a symmetric matrix (section "Validation using

@@ -15,7 +15,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libtwed.so")
 SOURCES = ["api.cu", "kernels_f32.cu", "kernels_f64.cu", "noalloc.cu", "xterm.cu", "encoder.cu",
-           "knn.cu", "peak.cu", "order.cu"]
+           "knn.cu", "peak.cu", "order.cu", "dp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ARCH + ["-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC",
                   "-diag-suppress", "177"]

@@ -472,6 +472,12 @@ twed_status_t set_error(twed_handle_t h, twed_status_t st, const char* msg) {
     return st;
 }
 int handle_sms(twed_handle_t h) { return h ? h->sms : 0; }
+void* handle_workspace(twed_handle_t h, size_t bytes, twed_status_t* st) {
+    *st = ensure_ws(h, bytes);
+    return *st == TWED_OK ? h->ws : nullptr;
+}
+void* handle_stream(twed_handle_t h) { return h ? (void*)h->stream : nullptr; }
+unsigned* handle_ctl(twed_handle_t h) { return h ? h->ctl : nullptr; }
 int handle_device(twed_handle_t h) { return h ? h->device : 0; }
 }  // namespace detail
 }  // namespace twed

@@ -17,5 +17,12 @@ twed_status_t batch_f32_shaped(twed_handle_t h, const twed_set_f32_t* A, const t
                                int rmax, int per_sm);
 int batch_f32_max_blocks_per_sm(int dim, int p);
 int batch_f32_rmax_limit();
+// The handle's grow-only device workspace, at least `bytes` long (nullptr
+// and the handle's last error set on failure; a growth synchronizes the
+// handle's stream first).
+void* handle_workspace(twed_handle_t h, size_t bytes, twed_status_t* st);
+void* handle_stream(twed_handle_t h);
+// The handle's [live error, sticky error] words (device).
+unsigned* handle_ctl(twed_handle_t h);
 }  // namespace detail
 }  // namespace twed

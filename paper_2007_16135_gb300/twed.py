@@ -45,6 +45,9 @@ EXPORTS = (
     "twed_encoder_param_count", "twed_encoder_stats_f32", "twed_encoder_forward_f32",
     "twed_encoder_loss_grad_f32", "twed_adam_f32", "twed_embed_search_f32", "twed_topk_rows_f32",
     "twed_pipe_peak",
+    "twed_path_f64", "twed_path_f32", "twed_path_batch_f64", "twed_path_batch_f32",
+    "twed_lcs_batch", "twed_lcs_pairs", "twed_dtw_batch_f64", "twed_dtw_batch_f32",
+    "twed_dtw_f64", "twed_dtw_f32",
 )
 
 
@@ -140,6 +143,16 @@ def load(path: str | None = None):
             "twed_embed_search_f32": (ci, [P, P, i64, P, i64, ci, P, P]),
             "twed_topk_rows_f32": (ci, [P, P, i64, i64, i64, ci, P, P, P]),
             "twed_pipe_peak": (ci, [P, ci, P]),
+            "twed_path_f64": (ci, [P, P, P, i64, P, P, i64, ci, d, d, ci, P, P, P]),
+            "twed_path_f32": (ci, [P, P, P, i64, P, P, i64, ci, f, f, ci, P, P, P]),
+            "twed_path_batch_f64": (ci, [P, P, P, P, i64, ci, d, d, ci, P, P, P, P, P]),
+            "twed_path_batch_f32": (ci, [P, P, P, P, i64, ci, f, f, ci, P, P, P, P, P]),
+            "twed_lcs_batch": (ci, [P, P, P, P, i64, P, P]),
+            "twed_lcs_pairs": (ci, [P, P, i64, P, i64, P, P, P]),
+            "twed_dtw_batch_f64": (ci, [P, P, P, P, i64, ci, ci, P, P]),
+            "twed_dtw_batch_f32": (ci, [P, P, P, P, i64, ci, ci, P, P]),
+            "twed_dtw_f64": (ci, [P, P, i64, P, i64, ci, ci, P]),
+            "twed_dtw_f32": (ci, [P, P, i64, P, i64, ci, ci, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -339,6 +352,139 @@ def twed_batch(A: DeviceSet, B: DeviceSet, pairs, nu, lam, p=2, out=None, stream
 
 twed_batch_f64 = twed_batch
 twed_batch_f32 = twed_batch
+
+
+# ---------------------------------------------------------------- edit paths
+MOVE_CHARS = "MAB"  # 0 match, 1 delete in a, 2 delete in b
+
+
+def twed_path(a, ta, b, tb, nu, lam, p=2, dtype="f64", handle: Handle | None = None):
+    """TWED of one pair and an optimal edit path, ``(value, moves)`` with
+    ``moves`` a string over 'M' (match), 'A' (delete in a), 'B' (delete in b),
+    the steps after the forced first match (twed_path_f64 / _f32)."""
+    h = handle or default_handle()
+    npd = np.float64 if dtype == "f64" else np.float32
+    a, ta = _series_np(a, ta, npd)
+    b, tb = _series_np(b, tb, npd)
+    if a.shape[1] != b.shape[1]:
+        raise ValueError("series dimensions differ")
+    moves = np.zeros(max(a.shape[0] + b.shape[0] - 2, 1), dtype=np.int8)
+    out = np.zeros(1, dtype=npd)
+    n = np.zeros(1, dtype=np.int64)
+    fn = h.lib.twed_path_f64 if dtype == "f64" else h.lib.twed_path_f32
+    h.check(fn(h.h, _np_ptr(a), _np_ptr(ta), a.shape[0], _np_ptr(b), _np_ptr(tb), b.shape[0], a.shape[1],
+               float(nu), float(lam), int(p), _np_ptr(out), _np_ptr(moves), _np_ptr(n)))
+    return float(out[0]), "".join(MOVE_CHARS[x] for x in moves[:int(n[0])])
+
+
+def twed_path_batch(A: DeviceSet, B: DeviceSet, pairs, nu, lam, p=2, stream=None,
+                    handle: Handle | None = None):
+    """Distances and edit paths of listed pairs (device int64 [k, 2]):
+    ``(dist [k], moves int8, move_offs [k], lens [k])`` on the device; pair
+    k's moves are ``moves[move_offs[k] : move_offs[k] + lens[k]]``."""
+    import torch
+    h = handle or default_handle()
+    pairs = pairs.contiguous()
+    k = pairs.shape[0]
+    la = torch.as_tensor(np.diff(A.offs_host), device=pairs.device)
+    lb = torch.as_tensor(np.diff(B.offs_host), device=pairs.device)
+    cap = (la[pairs[:, 0]] + lb[pairs[:, 1]] - 2).clamp(min=1)
+    offs = torch.zeros(k, dtype=torch.int64, device=pairs.device)
+    if k > 1:
+        offs[1:] = torch.cumsum(cap, 0)[:-1]
+    moves = torch.zeros(int(cap.sum().item()) if k else 1, dtype=torch.int8, device=pairs.device)
+    dist = torch.empty(k, dtype=A.vals.dtype, device=pairs.device)
+    lens = torch.empty(k, dtype=torch.int64, device=pairs.device)
+    sa, sb = A.cstruct(), B.cstruct()
+    f64 = A.vals.dtype == torch.float64
+    fn = h.lib.twed_path_batch_f64 if f64 else h.lib.twed_path_batch_f32
+    h.check(fn(h.h, ctypes.byref(sa), ctypes.byref(sb), _t_ptr(pairs), k, A.dim, float(nu), float(lam), p,
+               _t_ptr(dist), _t_ptr(moves), _t_ptr(offs), _t_ptr(lens), _stream_ptr(stream)))
+    return dist, moves, offs, lens
+
+
+# ---------------------------------------------------------------- LCS and DTW
+class _Seq(ctypes.Structure):
+    _fields_ = [("sym", ctypes.c_void_p), ("offs", ctypes.c_void_p), ("offs_host", ctypes.c_void_p),
+                ("n", ctypes.c_int64)]
+
+
+@dataclass
+class DeviceSeqs:
+    """Packed int32 symbol sequences on the device (may be empty)."""
+    sym: "object"  # torch int32 [sum_len]
+    offs: "object"  # torch int64 [n + 1]
+    offs_host: np.ndarray
+
+    @classmethod
+    def from_lists(cls, seqs, device="cuda"):
+        import torch
+        lens = [len(x) for x in seqs]
+        offs = np.zeros(len(seqs) + 1, dtype=np.int64)
+        offs[1:] = np.cumsum(lens)
+        flat = np.concatenate([np.asarray(x, dtype=np.int32).ravel() for x in seqs]) if offs[-1] else \
+            np.zeros(1, dtype=np.int32)
+        return cls(torch.as_tensor(flat, device=device), torch.as_tensor(offs, device=device), offs)
+
+    @property
+    def n(self) -> int:
+        return int(self.offs_host.shape[0] - 1)
+
+    def cstruct(self):
+        return _Seq(self.sym.data_ptr(), self.offs.data_ptr(), self.offs_host.ctypes.data, self.n)
+
+
+def lcs_batch(X: DeviceSeqs, Y: DeviceSeqs, pairs, stream=None, handle: Handle | None = None):
+    """LCS lengths of listed pairs (device int64 [k, 2]) -> device int32 [k]."""
+    import torch
+    h = handle or default_handle()
+    pairs = pairs.contiguous()
+    out = torch.empty(pairs.shape[0], dtype=torch.int32, device=pairs.device)
+    sx, sy = X.cstruct(), Y.cstruct()
+    h.check(h.lib.twed_lcs_batch(h.h, ctypes.byref(sx), ctypes.byref(sy), _t_ptr(pairs), pairs.shape[0],
+                                 _t_ptr(out), _stream_ptr(stream)))
+    return out
+
+
+def lcs_pairs(x, y, handle: Handle | None = None):
+    """One longest common subsequence as matched positions ``(xi, yj)``."""
+    h = handle or default_handle()
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.int32).ravel())
+    y = np.ascontiguousarray(np.asarray(y, dtype=np.int32).ravel())
+    k = max(min(x.size, y.size), 1)
+    xi = np.zeros(k, dtype=np.int64)
+    yj = np.zeros(k, dtype=np.int64)
+    n = np.zeros(1, dtype=np.int64)
+    h.check(h.lib.twed_lcs_pairs(h.h, _np_ptr(x) if x.size else None, x.size, _np_ptr(y) if y.size else None,
+                                 y.size, _np_ptr(xi), _np_ptr(yj), _np_ptr(n)))
+    return xi[:int(n[0])].copy(), yj[:int(n[0])].copy()
+
+
+def dtw_batch(A: DeviceSet, B: DeviceSet, pairs, p=2, stream=None, handle: Handle | None = None):
+    """DTW of listed pairs (device int64 [k, 2]) -> device tensor [k]."""
+    import torch
+    h = handle or default_handle()
+    pairs = pairs.contiguous()
+    out = torch.empty(pairs.shape[0], dtype=A.vals.dtype, device=pairs.device)
+    sa, sb = A.cstruct(), B.cstruct()
+    fn = h.lib.twed_dtw_batch_f64 if A.vals.dtype == torch.float64 else h.lib.twed_dtw_batch_f32
+    h.check(fn(h.h, ctypes.byref(sa), ctypes.byref(sb), _t_ptr(pairs), pairs.shape[0], A.dim, int(p),
+               _t_ptr(out), _stream_ptr(stream)))
+    return out
+
+
+def dtw(a, b, p=2, dtype="f64", handle: Handle | None = None) -> float:
+    """DTW of one pair of ``[len, dim]`` host arrays (twed_dtw_f64 / _f32)."""
+    h = handle or default_handle()
+    npd = np.float64 if dtype == "f64" else np.float32
+    a = np.ascontiguousarray(np.asarray(a, dtype=npd))
+    b = np.ascontiguousarray(np.asarray(b, dtype=npd))
+    a = a[:, None] if a.ndim == 1 else a
+    b = b[:, None] if b.ndim == 1 else b
+    out = np.zeros(1, dtype=npd)
+    fn = h.lib.twed_dtw_f64 if dtype == "f64" else h.lib.twed_dtw_f32
+    h.check(fn(h.h, _np_ptr(a), a.shape[0], _np_ptr(b), b.shape[0], a.shape[1], int(p), _np_ptr(out)))
+    return float(out[0])
 
 
 def twed_batch_f32_noalloc(A: DeviceSet, B: DeviceSet, pairs, nu, lam, p=2, out=None,
