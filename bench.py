@@ -7,8 +7,11 @@ Default workload: all i<j pairs of 4096 dim-8 series with lengths U[64, 2048]
 Other workloads: --workload w2 (one 3-D pair, n = m = 1e6 FP32, or 1e5 FP64
 with --dtype f64), w1 (one 1-D FP64 pair, n = m = 1000), w4 (2048 x 2048
 dim-64 block, tensor-core cross term), w5 (learned k-NN: 1e5-series database,
-1000 queries; queries/s at recall@10 >= 0.99 against the exact batched path).
-The default run also appends a "knn" object with the w5 result.
+1000 queries; queries/s at recall@10 >= 0.99 against the exact batched path),
+path / lcs / dtw (TWED edit paths, LCS lengths and DTW on the same wavefront
+engine, GCUPS).  The default run also appends the w1, w2 and w4 lines, a "dp"
+object with the path, lcs and dtw lines and a "knn" object with the w5
+result.
 
 `python bench.py --gpus N --steps K --warmup W` prints one JSON line.  Under
 torchrun each rank runs its own instance of the workload (independent
@@ -46,10 +49,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["w3", "w4", "w2", "w1", "w5", "u1", "u2"], default="w3")
+    ap.add_argument("--workload", choices=["w3", "w4", "w2", "w1", "w5", "u1", "u2", "path", "lcs", "dtw"],
+                    default="w3")
     ap.add_argument("--no-knn", action="store_true", help="w3: skip the appended w5 result")
     ap.add_argument("--no-extra", action="store_true",
                     help="w3: skip the appended w1, w2 and w4 results")
+    ap.add_argument("--no-dp", action="store_true",
+                    help="w3: skip the appended edit-path, LCS and DTW results")
     ap.add_argument("--knn-epochs", type=int, default=40)
     ap.add_argument("--knn-pairs", type=int, default=1_000_000)
     ap.add_argument("--knn-db", type=int, default=100_000)
@@ -547,7 +553,7 @@ def _sub(args, **kw):
 
 EXTRA_KEYS = ("value", "unit", "ms_per_step", "steps", "warmup", "config", "dtype", "roofline",
               "tensor", "cpu_baseline", "error_vs_oracle", "error_vs_f64_gpu", "clocks", "result",
-              "cells_per_step", "kernel_ms", "plan")
+              "cells_per_step", "kernel_ms", "plan", "gpu_launches")
 
 
 def _extra_line(res, steps, warmup):
@@ -579,6 +585,223 @@ def bench_extra(args, rank, world, dev):
     a4 = _sub(args, workload="w4", xterm="tf32", steps=3, warmup=3, no_e2e=True,
               cpu_seconds=min(args.cpu_seconds, 6.0))
     out["w4"] = _extra_line(bench_plan(a4, rank, world, dev, "w4"), 3, 3)
+    return out
+
+
+def _timed_steps(fn, steps, warmup, world, dev, flush=None):
+    """Device time per step of fn(stream), CUDA events on the launching
+    stream; with `flush` (a tensor larger than L2), L2 is overwritten before
+    every step outside the timed events."""
+    import torch
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        fn(stream)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps if flush is not None else 1)]
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        barrier(world)
+        if flush is None:
+            evs[0][0].record(stream)
+            for _ in range(steps):
+                fn(stream)
+            evs[0][1].record(stream)
+        else:
+            for e0, e1 in evs:
+                flush.add_(1)
+                e0.record(stream)
+                fn(stream)
+                e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(world)
+    ms = sum(e0.elapsed_time(e1) for e0, e1 in evs)
+    return max_over_ranks(ms, world, dev) / steps, clk.summary()
+
+
+def _fp32_roof(cells, ms, opc, kernel, dev):
+    import torch
+    props = torch.cuda.get_device_properties(dev)
+    sm_max = float(measured_peaks().get("sm_max_mhz", FALLBACK_SM_MAX_MHZ))
+    peak = props.multi_processor_count * FP32_LANES_PER_SM * sm_max * 1e6
+    mp = ffma_peak()
+    ach = cells * opc / (ms / 1e3)
+    return {"bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "Top/s",
+            "frac": ach / peak, "traffic": None, "ops_per_cell": opc, "kernel": kernel,
+            "peak_basis": f"{props.multi_processor_count} SMs x {FP32_LANES_PER_SM} FP32 lanes x "
+                          f"{sm_max:.0f} MHz", "peak_measured": mp / 1e12, "frac_of_measured": ach / mp}
+
+
+def bench_dp(args, rank, world, dev, which=("path", "lcs", "dtw"), steps=5, warmup=3):
+    """The dynamic programs beside TWED's value, one line each:
+    path -- TWED with its optimal edit path (2 choice bits per cell, walk
+            back), FP32, 2048 seeded i<j pairs of the 4096-series dim-8 set;
+    lcs  -- LCS lengths of 65,536 seeded i<j pairs of 4096 symbol sequences
+            (alphabet 4, lengths U[64, 2048]), L2 flushed before every step;
+    dtw  -- DTW (lp point distance, p = 2), FP32, 32,768 seeded i<j pairs of
+            the 4096-series dim-8 set.
+    Each reports GCUPS (interior cells / s), its roofline, the oracle timed
+    on a bounded sample of the same pairs and the GPU results against the
+    oracle's on that sample."""
+    import ctypes
+
+    import torch
+
+    import oracle
+    from paper_2007_16135_gb300 import twed
+    from paper_2007_16135_gb300 import workloads as W
+
+    out = {}
+    budget = min(args.cpu_seconds, 6.0)
+    sets = {}
+
+    def w3():
+        if "w3" not in sets:
+            S = w3_set(rank)
+            sets["w3"] = (S, twed.DeviceSet.from_numpy(S.vals, S.ts, S.offs, torch.float32, device=dev))
+        return sets["w3"]
+
+    if "path" in which:
+        S, D = w3()
+        nu, lam, p = 0.5, 0.5, 2
+        pairs = W.sample_upper_pairs(S.n, 2048, 3)
+        pd = torch.as_tensor(pairs, device=dev)
+        bufs = twed.path_batch_buffers(D, D, pd)
+        L = S.lengths.astype(np.int64)
+        cells = int((L[pairs[:, 0]] * L[pairs[:, 1]]).sum())
+        ms, clk = _timed_steps(lambda st: twed.twed_path_batch(D, D, pd, nu, lam, p, stream=st, out=bufs),
+                               steps, warmup, world, dev)
+        twed.default_handle().sync_status()
+        res = {"value": cells * world / (ms / 1e3) / 1e9, "unit": "GCUPS", "ms_per_step": ms,
+               "cells_per_step": cells, "dtype": "f32", "clocks": clk, "gpu_launches": 3 * steps,
+               "roofline": _fp32_roof(cells, ms, ops_per_cell(8, p), "path_pairs_kernel<float,8,2,4>", dev),
+               "config": {"workload": "TWED edit paths: 2048 seeded i<j pairs of 4096 dim-8 series, "
+                                      "lengths U[64,2048], FP32, nu=lambda=0.5, p=2",
+                          "pairs": len(pairs), "l2": "series records 208 MB > 126 MB L2",
+                          "output": "distance + move string per pair (2-bit choices, walk back)"}}
+        if rank == 0 and not args.no_cpu:
+            dist, moves, offs, lens = (x.cpu().numpy() for x in bufs)
+            S64 = S.astype(np.float64)
+            t0, done, cells_cpu, errs, ok = time.perf_counter(), 0, 0, [], 0
+            while done < len(pairs) and time.perf_counter() - t0 < budget:
+                x, y = pairs[done]
+                (av, at), (bv, bt) = S64.series(x), S64.series(y)
+                value, want = oracle.twed_path(av, at, bv, bt, nu, lam, p)
+                got = moves[offs[done]:offs[done] + lens[done]]
+                nm = int((got == 0).sum())
+                ok += int(nm + int((got == 1).sum()) == len(at) - 1 and nm + int((got == 2).sum()) == len(bt) - 1)
+                errs.append(abs(float(dist[done]) - value) / value)
+                cells_cpu += len(at) * len(bt)
+                done += 1
+            el = time.perf_counter() - t0
+            res["cpu_baseline"] = {"value": cells_cpu / el / 1e9, "unit": "GCUPS", "cores": 1, "kind": "oracle",
+                                   "sample": f"the first {done} of the pairs ({cells_cpu:.3e} cells, {el:.1f} s), "
+                                             "FP64 full-matrix oracle with path, one thread"}
+            # FP64 GPU paths of the same sample, move for move against the oracle
+            D64 = twed.DeviceSet.from_numpy(S.vals.astype(np.float64), S.ts.astype(np.float64), S.offs,
+                                            torch.float64, device=dev)
+            ps = torch.as_tensor(pairs[:done], device=dev)
+            d64, m64, o64, l64 = (x.cpu().numpy() for x in twed.twed_path_batch(D64, D64, ps, nu, lam, p))
+            twed.default_handle().sync_status()
+            same = 0
+            for k in range(done):
+                x, y = pairs[k]
+                (av, at), (bv, bt) = S64.series(x), S64.series(y)
+                value, want = oracle.twed_path(av, at, bv, bt, nu, lam, p)
+                got = "".join(twed.MOVE_CHARS[v] for v in m64[o64[k]:o64[k] + l64[k]])
+                same += int(got == want and d64[k] == value)
+            res["error_vs_oracle"] = {"rel_max_f32": float(max(errs)), "bound": 1e-5, "pairs": done,
+                                      "f32_paths_consistent": ok,
+                                      "f64_moves_equal_oracle": same,
+                                      "how": "oracle on the FP32-rounded inputs upcast; FP64 GPU paths "
+                                             "compared move for move, distances bitwise"}
+        out["path"] = _extra_line(res, steps, warmup)
+
+    if "lcs" in which:
+        seqs = W.seqs_w8(4096, stream=0 if rank == 0 else 10 + rank)
+        X = twed.DeviceSeqs.from_lists(seqs, device=dev)
+        pairs = W.sample_upper_pairs(len(seqs), 65536, 8)
+        pd = torch.as_tensor(pairs, device=dev)
+        L = np.array([len(x) for x in seqs], dtype=np.int64)
+        cells = int((L[pairs[:, 0]] * L[pairs[:, 1]]).sum())
+        res_t = torch.empty(len(pairs), dtype=torch.int32, device=dev)
+        flush = torch.empty(64 << 20, dtype=torch.float32, device=dev)  # 256 MB > L2
+
+        def run_lcs(st):
+            h = twed.default_handle()
+            sx = X.cstruct()
+            h.check(h.lib.twed_lcs_batch(h.h, ctypes.byref(sx), ctypes.byref(sx), pd.data_ptr(), len(pairs),
+                                         res_t.data_ptr(), ctypes.c_void_p(st.cuda_stream)))
+
+        ms, clk = _timed_steps(run_lcs, steps, warmup, world, dev, flush=flush)
+        twed.default_handle().sync_status()
+        del flush
+        ialu = twed.pipe_peak(twed.PEAK_IALU32)
+        opc = 4
+        ach = cells * opc / (ms / 1e3)
+        res = {"value": cells * world / (ms / 1e3) / 1e9, "unit": "GCUPS", "ms_per_step": ms,
+               "cells_per_step": cells, "dtype": "int32", "clocks": clk, "gpu_launches": steps,
+               "roofline": {"bound": "alu", "achieved": ach / 1e12, "peak": ialu / 1e12, "unit": "Top/s",
+                            "frac": ach / ialu, "traffic": None, "ops_per_cell": opc,
+                            "kernel": "lcs_pairs_kernel<8>",
+                            "peak_basis": "measured 32-bit integer xor/max chains on every SM (ALU pipe)"},
+               "config": {"workload": "LCS lengths: 65,536 seeded i<j pairs of 4096 sequences, alphabet 4, "
+                                      "lengths U[64,2048]", "pairs": len(pairs),
+                          "l2": "256 MB buffer written before every step (outside the events)"}}
+        if rank == 0 and not args.no_cpu:
+            got = res_t.cpu().numpy()
+            t0, done, cells_cpu, bad = time.perf_counter(), 0, 0, 0
+            while done < len(pairs) and time.perf_counter() - t0 < budget:
+                x, y = pairs[done]
+                bad += int(oracle.lcs_length_rolling(seqs[x], seqs[y]) != int(got[done]))
+                cells_cpu += int(L[x] * L[y])
+                done += 1
+            el = time.perf_counter() - t0
+            res["cpu_baseline"] = {"value": cells_cpu / el / 1e9, "unit": "GCUPS", "cores": 1, "kind": "oracle",
+                                   "sample": f"the first {done} of the pairs ({cells_cpu:.3e} cells, {el:.1f} s), "
+                                             "rolling-row oracle, one thread"}
+            res["error_vs_oracle"] = {"mismatches": bad, "pairs": done, "bound": "bit-exact"}
+        out["lcs"] = _extra_line(res, steps, warmup)
+
+    if "dtw" in which:
+        S, D = w3()
+        p = 2
+        pairs = W.sample_upper_pairs(S.n, 32768, 3)
+        pd = torch.as_tensor(pairs, device=dev)
+        L = S.lengths.astype(np.int64)
+        cells = int((L[pairs[:, 0]] * L[pairs[:, 1]]).sum())
+        res_t = torch.empty(len(pairs), dtype=torch.float32, device=dev)
+
+        def run_dtw(st):
+            h = twed.default_handle()
+            sa = D.cstruct()
+            h.check(h.lib.twed_dtw_batch_f32(h.h, ctypes.byref(sa), ctypes.byref(sa), pd.data_ptr(), len(pairs),
+                                             8, p, res_t.data_ptr(), ctypes.c_void_p(st.cuda_stream)))
+
+        ms, clk = _timed_steps(run_dtw, steps, warmup, world, dev)
+        twed.default_handle().sync_status()
+        res = {"value": cells * world / (ms / 1e3) / 1e9, "unit": "GCUPS", "ms_per_step": ms,
+               "cells_per_step": cells, "dtype": "f32", "clocks": clk, "gpu_launches": steps,
+               "roofline": _fp32_roof(cells, ms, 2 * 8 + 1, "dtw_pairs_kernel<float,8,2,4>", dev),
+               "config": {"workload": "DTW: 32,768 seeded i<j pairs of 4096 dim-8 series, lengths U[64,2048], "
+                                      "FP32, p=2", "pairs": len(pairs),
+                          "l2": "series values 139 MB > 126 MB L2"}}
+        if rank == 0 and not args.no_cpu:
+            got = res_t.cpu().numpy()
+            S64 = S.astype(np.float64)
+            t0, done, cells_cpu, errs = time.perf_counter(), 0, 0, []
+            while done < len(pairs) and time.perf_counter() - t0 < budget:
+                x, y = pairs[done]
+                want = oracle.dtw(S64.series(x)[0], S64.series(y)[0], p)
+                errs.append(abs(float(got[done]) - want) / want)
+                cells_cpu += int(L[x] * L[y])
+                done += 1
+            el = time.perf_counter() - t0
+            res["cpu_baseline"] = {"value": cells_cpu / el / 1e9, "unit": "GCUPS", "cores": 1, "kind": "oracle",
+                                   "sample": f"the first {done} of the pairs ({cells_cpu:.3e} cells, {el:.1f} s), "
+                                             "FP64 rolling-row oracle, one thread"}
+            res["error_vs_oracle"] = {"rel_max": float(max(errs)), "bound": 1e-5, "pairs": done,
+                                      "how": "oracle on the FP32-rounded inputs upcast"}
+        out["dtw"] = _extra_line(res, steps, warmup)
     return out
 
 
@@ -859,6 +1082,8 @@ def main():
         res = bench_plan(args, rank, world, dev, args.workload)
         if args.workload == "w3" and not args.no_extra:
             res.update(bench_extra(args, rank, world, dev))
+        if args.workload == "w3" and not args.no_dp:
+            res["dp"] = bench_dp(args, rank, world, dev)
         if args.workload == "w3" and not args.no_knn:
             kn = bench_knn(args, rank, world, dev, steps=10, warmup=3)
             res["knn"] = {"metric": "k-NN queries/s at recall@10>=0.99 vs exact batched",
@@ -870,6 +1095,9 @@ def main():
                           "config": kn["config"]}
     elif args.workload == "w5":
         res = bench_knn(args, rank, world, dev, steps=args.steps, warmup=args.warmup)
+    elif args.workload in ("path", "lcs", "dtw"):
+        res = bench_dp(args, rank, world, dev, which=(args.workload,), steps=args.steps,
+                       warmup=args.warmup)[args.workload]
     else:
         res = bench_pair(args, rank, world, dev, args.workload)
     if rank == 0:
@@ -880,7 +1108,7 @@ def main():
                 "config": res["config"]}
         for k in ("roofline", "tensor", "cpu_baseline", "e2e", "gpu_launches", "clocks",
                   "error_vs_oracle", "error_vs_f64_gpu", "kernel_ms", "plan", "cells_per_step", "result",
-                  "knn", "w1", "w2", "w4"):
+                  "knn", "w1", "w2", "w4", "dp"):
             if k in res:
                 line[k] = res[k]
         print(json.dumps(line), flush=True)

@@ -518,11 +518,13 @@ twed_status_t twed_topk_rows_f32(twed_handle_t handle, const float* d_D, int64_t
 /* ---- pipe peaks -----------------------------------------------------------
  * Not from the paper: measures the issue rate that bounds the ALU-bound
  * kernels, for their roofline.  Independent FFMA (FP32) or DFMA (FP64)
- * chains on every SM, timed with CUDA events on the legacy stream (best of
- * three after a warm-up); *ops_per_s = lane operations per second (one FMA =
- * one operation).  Blocking. */
+ * chains, or (IALU32) chains of a 32-bit integer xor and max, on every SM,
+ * timed with CUDA events on the legacy stream (best of three after a
+ * warm-up); *ops_per_s = lane operations per second (one FMA, one xor or one
+ * max = one operation).  Blocking. */
 #define TWED_PEAK_FFMA32 0
 #define TWED_PEAK_DFMA64 1
+#define TWED_PEAK_IALU32 2
 twed_status_t twed_pipe_peak(twed_handle_t handle, int kind, double* ops_per_s);
 
 #ifdef __cplusplus

@@ -377,14 +377,10 @@ def twed_path(a, ta, b, tb, nu, lam, p=2, dtype="f64", handle: Handle | None = N
     return float(out[0]), "".join(MOVE_CHARS[x] for x in moves[:int(n[0])])
 
 
-def twed_path_batch(A: DeviceSet, B: DeviceSet, pairs, nu, lam, p=2, stream=None,
-                    handle: Handle | None = None):
-    """Distances and edit paths of listed pairs (device int64 [k, 2]):
-    ``(dist [k], moves int8, move_offs [k], lens [k])`` on the device; pair
-    k's moves are ``moves[move_offs[k] : move_offs[k] + lens[k]]``."""
+def path_batch_buffers(A: DeviceSet, B: DeviceSet, pairs):
+    """Output buffers for :func:`twed_path_batch`: ``(dist, moves, move_offs,
+    lens)``, with room for n + m - 2 moves per pair."""
     import torch
-    h = handle or default_handle()
-    pairs = pairs.contiguous()
     k = pairs.shape[0]
     la = torch.as_tensor(np.diff(A.offs_host), device=pairs.device)
     lb = torch.as_tensor(np.diff(B.offs_host), device=pairs.device)
@@ -395,6 +391,21 @@ def twed_path_batch(A: DeviceSet, B: DeviceSet, pairs, nu, lam, p=2, stream=None
     moves = torch.zeros(int(cap.sum().item()) if k else 1, dtype=torch.int8, device=pairs.device)
     dist = torch.empty(k, dtype=A.vals.dtype, device=pairs.device)
     lens = torch.empty(k, dtype=torch.int64, device=pairs.device)
+    return dist, moves, offs, lens
+
+
+def twed_path_batch(A: DeviceSet, B: DeviceSet, pairs, nu, lam, p=2, stream=None,
+                    handle: Handle | None = None, out=None):
+    """Distances and edit paths of listed pairs (device int64 [k, 2]):
+    ``(dist [k], moves int8, move_offs [k], lens [k])`` on the device; pair
+    k's moves are ``moves[move_offs[k] : move_offs[k] + lens[k]]``.  ``out``
+    reuses buffers from :func:`path_batch_buffers` (no allocation, no
+    synchronization)."""
+    import torch
+    h = handle or default_handle()
+    pairs = pairs.contiguous()
+    k = pairs.shape[0]
+    dist, moves, offs, lens = out if out is not None else path_batch_buffers(A, B, pairs)
     sa, sb = A.cstruct(), B.cstruct()
     f64 = A.vals.dtype == torch.float64
     fn = h.lib.twed_path_batch_f64 if f64 else h.lib.twed_path_batch_f32
@@ -817,11 +828,12 @@ def topk_rows(D, k, cols=None, stream=None, handle: Handle | None = None):
     return idx, val
 
 
-PEAK_FFMA32, PEAK_DFMA64 = 0, 1
+PEAK_FFMA32, PEAK_DFMA64, PEAK_IALU32 = 0, 1, 2
 
 
 def pipe_peak(kind=PEAK_FFMA32, handle: Handle | None = None) -> float:
-    """Measured FMA lane operations per second (FP32 or FP64 pipe)."""
+    """Measured lane operations per second: FP32 or FP64 FMA, or 32-bit
+    integer xor/max (the integer ALU pipe)."""
     h = handle or default_handle()
     v = ctypes.c_double()
     h.check(h.lib.twed_pipe_peak(h.h, int(kind), ctypes.byref(v)))

@@ -26,6 +26,8 @@ Workload numbers:
    and falling trends, upward and downward shifts), t_i = i.
 7. stand-in with the shape of its second validation set: 10 1-D series of
    100,000 points (sinusoids whose periods drift, plus noise), t_i = i.
+8. symbol sequences for the LCS program: 4096 sequences of i.i.d. uniform
+   symbols over an alphabet of 4, lengths U[64, 2048] (the lengths of 3).
 
 All use p = 2.  The paper's own timing runs used random series of power-of-two
 lengths (section "Basic Methodology and Results"); its UCI and MNIST data are
@@ -165,6 +167,14 @@ def set_w4(nseries: int = 2048, len_lo: int = 256, len_hi: int = 1024, dim: int 
         v = (c[5:] - c[:-5]) / 5.0
         out.append((v, unit_times(n)))
     return pack(out)
+
+
+def seqs_w8(nseries: int = 4096, len_lo: int = 64, len_hi: int = 2048, alphabet: int = 4,
+            stream: int = 0) -> list:
+    """Workload 8: i.i.d. uniform int32 symbols in [0, alphabet)."""
+    rng = rng_for(8, stream)
+    lens = _lengths(rng, nseries, len_lo, len_hi)
+    return [rng.integers(0, alphabet, int(n)).astype(np.int32) for n in lens]
 
 
 def set_w5(nseries: int = 100_000, len_lo: int = 128, len_hi: int = 512, dim: int = 4,
