@@ -16,18 +16,24 @@
 // The four strips of a sweep share every B tile (y's points): the MMA of one
 // 16-column tile is 2 x (128 x 16 x 64), A = the four strips' rows in TMEM
 // (row 2L + r of warp q's strip on lane 32q + L of row tile r), written there
-// by the consumers themselves with tcgen05.st.  Roles:
+// by the consumers themselves with tcgen05.st at the start of the sweep.
+// Roles:
 //   warps 0..3  consumers: per 16-step block, tcgen05.ld of their own lanes'
 //               accumulators of the next tile, cost formation for it
-//               interleaved with the 16 wavefront steps of the current tile
-//               (lane L on column s - L + 1 at step s), costs through a
-//               private skewed shared-memory ring; the bottom rows of a strip
-//               go to a per-warp boundary row in global memory, read back by
-//               the warp's next strip of the same series.
+//               (packed f32x2 over adjacent columns) interleaved with the 16
+//               wavefront steps of the current tile (lane L on column
+//               s - L + 1 at step s), costs through a private skewed
+//               shared-memory ring whose first 16 slots are mirrored past its
+//               end so that a block's reads never wrap; the bottom rows of a
+//               strip go to a per-warp boundary row in global memory (two
+//               columns per store), read back by the warp's next strip of the
+//               same series.
 //   warp 4      TMA (cp.async.bulk.tensor) of the B tiles into a 4-stage
 //               ring, as far ahead as the ring allows.
 //   warp 5      tcgen05.mma issue and tcgen05.commit (to the consumers'
 //               accumulator barrier and to the B stage's free barrier).
+// The TMA and MMA warps wait in mbarrier.try_wait with a suspend-time hint,
+// so they take no issue slots from the consumers while they wait.
 // Columns past m get cost +inf and column delete cost 0, which freezes every
 // row at its column-m value, so all lanes can run the same number of steps.
 // Every wait is bounded (%globaltimer, then the launch's error word).
@@ -46,9 +52,11 @@ namespace twed {
 namespace x64 {
 constexpr int D = 64;            // point dimension (MMA K)
 constexpr int RT = 2;            // row tiles per block = DP rows per lane
-constexpr int N = 16;            // columns per tile = wavefront steps per block
-constexpr int NS = 4;            // accumulator stages in TMEM
-constexpr int NBS = 4;           // B tile stages in shared memory (== NS)
+constexpr int N = 16;            // columns per consumer tile = wavefront steps per block
+constexpr int NM = 16;           // columns per MMA tile (a B tile), a multiple of N
+constexpr int HALVES = NM / N;   // consumer tiles per MMA tile
+constexpr int NS = 64 / NM;      // accumulator stages in TMEM (NS x RT x NM = 128 columns)
+constexpr int NBS = NS;          // B tile stages in shared memory
 constexpr int CW = 4;            // consumer warps (one per TMEM lane quadrant)
 constexpr int TMA_WARP = CW;     // B tile loads
 constexpr int MMA_WARP = CW + 1; // tcgen05.mma issue
@@ -61,8 +69,9 @@ constexpr int RS = 2 * (RMIR + 2); // floats per lane: 82 float2, == 2 mod 4 (co
 constexpr int CH = 64;           // row series per work item
 constexpr int TMEM_COLS = 256;
 constexpr int ACC_COL = RT * D;  // accumulators follow the A tiles
-constexpr int BOXES = D / 4;     // TMA boxes per B tile: 4 values x N points each
-constexpr uint32_t TILE_BYTES = N * D * 4;
+constexpr int BOXES = D / 4;     // TMA boxes per B tile: 4 values x NM points each
+constexpr uint32_t TILE_BYTES = NM * D * 4;
+static_assert(NM % N == 0 && NS * RT * NM == 128, "accumulator layout");
 constexpr int BND_PAD = 32;      // boundary rows start 32 entries in (lane 31 writes from column -30)
 
 constexpr int OFF_B = 0;
@@ -149,11 +158,31 @@ __device__ __forceinline__ bool xwait(uint64_t* bar, uint32_t parity, const Sync
     return xwait_sleep(bar, parity, sc, 16);
 }
 
+
+// Waits of the TMA and MMA warps, which run ahead and wait most of the time:
+// try_wait with a suspend-time hint, so a waiting warp is descheduled until
+// the phase completes (or the hint expires) instead of polling.
+__device__ __forceinline__ bool xwait_prod(uint64_t* bar, uint32_t parity, const SyncCtl& sc) {
+    if (tc::mbar_test_wait(bar, parity)) return true;
+    const unsigned long long t0 = globaltimer();
+    while (!tc::mbar_try_wait_sleep(bar, parity, 50000u))
+        if (xwait_fail(sc, t0)) return false;
+    return true;
+}
+
 // Predicated 8-byte global store at p + OFF bytes (no branch around it).
 template <int OFF>
 __device__ __forceinline__ void st_global_pred(float2* p, float a, float b, int pred) {
     asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %3, 0;\n\t@q st.global.v2.f32 [%0+%4], {%1, %2};\n\t}" ::"l"(p),
                  "f"(a), "f"(b), "r"(pred), "n"(OFF)
+                 : "memory");
+}
+
+// Predicated 16-byte global store of two (D, c) columns at p + OFF bytes.
+template <int OFF>
+__device__ __forceinline__ void st_global_pred4(float2* p, float a, float b, float c, float d, int pred) {
+    asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %5, 0;\n\t@q st.global.v4.f32 [%0+%6], {%1, %2, %3, %4};\n\t}" ::"l"(p),
+                 "f"(a), "f"(b), "f"(c), "f"(d), "r"(pred), "n"(OFF)
                  : "memory");
 }
 
@@ -205,6 +234,8 @@ struct XSched {  // 72 bytes
     int rem[x64::CW];      // strips left, the current one included
     int k[x64::CW];        // current strip index
 };
+
+static_assert(sizeof(XSched) <= 80, "the next-strip record follows the schedule at byte 80");
 
 __device__ __forceinline__ int series_len(const XtermArgs& a, int64_t pos) {
     const int64_t x = a.perm_a[pos];
@@ -286,7 +317,7 @@ __global__ void __launch_bounds__(x64::THREADS, 2) xterm_sweep_kernel(const __gr
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = misc[0];
-    const uint32_t idesc = tc::idesc_tf32(128, N);
+    const uint32_t idesc = tc::idesc_tf32(128, NM);
     // the TMA destinations need a 1024-byte aligned shared window
     const bool aligned = (tc::smem_u32(sm) & 1023u) == 0;
 
@@ -310,7 +341,8 @@ __global__ void __launch_bounds__(x64::THREADS, 2) xterm_sweep_kernel(const __gr
         if (w >= a.nitems || !ok) break;
         const XItem it = decode_item(a, w);
         const int m = it.m;
-        const int ntiles = (m + N - 1) / N;
+        const int ntiles = (m + N - 1) / N;     // consumer tiles (16 columns)
+        const int ntilesM = (m + NM - 1) / NM;  // MMA / B tiles
         // each warp keeps its copy of the schedule in shared memory (every lane
         // computes the same values)
         XSched& sch = *reinterpret_cast<XSched*>(sm + OFF_SCHED + warp * SCHED_BYTES);
@@ -325,21 +357,21 @@ __global__ void __launch_bounds__(x64::THREADS, 2) xterm_sweep_kernel(const __gr
                     ++nsw;
                     sched_end(sch);
                 }
-                total = nsw * (uint32_t)ntiles;
+                total = nsw * (uint32_t)ntilesM;
             }
             if (warp == TMA_WARP) {
                 // ======================= B tiles by TMA, up to NBS ahead of the MMA
                 for (uint32_t idx = 0; idx < total; ++idx) {
                     const int st = (int)(Lp % NBS);
                     bool w2 = true;
-                    if (Lp >= NBS) w2 = xwait_sleep(&b_empty[st], ((Lp / NBS) - 1) & 1, a.sc, 512);
+                    if (Lp >= NBS) w2 = xwait_prod(&b_empty[st], ((Lp / NBS) - 1) & 1, a.sc);
                     if (!__all_sync(kFull, w2)) { ok = false; break; }
-                    const int t = (int)(idx % (uint32_t)ntiles);
+                    const int t = (int)(idx % (uint32_t)ntilesM);
                     unsigned char* dst = sm + OFF_B + st * TILE_BYTES;
                     if (lane == 0) tc::mbar_arrive_expect_tx(&b_full[st], TILE_BYTES);
                     __syncwarp();
                     if (lane < BOXES)
-                        tc::tma_load_2d(dst + lane * (N * 16), &tmap_b, 4 * lane, (int)(it.yb + (int64_t)N * t),
+                        tc::tma_load_2d(dst + lane * (NM * 16), &tmap_b, 4 * lane, (int)(it.yb + (int64_t)NM * t),
                                         &b_full[st]);
                     __syncwarp();
                     ++Lp;
@@ -348,10 +380,10 @@ __global__ void __launch_bounds__(x64::THREADS, 2) xterm_sweep_kernel(const __gr
                 // ======================= MMA issue
                 for (uint32_t idx = 0; idx < total; ++idx) {
                     const int st = (int)(Tp % NBS), s = (int)(Tp % NS);
-                    const int t = (int)(idx % (uint32_t)ntiles);
-                    bool w2 = xwait_sleep(&b_full[st], (Tp / NBS) & 1, a.sc, 128);
-                    if (w2 && t == 0) w2 = xwait_sleep(a_ready, sweep_p & 1, a.sc, 32);
-                    if (w2 && Tp >= NS) w2 = xwait_sleep(&acc_empty[s], ((Tp / NS) - 1) & 1, a.sc, 256);
+                    const int t = (int)(idx % (uint32_t)ntilesM);
+                    bool w2 = xwait_prod(&b_full[st], (Tp / NBS) & 1, a.sc);
+                    if (w2 && t == 0) w2 = xwait_prod(a_ready, sweep_p & 1, a.sc);
+                    if (w2 && Tp >= NS) w2 = xwait_prod(&acc_empty[s], ((Tp / NS) - 1) & 1, a.sc);
                     if (!__all_sync(kFull, w2)) { ok = false; break; }
                     tc::fence_after_sync();
                     if (lane == 0) {
@@ -360,10 +392,10 @@ __global__ void __launch_bounds__(x64::THREADS, 2) xterm_sweep_kernel(const __gr
                         for (int r = 0; r < RT; ++r) {
 #pragma unroll
                             for (int ks = 0; ks < D / 8; ++ks) {
-                                // K step ks covers k-groups 2ks, 2ks+1 (boxes 256 bytes apart);
-                                // points 8..15 of the tile sit 128 bytes after points 0..7
-                                const uint64_t bd = tc::smem_desc(bad + ks * 2 * (N * 16), N * 16, 128);
-                                tc::mma_tf32_tmem_a(tmem + (uint32_t)(ACC_COL + s * (RT * N) + r * N),
+                                // K step ks covers k-groups 2ks, 2ks+1 (boxes NM * 16 bytes apart);
+                                // each further 8 points of the tile sit 128 bytes on
+                                const uint64_t bd = tc::smem_desc(bad + ks * 2 * (NM * 16), NM * 16, 128);
+                                tc::mma_tf32_tmem_a(tmem + (uint32_t)(ACC_COL + s * (RT * NM) + r * NM),
                                                     tmem + (uint32_t)(r * D + ks * 8), bd, idesc, ks > 0);
                             }
                         }
@@ -372,7 +404,7 @@ __global__ void __launch_bounds__(x64::THREADS, 2) xterm_sweep_kernel(const __gr
                     }
                     __syncwarp();
                     ++Tp;
-                    if (t == ntiles - 1) ++sweep_p;
+                    if (t == ntilesM - 1) ++sweep_p;
                 }
             }
         } else {
@@ -387,7 +419,13 @@ __global__ void __launch_bounds__(x64::THREADS, 2) xterm_sweep_kernel(const __gr
             float2* bnd_g = a.bnd + (int64_t)(blockIdx.x * CW + q) * a.bnd_stride + BND_PAD;
             const float4* rec_y = a.rec_b + it.yb;
             const float nu = a.nu;
-            while (ok && sched_begin(sch, a, it)) {
+            // the strip this warp runs in a sweep, from its copy of the schedule
+            struct Strip {
+                int64_t x, xa;
+                int n, r0, i0, i1;
+                bool idle, first, last;
+            };
+            auto strip_of = [&]() -> Strip {
                 int64_t pos = -1;
                 int kq = 0, remq = 0;
 #pragma unroll
@@ -398,22 +436,27 @@ __global__ void __launch_bounds__(x64::THREADS, 2) xterm_sweep_kernel(const __gr
                         remq = sch.rem[w];
                     }
                 }
-                const bool idle = pos < 0;
-                const int64_t x = a.perm_a[idle ? it.r_lo : pos];
-                const int64_t xa = a.offs_a[x];
-                const int n = (int)(a.offs_a[x + 1] - xa);
-                const int r0 = STRIP * kq + 1;
-                const bool first = idle || kq == 0;
-                const bool last = !idle && remq == 1;
-                const int i0 = min(r0 + 2 * lane, n), i1 = min(r0 + 2 * lane + 1, n);
-                const float4 ra0 = __ldg(a.rec_a + xa + i0 - 1);
-                const float4 ra1 = __ldg(a.rec_a + xa + i1 - 1);
-                // ---- this strip's rows into the A tiles (every MMA of the previous
-                // sweep has completed: this warp read all of its accumulators)
-                if (!idle) {
+                Strip S;
+                S.idle = pos < 0;
+                S.x = a.perm_a[S.idle ? it.r_lo : pos];
+                S.xa = a.offs_a[S.x];
+                S.n = (int)(a.offs_a[S.x + 1] - S.xa);
+                S.r0 = STRIP * kq + 1;
+                S.first = S.idle || kq == 0;
+                S.last = !S.idle && remq == 1;
+                S.i0 = min(S.r0 + 2 * lane, S.n);
+                S.i1 = min(S.r0 + 2 * lane + 1, S.n);
+                return S;
+            };
+            // this lane's point row r (0, 1) of a strip
+            auto a_src = [&](const Strip& S, int r) -> const float4* {
+                return reinterpret_cast<const float4*>(a.vals_a + (S.xa + (r ? S.i1 : S.i0) - 1) * D);
+            };
+            auto write_a = [&](const Strip& S) {
+                if (!S.idle) {
 #pragma unroll
                     for (int r = 0; r < RT; ++r) {
-                        const float4* src = reinterpret_cast<const float4*>(a.vals_a + (xa + (r ? i1 : i0) - 1) * D);
+                        const float4* src = a_src(S, r);
 #pragma unroll
                         for (int h = 0; h < 2; ++h) {
                             float v[32];
@@ -433,6 +476,34 @@ __global__ void __launch_bounds__(x64::THREADS, 2) xterm_sweep_kernel(const __gr
                 tc::fence_before_sync();
                 __syncwarp();
                 if (lane == 0) tc::mbar_arrive(a_ready);
+            };
+            bool more = sched_begin(sch, a, it);
+            while (ok && more) {
+                const Strip cur = strip_of();  // the schedule holds this sweep's assignment
+                // ---- this strip's rows into the A tiles (every MMA of the previous
+                // sweep has completed: this warp read all of its accumulators)
+                write_a(cur);
+                const int64_t x = cur.x;
+                const int n = cur.n;
+                const int r0 = cur.r0;
+                const bool first = cur.first, last = cur.last;
+                const float4 ra0 = __ldg(a.rec_a + cur.xa + cur.i0 - 1);
+                const float4 ra1 = __ldg(a.rec_a + cur.xa + cur.i1 - 1);
+                // the next sweep's strip, decided now: its rows go into the A tiles
+                // during this sweep's last blocks, once every MMA of this sweep has
+                // completed, so that the MMA warp can start the next sweep early
+                sched_end(sch);
+                more = sched_begin(sch, a, it);
+                if (more) {
+                    const Strip nx = strip_of();
+                    if (!nx.idle) {
+#pragma unroll
+                        for (int r = 0; r < RT; ++r) {
+                            tc::prefetch_l2(a_src(nx, r));
+                            tc::prefetch_l2(a_src(nx, r) + 8);
+                        }
+                    }
+                }
                 // the TMA warp keeps the B loads four tiles ahead of its own use; the
                 // MMA warp, once every warp's rows are in, issues tiles 0..2
 
@@ -443,8 +514,10 @@ __global__ void __launch_bounds__(x64::THREADS, 2) xterm_sweep_kernel(const __gr
                 delb_r[CRING - 32 + lane] = 0.f;
                 // column record of column j (1-based) of y: (t', dB, |b|^2, 0); past m the
                 // norm is +inf (cost +inf) and the delete cost 0, which freezes the rows
-                auto colrec = [&](int j) -> float4 {
-                    float4 v = __ldg(rec_y + (min(j, m) - 1));  // j >= 1
+                // (loaded raw; the selects are applied when the value is stored, so
+                // that no instruction waits for the load before then)
+                auto colrec_ld = [&](int j) -> float4 { return __ldg(rec_y + (min(j, m) - 1)); };  // j >= 1
+                auto colrec_fix = [&](float4 v, int j) -> float4 {
                     const bool in = j <= m;
                     v.x = in ? v.x : 0.f;
                     v.y = in ? v.y : 0.f;
@@ -453,22 +526,22 @@ __global__ void __launch_bounds__(x64::THREADS, 2) xterm_sweep_kernel(const __gr
                 };
                 // the row above the strip at column j (1-based): (inf, 0) above a
                 // series' first strip and past m
-                auto rowabove = [&](int j) -> float2 {
-                    const float2 v = __ldcg(bnd_g + min(j, m));
+                auto rowabove_ld = [&](int j) -> float2 { return __ldcg(bnd_g + min(j, m)); };
+                auto rowabove_fix = [&](float2 v, int j) -> float2 {
                     return (first || j > m) ? make_float2(INF, 0.f) : v;
                 };
                 // tile 0's records (lanes 16..31 write the same values again), then the
                 // staged inputs of the first two blocks: records of tiles 1 and 2, the
                 // row above for steps 0..31
                 {
-                    const float4 c0 = colrec((lane & (N - 1)) + 1);
+                    const float4 c0 = colrec_fix(colrec_ld((lane & (N - 1)) + 1), (lane & (N - 1)) + 1);
                     ctime[lane & (N - 1)] = c0.x;
                     cnorm[lane & (N - 1)] = c0.z;
                     delb_r[lane & (N - 1)] = c0.y;
                     delb_r[CRING + (lane & (N - 1))] = c0.y;  // mirror
                 }
-                float4 cr_st = colrec(N + 1 + lane);
-                float2 bd_st = rowabove(1 + lane);
+                float4 cr_st = colrec_ld(N + 1 + lane);
+                float2 bd_st = rowabove_ld(1 + lane);
                 __syncwarp();
                 // ---- costs of tile 0
                 const float na0 = ra0.z, na1 = ra1.z, ti0 = ra0.x, ti1 = ra1.x;
@@ -479,25 +552,44 @@ __global__ void __launch_bounds__(x64::THREADS, 2) xterm_sweep_kernel(const __gr
                     const bool w2 = xwait(&acc_full[s], (Tc / NS) & 1, a.sc);
                     if (!__all_sync(kFull, w2)) { ok = false; break; }
                     tc::fence_after_sync();
-                    tc::tmem_ld16x2(tmem + tlane + (uint32_t)(ACC_COL + s * (RT * N)),
-                                    tmem + tlane + (uint32_t)(ACC_COL + s * (RT * N) + N), X0, X1);
+                    tc::tmem_ld16x2(tmem + tlane + (uint32_t)(ACC_COL + s * (RT * NM)),
+                                    tmem + tlane + (uint32_t)(ACC_COL + s * (RT * NM) + NM), X0, X1);
                     tc::fence_before_sync();
                     __syncwarp();
-                    if (lane == 0) tc::mbar_arrive(&acc_empty[s]);
-                    ++Tc;
+                    // the stage is released after its last consumer tile has been read
+                    if (HALVES == 1 || ntiles == 1) {
+                        if (lane == 0) tc::mbar_arrive(&acc_empty[s]);
+                        ++Tc;
+                    }
                 }
-                // c(i, j) = sqrt(max(|a_i|^2 + |b_j|^2 - 2 X, 0)) + nu |t_i - t'_j|
-                auto cost = [&](float x, float na, float ti, float nb, float tj) -> float {
-                    const float d2 = fmaf(-2.f, x, na + nb);
-                    return fmaf(nu, fabsf(ti - tj), Arith<float>::root(fmaxf(d2, 0.f)));
+                // c(i, j) = sqrt(|d^2|) + nu |t_i - t'_j| with d^2 = |a_i|^2 + |b_j|^2 - 2 X.
+                // d^2 < 0 only through cancellation when the true d^2 is within
+                // rounding of 0; |d^2| then stays within that rounding of the
+                // truth, like max(d^2, 0) would.  d^2 and t_i - t'_j are formed for
+                // two adjacent columns at once (packed f32x2).
+                const unsigned long long na0p = f2_pack(na0, na0), na1p = f2_pack(na1, na1);
+                const unsigned long long ti0p = f2_pack(ti0, ti0), ti1p = f2_pack(ti1, ti1);
+                const unsigned long long m2p = f2_pack(-2.f, -2.f);
+                auto cost2 = [&](unsigned long long x2, unsigned long long nap, unsigned long long nb2,
+                                 unsigned long long tip, unsigned long long tj2, float& e_lo, float& e_hi) {
+                    const unsigned long long d2 = f2_fma(x2, m2p, f2_add(nap, nb2));
+                    const unsigned long long dt = f2_sub(tip, tj2);
+                    float s0, s1, t0, t1;
+                    f2_unpack(d2, s0, s1);
+                    f2_unpack(dt, t0, t1);
+                    e_lo = fmaf(nu, fabsf(t0), Arith<float>::root(fabsf(s0)));
+                    e_hi = fmaf(nu, fabsf(t1), Arith<float>::root(fabsf(s1)));
                 };
                 // the costs of 4 columns (u0 .. u0+3 of a tile) into the cost ring at
                 // `dst`, and also at `dst` + the mirror offset when `mirror`
                 auto cost4 = [&](int u0, const float4& tj, const float4& nb, float* dst, bool mirror) {
-                    const float e0 = cost(X0[u0], na0, ti0, nb.x, tj.x), e1 = cost(X1[u0], na1, ti1, nb.x, tj.x);
-                    const float e2 = cost(X0[u0 + 1], na0, ti0, nb.y, tj.y), e3 = cost(X1[u0 + 1], na1, ti1, nb.y, tj.y);
-                    const float e4 = cost(X0[u0 + 2], na0, ti0, nb.z, tj.z), e5 = cost(X1[u0 + 2], na1, ti1, nb.z, tj.z);
-                    const float e6 = cost(X0[u0 + 3], na0, ti0, nb.w, tj.w), e7 = cost(X1[u0 + 3], na1, ti1, nb.w, tj.w);
+                    const unsigned long long nb01 = f2_pack(nb.x, nb.y), nb23 = f2_pack(nb.z, nb.w);
+                    const unsigned long long tj01 = f2_pack(tj.x, tj.y), tj23 = f2_pack(tj.z, tj.w);
+                    float e0, e1, e2, e3, e4, e5, e6, e7;
+                    cost2(f2_pack(X0[u0], X0[u0 + 1]), na0p, nb01, ti0p, tj01, e0, e2);
+                    cost2(f2_pack(X1[u0], X1[u0 + 1]), na1p, nb01, ti1p, tj01, e1, e3);
+                    cost2(f2_pack(X0[u0 + 2], X0[u0 + 3]), na0p, nb23, ti0p, tj23, e4, e6);
+                    cost2(f2_pack(X1[u0 + 2], X1[u0 + 3]), na1p, nb23, ti1p, tj23, e5, e7);
                     st_shared_v4(dst, e0, e1, e2, e3);
                     st_shared_v4(dst + 4, e4, e5, e6, e7);
                     if (mirror) {
@@ -519,32 +611,48 @@ __global__ void __launch_bounds__(x64::THREADS, 2) xterm_sweep_kernel(const __gr
                 const int is31 = lane == 31;
                 for (int b = 0; b < nblk; ++b) {
                     const int sb = N * b;
+                    if (b > 0 && (sb & (RING - 1)) == 0) {
+                        // this block and the next read the cost-ring slots 0..N-1 (written
+                        // in the previous block) past the ring's end: mirror them there
+                        const float4* from = reinterpret_cast<const float4*>(myring);
+                        float4* to = reinterpret_cast<float4*>(myring + 2 * RING);
+#pragma unroll
+                        for (int k = 0; k < N / 2; ++k) to[k] = from[k];
+                    }
                     if ((b & 1) == 0) {
                         // every 32 steps, all lanes: the staged records of tiles b+1,
                         // b+2 (columns 16b+17 ..) and the row above for steps sb ..
                         // sb+31 go to shared memory; then those of the next 32 steps
                         // are loaded (used 32 steps later)
                         const int slot = (N * (b + 1) + lane) & (CRING - 1);
-                        ctime[slot] = cr_st.x;
-                        cnorm[slot] = cr_st.z;
-                        delb_r[slot] = cr_st.y;
-                        if (slot < N) delb_r[CRING + slot] = cr_st.y;  // mirror
-                        bnd_r[(sb + lane) & 63] = bd_st;
+                        const float4 cr = colrec_fix(cr_st, N * (b + 1) + 1 + lane);
+                        ctime[slot] = cr.x;
+                        cnorm[slot] = cr.z;
+                        delb_r[slot] = cr.y;
+                        if (slot < N) delb_r[CRING + slot] = cr.y;  // mirror
+                        bnd_r[(sb + lane) & 63] = rowabove_fix(bd_st, sb + 1 + lane);
                         __syncwarp();
-                        cr_st = colrec(N * (b + 3) + 1 + lane);
-                        bd_st = rowabove(sb + 32 + 1 + lane);
+                        cr_st = colrec_ld(N * (b + 3) + 1 + lane);
+                        bd_st = rowabove_ld(sb + 32 + 1 + lane);
                     }
                     // accumulators of tile b+1: the load is issued here and waited for
                     // three steps later, just before the costs first use them
+                    // (consumer tile b+1 is part h of MMA tile (b+1) / HALVES: only its
+                    // first part waits for the MMA, its last part releases the stage)
                     const bool xload = b + 1 < ntiles;
                     const int xs = (int)(Tc % NS);
+                    const int xh = (b + 1) % HALVES;
+                    const bool xrel = xload && (xh == HALVES - 1 || b + 2 == ntiles);
                     if (xload) {
-                        const bool w2 = xwait(&acc_full[xs], (Tc / NS) & 1, a.sc);
-                        if (!__all_sync(kFull, w2)) { ok = false; break; }
+                        if (xh == 0) {
+                            const bool w2 = xwait(&acc_full[xs], (Tc / NS) & 1, a.sc);
+                            if (!__all_sync(kFull, w2)) { ok = false; break; }
+                        }
                         tc::fence_after_sync();
-                        tc::tmem_ld16x2_async(tmem + tlane + (uint32_t)(ACC_COL + xs * (RT * N)),
-                                              tmem + tlane + (uint32_t)(ACC_COL + xs * (RT * N) + N), X0, X1);
-                        ++Tc;
+                        tc::tmem_ld16x2_async(tmem + tlane + (uint32_t)(ACC_COL + xs * (RT * NM) + xh * N),
+                                              tmem + tlane + (uint32_t)(ACC_COL + xs * (RT * NM) + NM + xh * N), X0,
+                                              X1);
+                        if (xrel) ++Tc;
                     }
                     const int cslot = (N * (b + 1)) & (RING - 1);  // cost-ring slot of tile b+1's first column
                     const int rslot = (N * (b + 1)) & (CRING - 1);  // record-ring slot of the same column
@@ -560,8 +668,8 @@ __global__ void __launch_bounds__(x64::THREADS, 2) xterm_sweep_kernel(const __gr
                     float2 cn = rp[0];
                     float dbn = dp[0];
                     float2 bn = bp[0];
-                    auto block = [&](auto MC) {
-                      constexpr bool kMirror = decltype(MC)::value;
+                    float pD = 0.f, pC = 0.f;  // lane 31's bottom row at the previous (even) step
+                    {
                       unroll_seq(
                         [&](auto UC) {
                             constexpr int u = decltype(UC)::value;
@@ -587,28 +695,34 @@ __global__ void __launch_bounds__(x64::THREADS, 2) xterm_sweep_kernel(const __gr
                             Dl1 = D1;
                             botD = D1;
                             botC = c1;
-                            st_global_pred<8 * u>(bst, D1, c1, is31);
+                            // lane 31's bottom row, two columns per store: columns
+                            // sb - 31 + u (even) and sb - 30 + u at odd u
+                            if constexpr ((u & 1) == 0) {
+                                pD = D1;
+                                pC = c1;
+                            } else {
+                                st_global_pred4<8 * (u - 1)>(bst, pD, pC, D1, c1, is31);
+                            }
                             if constexpr (u == 2) {
                                 // the accumulators have landed: release the stage
                                 if (xload) {
                                     tc::tmem_wait_ld_tied(X0, X1);
-                                    tc::fence_before_sync();
-                                    __syncwarp();
-                                    if (lane == 0) tc::mbar_arrive(&acc_empty[xs]);
+                                    if (xrel) {
+                                        tc::fence_before_sync();
+                                        __syncwarp();
+                                        if (lane == 0) tc::mbar_arrive(&acc_empty[xs]);
+                                    }
                                 }
                             }
                             // costs of tile b+1, 4 columns every 4 steps (not read in this
-                            // block); cost slots 0..N-1 are mirrored at RING.. for the lanes
-                            // whose window wraps
+                            // block; slots 0..N-1 are mirrored at the start of the next block)
                             if constexpr ((u & 3) == 3)
                                 cost4(u - 3, *reinterpret_cast<const float4*>(ctime + rslot + u - 3),
-                                      *reinterpret_cast<const float4*>(cnorm + rslot + u - 3), cst + 2 * (u - 3),
-                                      kMirror);
+                                      *reinterpret_cast<const float4*>(cnorm + rslot + u - 3), cst + 2 * (u - 3), false);
                         },
                         std::make_integer_sequence<int, N>{});
-                    };
-                    if (cslot == 0) block(std::true_type{});
-                    else block(std::false_type{});
+                    }
+
                     __syncwarp();
                 }
                 if (!ok) break;
@@ -625,7 +739,6 @@ __global__ void __launch_bounds__(x64::THREADS, 2) xterm_sweep_kernel(const __gr
                         }
                     }
                 }
-                sched_end(sch);
             }
         }
         if (!ok && lane == 0) {
@@ -673,7 +786,7 @@ static cudaError_t xterm_attributes() {
 }
 
 // Tensor map of a set's 64-dimensional values for the B tiles: [total][64]
-// FP32, rows 256 bytes apart; a box is 4 values (16 bytes) of 16 points, so
+// FP32, rows 256 bytes apart; a box is 4 values (16 bytes) of NM points, so
 // one tile is 16 boxes at x = 0, 4, .., 60.  Points past the end read 0.
 cudaError_t xterm_tensor_map(void* tmap, const float* vals, int64_t total) {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
@@ -688,7 +801,7 @@ cudaError_t xterm_tensor_map(void* tmap, const float* vals, int64_t total) {
     }
     const cuuint64_t dims[2] = {(cuuint64_t)x64::D, (cuuint64_t)total};
     const cuuint64_t strides[1] = {(cuuint64_t)x64::D * sizeof(float)};
-    const cuuint32_t box[2] = {4, (cuuint32_t)x64::N};
+    const cuuint32_t box[2] = {4, (cuuint32_t)x64::NM};
     const cuuint32_t estr[2] = {1, 1};
     CUresult r = encode(reinterpret_cast<CUtensorMap*>(tmap), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
                         const_cast<float*>(vals), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -756,6 +869,8 @@ void xterm_resources(char* buf, int len) {
 int xterm_rows_per_item() { return x64::CH; }
 int xterm_warps_per_block() { return x64::CW; }
 int xterm_threads() { return x64::THREADS; }
-int64_t xterm_bnd_stride(int64_t max_len) { return max_len + 64 + x64::BND_PAD; }
+// even, so that every boundary row starts on a 16-byte boundary (pairs of
+// columns are stored as one 16-byte vector)
+int64_t xterm_bnd_stride(int64_t max_len) { return (max_len + 64 + x64::BND_PAD + 1) & ~(int64_t)1; }
 
 }  // namespace twed
