@@ -56,7 +56,9 @@ def parse():
                     help="w3: skip the appended w1, w2 and w4 results")
     ap.add_argument("--no-dp", action="store_true",
                     help="w3: skip the appended edit-path, LCS and DTW results")
-    ap.add_argument("--knn-epochs", type=int, default=40)
+    ap.add_argument("--knn-epochs", type=int, default=80)
+    ap.add_argument("--knn-rel-floor", type=float, default=0.2,
+                    help="encoder loss: squared relative error with this floor (0: squared error)")
     ap.add_argument("--knn-pairs", type=int, default=1_000_000)
     ap.add_argument("--knn-db", type=int, default=100_000)
     ap.add_argument("--knn-queries", type=int, default=1000)
@@ -823,7 +825,7 @@ def bench_knn(args, rank, world, dev, steps, warmup):
     D = twed.DeviceSet.from_numpy(db.vals, db.ts, db.offs, torch.float32, device=dev)
     Q = twed.DeviceSet.from_numpy(qs.vals, qs.ts, qs.offs, torch.float32, device=dev)
     QT = twed.DeviceSet.from_numpy(qt.vals, qt.ts, qt.offs, torch.float32, device=dev)
-    cfg = twed.knn_config(train_pairs=args.knn_pairs, epochs=args.knn_epochs)
+    cfg = twed.knn_config(train_pairs=args.knn_pairs, epochs=args.knn_epochs, rel_floor=args.knn_rel_floor)
     index = twed.KnnIndex(D, nu, lam, p, config=cfg)
     train = index.train()
     stream = torch.cuda.current_stream()
@@ -849,25 +851,28 @@ def bench_knn(args, rank, world, dev, steps, warmup):
         return recall(dist, kth_t)
 
     # the smallest candidate count (to within 100) whose recall@10 on the
-    # tuning queries reaches 0.99
+    # tuning queries reaches 0.99 plus two binomial standard errors of a
+    # recall of 0.99 over their qt.n * k neighbours, so that the reported
+    # queries (a separate draw) clear 0.99 too
+    target = 0.99 + 2.0 * float(np.sqrt(0.99 * 0.01 / (qt.n * k)))
     sweep, c_op = {}, None
     for C in (200, 400, 800, 1600, 3200, 4096):
         if C > db.n:
             break
         sweep[C] = recall_t(C)
-        if sweep[C] >= 0.99:
+        if sweep[C] >= target:
             c_op = C
             break
     if c_op is None:
         c_op = max(sweep)
     else:
-        lo = max([c for c in sweep if sweep[c] < 0.99], default=None)
+        lo = max([c for c in sweep if sweep[c] < target], default=None)
         while lo is not None and c_op - lo > 100:
             mid = ((lo + c_op) // 2 + 99) // 100 * 100
             if mid >= c_op:
                 break
             sweep[mid] = recall_t(mid)
-            if sweep[mid] >= 0.99:
+            if sweep[mid] >= target:
                 c_op = mid
             else:
                 lo = mid
@@ -896,8 +901,9 @@ def bench_knn(args, rank, world, dev, steps, warmup):
     res = {"value": value, "unit": "queries/s", "ms_per_step": ms_step, "clocks": clk.summary(),
            "dtype": "f32",
            "knn": {"recall_at_10": rec_op, "n_candidates": c_op, "k": k,
-                   "n_candidates_chosen_on": f"{qt.n} separate tuning queries (seed stream 5); "
-                                             "recall_at_10 is measured on the reported queries",
+                   "n_candidates_chosen_on": f"{qt.n} separate tuning queries (seed stream 5), smallest C "
+                                             f"with tuning recall >= {target:.4f} (0.99 + 2 standard "
+                                             "errors); recall_at_10 is measured on the reported queries",
                    "recall_sweep_tuning_queries": {str(c): r for c, r in sweep.items()},
                    "exact_queries_per_s": qs.n / exact_s, "exact_s": exact_s,
                    "exact_gcups": exact_cells / exact_s / 1e9,
@@ -963,7 +969,8 @@ def bench_knn(args, rank, world, dev, steps, warmup):
     res["config"] = {"workload": f"w5 learned k-NN: database {db.n} series, {qs.n} queries, dim 4, "
                                  "len U[128,512], random walks, t_i=i, nu=lambda=1, p=2, FP32; "
                                  "encoder 3 x conv1d(64 ch, 5 taps) + length-weighted mean pool + "
-                                 f"linear 32 trained on {train['label_pairs']} exact GPU TWED pairs",
+                                 f"linear 32 trained on {train['label_pairs']} exact GPU TWED pairs "
+                                 f"(squared relative error, floor {args.knn_rel_floor}, {args.knn_epochs} epochs)",
                      "k": k, "n_candidates": c_op, "queries": qs.n, "database": db.n,
                      "l2": "database values + records 0.9 GB > 126 MB L2",
                      "parallelism": f"{world} independent replica(s)"}

@@ -394,7 +394,8 @@ twed_status_t twed_allpairs_host_f32(twed_handle_t handle, const float* a_vals,
  * (group_size (group_size-1) / 2) series.  sigma = mean label.  Each Adam
  * step (beta 0.9 / 0.999, eps 1e-8, cosine-decayed learning rate) minimises
  * the mean squared error of the model over the pairs of `groups_per_step`
- * groups.  With mine_fraction f > 0, (1-f) train_pairs come from random
+ * groups (with rel_floor > 0, the mean squared relative error: each
+ * residual divided by label / sigma + rel_floor).  With mine_fraction f > 0, (1-f) train_pairs come from random
  * groups, used alone for the first half of the epochs; then the database is
  * embedded and f train_pairs come from mined groups -- a seeded anchor and
  * the group_size-1 series nearest to it under the current model -- labelled
@@ -409,6 +410,8 @@ typedef struct {
     float lr;             /* peak learning rate (default 2e-3) */
     uint64_t seed;        /* group sampling and weight initialisation (default 1) */
     float mine_fraction;  /* share of train_pairs from mined groups, [0, 1) (default 0) */
+    float rel_floor;      /* 0: squared error; > 0: squared relative error, each pair's
+                             residual divided by (label / sigma + rel_floor) (default 0) */
 } twed_knn_config_t;
 
 typedef struct {

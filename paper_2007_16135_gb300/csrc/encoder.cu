@@ -436,17 +436,20 @@ pool_kernel(const float* __restrict__ H3, const int64_t* __restrict__ base, floa
 }
 
 // One block per group of G series (batch series gi*G .. gi*G + G - 1):
-// r_ab = |psi_a - psi_b|^2 + z_a + z_b - y_ab * inv_sigma for a < b,
-// de[a] = inv_npairs * sum_b 2 r_ab * d(model)/d e_a, dpooled[a] = Wl^T de[a],
-// gloss[gi] = sum r_ab^2.
+// r_ab = |psi_a - psi_b|^2 + z_a + z_b - y_ab * inv_sigma for a < b, weight
+// w_ab = 1 (rel_floor = 0) or 1 / (y_ab * inv_sigma + rel_floor)^2 (a relative
+// error, which weighs near pairs as much as far ones),
+// de[a] = inv_npairs * sum_b 2 w_ab r_ab * d(model)/d e_a, dpooled[a] = Wl^T de[a],
+// gloss[gi] = sum w_ab r_ab^2.
 constexpr int kMaxGroup = 64;
 __global__ void __launch_bounds__(256)
 group_loss_kernel(const float* __restrict__ emb, int gsize, const int64_t* __restrict__ gids,
                   const float* __restrict__ labels, const float* __restrict__ inv_sigma,
-                  float inv_npairs, const float* __restrict__ Wl, float* __restrict__ de,
+                  float inv_npairs, float rel_floor, const float* __restrict__ Wl, float* __restrict__ de,
                   float* __restrict__ dpooled, float* __restrict__ gloss) {
     __shared__ float e[kMaxGroup][EMB + 1];
-    __shared__ float r[kMaxGroup][kMaxGroup];
+    __shared__ float r[kMaxGroup][kMaxGroup];  // w_ab r_ab
+    __shared__ float wsum[8];
     __shared__ float dE[kMaxGroup][EMB + 1];
     const int G = gsize;
     const int64_t gi = blockIdx.x;
@@ -456,6 +459,7 @@ group_loss_kernel(const float* __restrict__ emb, int gsize, const int64_t* __res
     const float isg = *inv_sigma;
     for (int i = threadIdx.x; i < G * EMB; i += blockDim.x) e[i / EMB][i % EMB] = emb[(s0 + i / EMB) * EMB + i % EMB];
     __syncthreads();
+    float lacc = 0.f;
     for (int q = threadIdx.x; q < npg; q += blockDim.x) {
         // invert the row-major triangle index q -> (a, b), a < b
         int a = 0, rem = q;
@@ -469,9 +473,16 @@ group_loss_kernel(const float* __restrict__ emb, int gsize, const int64_t* __res
             const float d = e[a][j] - e[b][j];
             d2 = fmaf(d, d, d2);
         }
-        const float rv = (d2 + e[a][PSI] + e[b][PSI]) - lab[q] * isg;
-        r[a][b] = rv;
-        r[b][a] = rv;
+        const float y = lab[q] * isg;
+        const float rv = (d2 + e[a][PSI] + e[b][PSI]) - y;
+        float w = 1.f;
+        if (rel_floor > 0.f) {
+            const float iy = 1.f / (y + rel_floor);
+            w = iy * iy;
+        }
+        lacc = fmaf(w * rv, rv, lacc);
+        r[a][b] = w * rv;
+        r[b][a] = w * rv;
     }
     __syncthreads();
     for (int i = threadIdx.x; i < G * EMB; i += blockDim.x) {
@@ -492,14 +503,13 @@ group_loss_kernel(const float* __restrict__ emb, int gsize, const int64_t* __res
         for (int j = 0; j < EMB; ++j) acc = fmaf(Wl[j * CH + c], dE[a][j], acc);
         dpooled[(s0 + a) * CH + c] = acc;
     }
-    if (threadIdx.x < 32) {
+    for (int o = 16; o > 0; o >>= 1) lacc += __shfl_down_sync(0xffffffffu, lacc, o);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = lacc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
         float acc = 0.f;
-        for (int q = threadIdx.x; q < G * G; q += 32) {
-            const int a = q / G, b = q % G;
-            if (a < b) acc = fmaf(r[a][b], r[a][b], acc);
-        }
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-        if (threadIdx.x == 0) gloss[gi] = acc;
+        for (int w = 0; w < 8; ++w) acc += wsum[w];
+        gloss[gi] = acc;
     }
 }
 
@@ -970,11 +980,11 @@ cudaError_t pool_forward(const float* H3, const int64_t* base, int64_t nser, flo
 }
 
 cudaError_t group_loss(const float* emb, int64_t ngroups, int gsize, const int64_t* gids,
-                       const float* labels, const float* inv_sigma, float inv_npairs,
+                       const float* labels, const float* inv_sigma, float inv_npairs, float rel_floor,
                        const float* Wl, float* de, float* dpooled, float* gloss, cudaStream_t st) {
     if (gsize < 2 || gsize > kMaxGroup) return cudaErrorInvalidValue;
     group_loss_kernel<<<(unsigned)ngroups, 256, 0, st>>>(emb, gsize, gids, labels, inv_sigma,
-                                                         inv_npairs, Wl, de, dpooled, gloss);
+                                                         inv_npairs, rel_floor, Wl, de, dpooled, gloss);
     return cudaGetLastError();
 }
 

@@ -77,7 +77,7 @@ cudaError_t pool_forward(const float* H3, const int64_t* base, int64_t nser, flo
                          const float* Wl, const float* bl, float* pooled, float* emb,
                          cudaStream_t st);
 cudaError_t group_loss(const float* emb, int64_t ngroups, int gsize, const int64_t* gids,
-                       const float* labels, const float* inv_sigma, float inv_npairs,
+                       const float* labels, const float* inv_sigma, float inv_npairs, float rel_floor,
                        const float* Wl, float* de, float* dpooled, float* gloss, cudaStream_t st);
 cudaError_t pool_backward(const float* H3, const int32_t* rseries, const float* dpooled,
                           float inv_mean_len, int64_t P, float* dPre, cudaStream_t st);

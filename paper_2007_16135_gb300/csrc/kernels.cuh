@@ -10,6 +10,7 @@
 
 #include "engine.cuh"
 #include "engine_f32.cuh"
+#include "engine_wide.cuh"
 
 namespace twed {
 
@@ -259,13 +260,36 @@ __device__ __forceinline__ void triangle_pos(int64_t w, int64_t n, int64_t& p, i
     q = w - r * (2 * n - r - 1) / 2 + r + 1;
 }
 
-template <typename T, int DIM, int P, int RMAX>
+// Shared memory per warp of the many-pairs kernel (WD > 0: the wide-point
+// strips of engine_wide.cuh).
+template <typename T, int DIM, int WD>
+__host__ __device__ constexpr int pairs_smem_per_warp() {
+    if constexpr (WD > 0) return wide_bytes_per_warp<WD>();
+    else return smem_per_warp<T, DIM>();
+}
+
+template <typename T, int DIM, int P, int R, int WD>
+__device__ __forceinline__ void pairs_strip(const PairRef<T>& pr, int r0, int rows, const StripIO<T>& io,
+                                            const SyncCtl& sc, T* o1, T* o2, unsigned char* wsmem) {
+    if constexpr (WD > 0) {
+        (void)sc;
+        float* ring = reinterpret_cast<float*>(wsmem);
+        float2* bring = reinterpret_cast<float2*>(wsmem + kWideRing * wide_rec_floats<WD>() * 4);
+        run_strip_wide<WD, R>(pr, r0, rows, io, o1, o2, ring, bring);
+    } else {
+        strip_call<T, DIM, P, R>(pr, r0, rows, io, sc, o1, o2, wsmem);
+    }
+}
+
+// WD > 0: FP32 points of WD components, p = 2 (DIM = 0: the records hold
+// (t, delete cost) only and the points are read from the values).
+template <typename T, int DIM, int P, int RMAX, int WD = 0>
 __global__ void __launch_bounds__(128, TWED_PAIRS_MIN_BLOCKS) pairs_kernel(PairsArgs<T> a) {
     using V2 = typename Pair2<T>::V;
     // packed row pairs need an even number of rows per lane
     constexpr bool kEven = kStaged<T, DIM> && P == 2 && DIM >= 2;
     extern __shared__ __align__(16) unsigned char dyn_smem[];
-    unsigned char* wsmem = dyn_smem + (threadIdx.x >> 5) * smem_per_warp<T, DIM>();
+    unsigned char* wsmem = dyn_smem + (threadIdx.x >> 5) * pairs_smem_per_warp<T, DIM, WD>();
     const int lane = threadIdx.x & 31;
     const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     V2* row = reinterpret_cast<V2*>(a.scratch) + gw * a.scratch_cols;
@@ -344,14 +368,14 @@ __global__ void __launch_bounds__(128, TWED_PAIRS_MIN_BLOCKS) pairs_kernel(Pairs
             StripIO<T> io = strip_io_global<T>(r0 == 1 ? nullptr : row, nullptr,
                                                last ? nullptr : row, nullptr, true);
             switch (R) {
-                case 1: if constexpr (!kEven) strip_call<T, DIM, P, 1>(pr, r0, rows, io, a.sc, o1, o2, wsmem); break;
-                case 2: if constexpr (RMAX >= 2) strip_call<T, DIM, P, 2>(pr, r0, rows, io, a.sc, o1, o2, wsmem); break;
-                case 3: if constexpr (RMAX >= 3 && !kEven) strip_call<T, DIM, P, 3>(pr, r0, rows, io, a.sc, o1, o2, wsmem); break;
-                case 4: if constexpr (RMAX >= 4) strip_call<T, DIM, P, 4>(pr, r0, rows, io, a.sc, o1, o2, wsmem); break;
-                case 5: if constexpr (RMAX >= 5 && !kEven) strip_call<T, DIM, P, 5>(pr, r0, rows, io, a.sc, o1, o2, wsmem); break;
-                case 6: if constexpr (RMAX >= 6) strip_call<T, DIM, P, 6>(pr, r0, rows, io, a.sc, o1, o2, wsmem); break;
-                case 7: if constexpr (RMAX >= 7 && !kEven) strip_call<T, DIM, P, 7>(pr, r0, rows, io, a.sc, o1, o2, wsmem); break;
-                case 8: if constexpr (RMAX >= 8) strip_call<T, DIM, P, 8>(pr, r0, rows, io, a.sc, o1, o2, wsmem); break;
+                case 1: if constexpr (!kEven) pairs_strip<T, DIM, P, 1, WD>(pr, r0, rows, io, a.sc, o1, o2, wsmem); break;
+                case 2: if constexpr (RMAX >= 2) pairs_strip<T, DIM, P, 2, WD>(pr, r0, rows, io, a.sc, o1, o2, wsmem); break;
+                case 3: if constexpr (RMAX >= 3 && !kEven) pairs_strip<T, DIM, P, 3, WD>(pr, r0, rows, io, a.sc, o1, o2, wsmem); break;
+                case 4: if constexpr (RMAX >= 4) pairs_strip<T, DIM, P, 4, WD>(pr, r0, rows, io, a.sc, o1, o2, wsmem); break;
+                case 5: if constexpr (RMAX >= 5 && !kEven) pairs_strip<T, DIM, P, 5, WD>(pr, r0, rows, io, a.sc, o1, o2, wsmem); break;
+                case 6: if constexpr (RMAX >= 6) pairs_strip<T, DIM, P, 6, WD>(pr, r0, rows, io, a.sc, o1, o2, wsmem); break;
+                case 7: if constexpr (RMAX >= 7 && !kEven) pairs_strip<T, DIM, P, 7, WD>(pr, r0, rows, io, a.sc, o1, o2, wsmem); break;
+                case 8: if constexpr (RMAX >= 8) pairs_strip<T, DIM, P, 8, WD>(pr, r0, rows, io, a.sc, o1, o2, wsmem); break;
                 default: break;
             }
             r0 += rows;
@@ -440,10 +464,24 @@ int blocks_per_sm(K kernel, int smem_warp, int threads) {
     return nb;
 }
 
+// Wide FP32 points with compiled many-pairs strips: dims 16, 28 and 64 at
+// p = 2 (other wide dims run the run-time-dimension kernels).
+#define TWED_WIDE_DISPATCH(dim, p, BODY)                                        \
+    (((p) == 2 && (dim) == 16)   ? ([&] { constexpr int WD_ = 16; BODY; }(), true) \
+     : ((p) == 2 && (dim) == 28) ? ([&] { constexpr int WD_ = 28; BODY; }(), true) \
+     : ((p) == 2 && (dim) == 64) ? ([&] { constexpr int WD_ = 64; BODY; }(), true) \
+                                 : false)
+
 template <typename T, int RMAX_LIMIT>
 cudaError_t launch_pairs_t(const PairsArgs<T>& a, int blocks, int threads, cudaStream_t st) {
     if (a.npairs <= 0) return cudaSuccess;
     cudaError_t e = cudaSuccess;
+    if constexpr (sizeof(T) == 4) {
+        if (TWED_WIDE_DISPATCH(a.dim, a.p,
+                               (e = launch_with_smem(pairs_kernel<T, 0, 2, wide_rmax<WD_>(), WD_>,
+                                                     wide_bytes_per_warp<WD_>(), blocks, threads, st, a))))
+            return e;
+    }
     TWED_DISPATCH(a.dim, a.p, (e = launch_with_smem(pairs_kernel<T, DIM_, P_, RMAX_LIMIT>,
                                                     smem_per_warp<T, DIM_>(), blocks, threads, st, a)));
     return e;
@@ -452,6 +490,11 @@ cudaError_t launch_pairs_t(const PairsArgs<T>& a, int blocks, int threads, cudaS
 template <typename T, int RMAX_LIMIT>
 int pairs_blocks_per_sm_t(int dim, int p, int threads) {
     int nb = 0;
+    if constexpr (sizeof(T) == 4) {
+        if (TWED_WIDE_DISPATCH(dim, p, (nb = blocks_per_sm(pairs_kernel<T, 0, 2, wide_rmax<WD_>(), WD_>,
+                                                           wide_bytes_per_warp<WD_>(), threads))))
+            return nb;
+    }
     TWED_DISPATCH(dim, p, (nb = blocks_per_sm(pairs_kernel<T, DIM_, P_, RMAX_LIMIT>,
                                               smem_per_warp<T, DIM_>(), threads)));
     return nb;

@@ -118,6 +118,7 @@ struct Encoder {
     twed_handle_t h = nullptr;
     int dim = 0, p = 2, cin = 8, sms = 0;
     float nu = 1.f, lambda = 1.f;
+    float rel_floor = 0.f;  // loss weighting (twed_knn_config_t::rel_floor)
     Layout L;
     int conv_grid = 0, conv_in_grid = 0, wg_grid64 = 0, wg_grid_in = 0;
     DevBuf x0, rser, h1, h2, h3, da, db, part, wv, pooled, emb, de, dpooled, gloss, meta;
@@ -256,7 +257,7 @@ struct Encoder {
         if (s != TWED_OK) return s;
         const int64_t npairs = ngroups * (int64_t)gsize * (gsize - 1) / 2;
         KNN_CUDA(h, group_loss(emb.as<float>(), ngroups, gsize, d_gids, d_labels, d_inv_sigma,
-                               (float)(1.0 / (double)npairs), d_params + L.wl, de.as<float>(),
+                               (float)(1.0 / (double)npairs), rel_floor, d_params + L.wl, de.as<float>(),
                                dpooled.as<float>(), gloss.as<float>(), st));
         KNN_CUDA(h, sum_scaled(gloss.as<float>(), ngroups, 1.0 / (double)npairs, d_loss, st));
         const WeightViews w = views();
@@ -420,6 +421,7 @@ extern "C" void twed_knn_config_default(twed_knn_config_t* c) {
     c->lr = 2e-3f;
     c->seed = 1;
     c->mine_fraction = 0.0f;
+    c->rel_floor = 0.0f;
 }
 
 extern "C" twed_status_t twed_knn_create(twed_handle_t h, const twed_set_f32_t* db, int dim,
@@ -437,7 +439,7 @@ extern "C" twed_status_t twed_knn_create(twed_handle_t h, const twed_set_f32_t* 
     if (c.group_size < 2 || c.group_size > 64 || c.group_size > db->n)
         return err(h, TWED_ERR_INVALID_ARG, "group_size must be in [2, min(64, ndb)]");
     if (c.groups_per_step < 1 || c.epochs < 0 || c.train_pairs < 1 || !(c.lr > 0.f) ||
-        !(c.mine_fraction >= 0.f && c.mine_fraction < 1.f))
+        !(c.mine_fraction >= 0.f && c.mine_fraction < 1.f) || !(c.rel_floor >= 0.f && c.rel_floor < 1e30f))
         return err(h, TWED_ERR_INVALID_ARG, "bad training configuration");
     twed_knn_t k = new (std::nothrow) twed_knn_s();
     if (!k) return err(h, TWED_ERR_ALLOC, "index");
@@ -592,6 +594,7 @@ twed_status_t run_epochs(twed_knn_t k, const std::vector<int64_t>& members, int 
     KNN_CUDA(h, cudaMemcpyAsync(d_sgid, sgid.data(), sizeof(int64_t) * sgid.size(), cudaMemcpyHostToDevice, st));
     twed_status_t s = k->enc.reserve(max_rows, max_ng * G, max_ng, true);
     if (s != TWED_OK) return s;
+    k->enc.rel_floor = k->cfg.rel_floor;
     const float inv_mean_len = (float)(1.0 / k->mean_len);
     const double b1 = 0.9, b2 = 0.999;
     float* sc = k->scalars.as<float>();

@@ -623,7 +623,8 @@ def twed_allpairs_host_f32(a_vals, a_ts, a_offs, b=None, nu=1.0, lam=1.0, p=2,
 class KnnConfig(ctypes.Structure):
     _fields_ = [("group_size", ctypes.c_int), ("groups_per_step", ctypes.c_int),
                 ("epochs", ctypes.c_int), ("train_pairs", ctypes.c_int64), ("lr", ctypes.c_float),
-                ("seed", ctypes.c_uint64), ("mine_fraction", ctypes.c_float)]
+                ("seed", ctypes.c_uint64), ("mine_fraction", ctypes.c_float),
+                ("rel_floor", ctypes.c_float)]
 
 
 class KnnStats(ctypes.Structure):
