@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["w3", "w4", "w2", "w1", "w5", "u1", "u2", "path", "lcs", "dtw"],
+    ap.add_argument("--workload", choices=["w3", "w4", "w2", "w1", "w5", "u1", "u2", "u3", "path", "lcs", "dtw"],
                     default="w3")
     ap.add_argument("--no-knn", action="store_true", help="w3: skip the appended w5 result")
     ap.add_argument("--no-extra", action="store_true",
@@ -807,6 +807,128 @@ def bench_dp(args, rank, world, dev, which=("path", "lcs", "dtw"), steps=5, warm
     return out
 
 
+def bench_mnist(args, rank, world, dev):
+    """Lines with the shapes of the paper's digit-image validation runs
+    (workload 9, synthetic stand-in): one query image against a 60,000-image
+    database, and a sampled block of the 60k x 60k all-pairs matrix (its
+    whole-matrix time extrapolated from the block's cells per second), at
+    28 points in R^28, FP64 like the paper's table; the block also in FP32.
+    Oracle parity on sampled pairs of each."""
+    import torch
+
+    import oracle
+    from paper_2007_16135_gb300 import twed
+    from paper_2007_16135_gb300 import workloads as W
+
+    nu, lam, p = 1.0, 1.0, 2
+    db = W.set_u3(60_000, stream=1 if rank == 0 else 20 + rank)
+    qs = W.set_u3(16, stream=0 if rank == 0 else 10 + rank)
+    rng = W.rng_for(9, 2)
+    nb = 2048
+    rows = np.sort(rng.choice(db.n, nb, replace=False))
+    cols = np.sort(rng.choice(db.n, nb, replace=False))
+    out = {}
+
+    def sub(S, ids):
+        return W.pack([S.series(int(i)) for i in ids])
+
+    def timed(plan, outp, steps, warmup):
+        stream = torch.cuda.current_stream()
+        for _ in range(warmup):
+            plan.execute(outp, stream)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(torch.cuda.current_device()) as clk:
+            barrier(world)
+            ev0.record(stream)
+            for _ in range(steps):
+                plan.execute(outp, stream)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            barrier(world)
+        plan.status()
+        return max_over_ranks(ev0.elapsed_time(ev1), world, dev) / steps, clk.summary()
+
+    def roof(cells, ms, dtype, kernel):
+        props = torch.cuda.get_device_properties(dev)
+        sm_max = float(measured_peaks().get("sm_max_mhz", FALLBACK_SM_MAX_MHZ))
+        lanes = FP64_LANES_PER_SM if dtype == "f64" else FP32_LANES_PER_SM
+        peak = props.multi_processor_count * lanes * sm_max * 1e6
+        mp = twed.pipe_peak(twed.PEAK_DFMA64) if dtype == "f64" else ffma_peak()
+        opc = ops_per_cell(28, p)
+        ach = cells * opc / (ms / 1e3)
+        return {"bound": "alu", "achieved": ach / 1e12, "peak": peak / 1e12, "unit": "Top/s", "frac": ach / peak,
+                "traffic": None, "ops_per_cell": opc, "kernel": kernel,
+                "peak_basis": f"{props.multi_processor_count} SMs x {lanes} {dtype.upper()} lanes x {sm_max:.0f} MHz",
+                "peak_measured": mp / 1e12, "frac_of_measured": ach / mp}
+
+    def parity(M, SA, SB, pairs, dtype):
+        got = M[pairs[:, 0], pairs[:, 1]].astype(np.float64)
+        cast = (lambda S: S.astype(np.float32).astype(np.float64)) if dtype == "f32" else (lambda S: S)
+        ref = oracle.twed_pairs(cast(SA).as_tuple(), cast(SB).as_tuple(), pairs, nu, lam, p)
+        r = np.abs(got - ref) / np.maximum(np.abs(ref), 1e-300)
+        return {"max_rel": float(r.max()), "bitwise_equal": int((got == ref).sum()), "pairs": int(len(pairs)),
+                "bound": 1e-12 if dtype == "f64" else 1e-5}
+
+    # ---- one query against the database (FP64)
+    q = sub(qs, [0])
+    Q = twed.DeviceSet.from_numpy(q.vals, q.ts, q.offs, torch.float64, device=dev)
+    DBd = twed.DeviceSet.from_numpy(db.vals, db.ts, db.offs, torch.float64, device=dev)
+    plan = twed.Plan(Q, DBd, nu, lam, p)
+    outp = plan.new_output()
+    ms, clk = timed(plan, outp, 20, 3)
+    res = {"value": plan.cells * world / (ms / 1e3) / 1e9, "unit": "GCUPS", "ms_per_step": ms,
+           "cells_per_step": plan.cells, "dtype": "f64", "clocks": clk, "gpu_launches": 3 * 20,
+           "result": {"seconds_per_query": ms / 1e3, "paper_seconds_per_query_other_gpu": 0.20},
+           "roofline": roof(plan.cells, ms, "f64", "pairs_kernel<double,0,0,R> (run-time dimension)"),
+           "config": {"workload": "u3 single query: 1 x 60,000 synthetic 28 x 28 stroke images, rows as 28 "
+                                  "points in R^28 (the shape of the paper's digit-image query), t_i=i, "
+                                  "nu=lambda=1, p=2, FP64", "pairs": plan.pairs,
+                      "l2": "database 376 MB > 126 MB L2"}}
+    if rank == 0 and not args.no_cpu:
+        M = outp.cpu().numpy()
+        k = 2000
+        ids = np.arange(k)
+        t0 = time.perf_counter()
+        par = parity(M, q, db, np.stack([np.zeros(k, np.int64), ids], 1), "f64")
+        el = time.perf_counter() - t0
+        res["error_vs_oracle"] = par
+        res["cpu_baseline"] = {"value": k * 784 / el / 1e9, "unit": "GCUPS", "cores": os.cpu_count() or 1,
+                               "kind": "oracle", "sample": f"the query against the first {k} database images "
+                                                           f"({el:.2f} s, FP64 oracle, threads over pairs)"}
+    out["query_f64"] = _extra_line(res, 20, 3)
+    del DBd, plan, outp
+
+    # ---- sampled block of the all-pairs matrix (FP64, then FP32)
+    SA, SB = sub(db, rows), sub(db, cols)
+    for dtype in ("f64", "f32"):
+        td = torch.float64 if dtype == "f64" else torch.float32
+        A = twed.DeviceSet.from_numpy(SA.vals, SA.ts, SA.offs, td, device=dev)
+        B = twed.DeviceSet.from_numpy(SB.vals, SB.ts, SB.offs, td, device=dev)
+        plan = twed.Plan(A, B, nu, lam, p)
+        outp = plan.new_output()
+        steps = 3 if dtype == "f64" else 10
+        ms, clk = timed(plan, outp, steps, 2)
+        gcups = plan.cells * world / (ms / 1e3) / 1e9
+        full_cells = 60_000 * 59_999 // 2 * 784
+        res = {"value": gcups, "unit": "GCUPS", "ms_per_step": ms, "cells_per_step": plan.cells, "dtype": dtype,
+               "clocks": clk, "gpu_launches": 3 * steps,
+               "roofline": roof(plan.cells, ms, dtype, "pairs_kernel<double,0,0,R> (run-time dimension)"
+                                if dtype == "f64" else "pairs_kernel<float,0,2,4,28> (wide dim-28 strips)"),
+               "result": {"extrapolated_all_pairs_seconds": full_cells / (gcups * 1e9),
+                          "all_pairs_cells": full_cells, "paper_all_pairs_hours_other_gpu": "< 2.6"},
+               "config": {"workload": f"u3 block: {nb} x {nb} images sampled from the 60,000 (seeded), 28 "
+                                      f"points in R^28, t_i=i, nu=lambda=1, p=2, {dtype.upper()}; the 60k x 60k "
+                                      "upper triangle extrapolated from the block's rate", "pairs": plan.pairs,
+                          "l2": "block inputs 25 MB (FP64) fit in L2"}}
+        if rank == 0 and not args.no_cpu:
+            pairs = W.sample_block_pairs(nb, nb, 2000, 9)
+            res["error_vs_oracle"] = parity(outp.cpu().numpy(), SA, SB, pairs, dtype)
+        out[f"block_{dtype}"] = _extra_line(res, steps, 2)
+        del A, B, plan, outp
+    return out
+
+
 def bench_knn(args, rank, world, dev, steps, warmup):
     """Learned k-NN (w5): train the filter on exact labels, time the exact
     batched k-NN (the ground truth), pick the smallest candidate count whose
@@ -1091,6 +1213,8 @@ def main():
             res.update(bench_extra(args, rank, world, dev))
         if args.workload == "w3" and not args.no_dp:
             res["dp"] = bench_dp(args, rank, world, dev)
+        if args.workload == "w3" and not args.no_extra:
+            res["u3"] = bench_mnist(args, rank, world, dev)
         if args.workload == "w3" and not args.no_knn:
             kn = bench_knn(args, rank, world, dev, steps=10, warmup=3)
             res["knn"] = {"metric": "k-NN queries/s at recall@10>=0.99 vs exact batched",
@@ -1102,6 +1226,9 @@ def main():
                           "config": kn["config"]}
     elif args.workload == "w5":
         res = bench_knn(args, rank, world, dev, steps=args.steps, warmup=args.warmup)
+    elif args.workload == "u3":
+        res = bench_mnist(args, rank, world, dev)
+        res = {**res["block_f64"], "u3": res}
     elif args.workload in ("path", "lcs", "dtw"):
         res = bench_dp(args, rank, world, dev, which=(args.workload,), steps=args.steps,
                        warmup=args.warmup)[args.workload]
@@ -1115,7 +1242,7 @@ def main():
                 "config": res["config"]}
         for k in ("roofline", "tensor", "cpu_baseline", "e2e", "gpu_launches", "clocks",
                   "error_vs_oracle", "error_vs_f64_gpu", "kernel_ms", "plan", "cells_per_step", "result",
-                  "knn", "w1", "w2", "w4", "dp"):
+                  "knn", "w1", "w2", "w4", "dp", "u3"):
             if k in res:
                 line[k] = res[k]
         print(json.dumps(line), flush=True)

@@ -28,6 +28,9 @@ Workload numbers:
    100,000 points (sinusoids whose periods drift, plus noise), t_i = i.
 8. symbol sequences for the LCS program: 4096 sequences of i.i.d. uniform
    symbols over an alphabet of 4, lengths U[64, 2048] (the lengths of 3).
+9. stand-in with the shape of the paper's third validation set (handwritten
+   digit images): 28 x 28 images of one random cubic Bezier pen stroke each,
+   read row by row as 28 points in R^28, t_i = i (nu = 1, lambda = 1).
 
 All use p = 2.  The paper's own timing runs used random series of power-of-two
 lengths (section "Basic Methodology and Results"); its UCI and MNIST data are
@@ -235,6 +238,28 @@ def set_u1(nseries: int = 600, length: int = 60, stream: int = 0) -> SeriesSet:
             y += (1 if c == 4 else -1) * rng.uniform(7.5, 20) * (t >= t0)
         out.append((y[:, None], t.copy()))
     return pack(out)
+
+
+def set_u3(nseries: int = 60_000, stream: int = 0, samples: int = 48, pen: float = 1.0) -> SeriesSet:
+    """Workload 9: one pen stroke per 28 x 28 image: a cubic Bezier curve with
+    four control points U[4, 24]^2, sampled at `samples` points, each drawn as
+    a Gaussian blob of width `pen` pixels; intensities clipped to [0, 1].
+    Row r of the image is point r + 1 of the series (28 points in R^28)."""
+    rng = rng_for(9, stream)
+    ctrl = rng.uniform(4.0, 24.0, size=(nseries, 4, 2))
+    u = np.linspace(0.0, 1.0, samples)
+    basis = np.stack([(1 - u) ** 3, 3 * u * (1 - u) ** 2, 3 * u ** 2 * (1 - u), u ** 3], axis=1)  # [S, 4]
+    pts = np.einsum("sk,nkd->nsd", basis, ctrl)  # [n, S, 2] (row, column)
+    grid = np.arange(28, dtype=np.float64)
+    out = np.empty((nseries, 28, 28), dtype=np.float64)
+    for c0 in range(0, nseries, 4096):
+        p = pts[c0:c0 + 4096]
+        gr = np.exp(-0.5 * ((grid[None, None, :] - p[:, :, 0:1]) / pen) ** 2)  # [n, S, 28] rows
+        gc = np.exp(-0.5 * ((grid[None, None, :] - p[:, :, 1:2]) / pen) ** 2)  # [n, S, 28] columns
+        out[c0:c0 + 4096] = np.minimum(np.matmul(gr.transpose(0, 2, 1), gc), 1.0)
+    ts = np.tile(unit_times(28), nseries)
+    offs = np.arange(nseries + 1, dtype=np.int64) * 28
+    return SeriesSet(out.reshape(nseries * 28, 28), ts, offs)
 
 
 def set_u2(nseries: int = 10, length: int = 100_000, stream: int = 0) -> SeriesSet:

@@ -7,6 +7,10 @@
   for n + m > 1e5): within the FP32 bound, 1e-5 relative, of the stored
   FP64 oracle values on the same FP32-rounded inputs (measured: about 1e-6);
   one pair in FP64 bit-identical to the stored oracle value.  Stored values: tests/golden/make_u2_expected.py (oracle only).
+* u3: 28 x 28 stroke images read as 28 points in R^28 (the digit-image set):
+  one query against a database block and a block of all-pairs, FP64 within
+  1e-12 of the oracle (the run-time-dimension FP64 path), FP32 within 1e-5
+  (the compiled dim-28 strips).
 """
 import json
 import os
@@ -64,3 +68,41 @@ def test_u2_pair_f64_bitwise_against_stored_oracle(tw):
     a, ta = S.series(i)
     b, tb = S.series(j)
     assert tw.twed_f64(a, ta, b, tb, 1.0, 1.0, 2) == want
+
+
+def test_u3_generator_shape():
+    S = W.set_u3(50, stream=3)
+    assert S.n == 50 and np.all(S.lengths == 28) and S.vals.shape == (50 * 28, 28)
+    assert S.vals.min() >= 0.0 and S.vals.max() <= 1.0
+    assert np.array_equal(S.ts[:28], np.arange(1.0, 29.0))
+    assert np.array_equal(W.set_u3(50, stream=3).vals, S.vals)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32"])
+def test_u3_block_against_oracle(tw, dtype):
+    import torch
+    SA, SB = W.set_u3(70, stream=0), W.set_u3(90, stream=1)
+    if dtype == "f32":
+        SA, SB = SA.astype(np.float32), SB.astype(np.float32)
+    td = torch.float64 if dtype == "f64" else torch.float32
+    A = tw.DeviceSet.from_numpy(SA.vals, SA.ts, SA.offs, td)
+    B = tw.DeviceSet.from_numpy(SB.vals, SB.ts, SB.offs, td)
+    plan = tw.Plan(A, B, 1.0, 1.0, 2)
+    M = plan.execute().cpu().numpy()
+    plan.status()
+    pairs = np.array([(i, j) for i in range(SA.n) for j in range(SB.n)])
+    want = oracle.twed_pairs(SA.astype(np.float64).as_tuple(), SB.astype(np.float64).as_tuple(), pairs,
+                             1.0, 1.0, 2).reshape(SA.n, SB.n)
+    r = np.abs(M - want) / np.maximum(np.abs(want), 1e-300)
+    assert r.max() <= (1e-12 if dtype == "f64" else 1e-5)
+
+
+def test_u3_single_query_f64(tw):
+    import torch
+    db, q = W.set_u3(3000, stream=1), W.set_u3(1, stream=0)
+    D = tw.DeviceSet.from_numpy(db.vals, db.ts, db.offs, torch.float64)
+    Q = tw.DeviceSet.from_numpy(q.vals, q.ts, q.offs, torch.float64)
+    got = tw.Plan(Q, D, 1.0, 1.0, 2).execute().cpu().numpy()[0]
+    pairs = np.stack([np.zeros(db.n, np.int64), np.arange(db.n)], 1)
+    want = oracle.twed_pairs(q.as_tuple(), db.as_tuple(), pairs, 1.0, 1.0, 2)
+    assert np.max(np.abs(got - want) / want) <= 1e-12
