@@ -551,8 +551,8 @@ namespace {
 
 template <typename S>
 twed_status_t check_set(twed_handle_t h, const S* set, const char* name, int64_t* max_len,
-                        int64_t* total) {
-    if (!set || !set->vals || !set->ts || !set->offs || !set->offs_host)
+                        int64_t* total, bool need_ts = true) {
+    if (!set || !set->vals || (need_ts && !set->ts) || !set->offs || !set->offs_host)
         return fail(h, TWED_ERR_INVALID_ARG, "set %s: null pointer", name);
     if (set->n < 1) return fail(h, TWED_ERR_INVALID_ARG, "set %s: no series", name);
     if (set->offs_host[0] != 0) return fail(h, TWED_ERR_INVALID_ARG, "set %s: offs[0] != 0", name);
@@ -1272,7 +1272,8 @@ namespace {
 template <typename T, typename S>
 twed_status_t batch_impl(twed_handle_t h, const S* A, const S* B, const int64_t* d_pairs,
                          int64_t npairs, int dim, T nu, T lambda, int p, T* d_out, void* stream,
-                         int order_mode = TWED_ORDER_LIST, int rmax = 0, int per_sm_req = 0) {
+                         int order_mode = TWED_ORDER_LIST, int rmax = 0, int per_sm_req = 0,
+                         bool dtw = false) {
     if (!h) return TWED_ERR_INVALID_ARG;
     if (npairs < 0) return fail(h, TWED_ERR_INVALID_ARG, "npairs < 0");
     if (order_mode != TWED_ORDER_LIST && order_mode != TWED_ORDER_LONGEST_FIRST)
@@ -1282,8 +1283,8 @@ twed_status_t batch_impl(twed_handle_t h, const S* A, const S* B, const int64_t*
     twed_status_t s = check_params<T>(h, 1, 1, dim, nu, lambda, p);
     if (s != TWED_OK) return s;
     int64_t maxa, tota, maxb, totb;
-    if ((s = check_set(h, A, "A", &maxa, &tota)) != TWED_OK) return s;
-    if ((s = check_set(h, B, "B", &maxb, &totb)) != TWED_OK) return s;
+    if ((s = check_set(h, A, "A", &maxa, &tota, !dtw)) != TWED_OK) return s;
+    if ((s = check_set(h, B, "B", &maxb, &totb, !dtw)) != TWED_OK) return s;
     const bool same = (A->vals == B->vals && A->offs == B->offs && A->ts == B->ts);
     const int rl = twed::rec_len<T>(dim, p);
     const int threads = 128;
@@ -1336,6 +1337,7 @@ twed_status_t batch_impl(twed_handle_t h, const S* A, const S* B, const int64_t*
     pa.scratch = base + o_scr;
     pa.scratch_cols = scols;
     pa.sc = make_sync(h, nullptr);
+    pa.dtw = dtw ? 1 : 0;
     if (order) {
         int64_t* ord = (int64_t*)(base + o_ord);
         TWED_CUDA(h, twed::launch_order_pairs(d_pairs, npairs, A->offs, B->offs, ord,
@@ -1356,6 +1358,12 @@ twed_status_t batch_f32_shaped(twed_handle_t h, const twed_set_f32_t* A, const t
                                int rmax, int per_sm) {
     return batch_impl<float>(h, A, B, d_pairs, npairs, dim, nu, lambda, p, d_out, stream, order,
                              rmax, per_sm);
+}
+twed_status_t dtw_batch_f32_staged(twed_handle_t h, const twed_set_f32_t* A, const twed_set_f32_t* B,
+                                   const int64_t* d_pairs, int64_t npairs, int dim, int p, float* d_out,
+                                   void* stream) {
+    return batch_impl<float>(h, A, B, d_pairs, npairs, dim, 0.f, 0.f, p, d_out, stream,
+                             TWED_ORDER_LONGEST_FIRST, 0, 0, true);
 }
 int batch_f32_max_blocks_per_sm(int dim, int p) {
     return std::max(1, twed::pairs_blocks_per_sm<float>(dim, p, 128));

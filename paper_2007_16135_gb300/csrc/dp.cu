@@ -624,6 +624,12 @@ twed_status_t dtw_batch_impl(twed_handle_t h, const S* A, const S* B, const int6
     int64_t maxa, tota, maxb, totb;
     if (!good_set(A, &maxa, &tota) || !good_set(B, &maxb, &totb))
         return err(h, TWED_ERR_INVALID_ARG, "bad set (null pointer, empty series or offs[0] != 0)");
+    if constexpr (sizeof(T) == 4) {
+        // FP32 with a compiled point layout: the staged engine's DTW mode
+        // (column ring, packed rows); other cases run the generic strips here
+        if (twed::compiled_layout(dim, p))
+            return twed::detail::dtw_batch_f32_staged(h, A, B, d_pairs, npairs, dim, p, d_out, stream);
+    }
     const int sms = twed::detail::handle_sms(h);
     int blocks = 0;
     TWED_DP_DISPATCH(dim, p, (blocks = grid_for(twed::dp::dtw_pairs_kernel<T, DIM_, P_, kDtwR>, npairs, sms)));

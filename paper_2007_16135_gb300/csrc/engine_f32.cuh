@@ -98,7 +98,12 @@ constexpr float kBig = 1.2676506e30f;  // 2^100
 // areas (kRingCols records, kRingCols boundary entries).  Boundary rows hold
 // (D, c) float2 per column, or (D_hi, D_lo, c, 0) float4 when KH; `io.up`
 // must have at least m+1 readable entries (a staged copy may read one past m).
-template <int DIM, int P, int R, bool KH = false, int kStepBlock = kStepBlockPairs>
+// DTW = true runs dynamic time warping on the same strips instead (the
+// related distance of the paper's introduction): the cell cost is d(a_i,
+// b_j) alone and D(i,j) = d + min(D(i-1,j), D(i,j-1), D(i-1,j-1)); times,
+// delete costs and the hand-off of c are not used (many-pairs schedule, no
+// compensation).
+template <int DIM, int P, int R, bool KH = false, int kStepBlock = kStepBlockPairs, bool DTW = false>
 __device__ __forceinline__ bool run_strip_staged(const PairRef<float>& pr, int r0, int rows,
                                                  const StripIO<float>& io, const SyncCtl& sc,
                                                  float* result_a, float* result_b, float* ring,
@@ -267,8 +272,13 @@ __device__ __forceinline__ bool run_strip_staged(const PairRef<float>& pr, int r
                 }
                 float s0, s1;
                 f2_unpack(s2, s0, s1);
-                cn[2 * q] = fmaf(pr.nu, fabsf(rt[2 * q] - tbn), Arith<float>::root(s0));
-                cn[2 * q + 1] = fmaf(pr.nu, fabsf(rt[2 * q + 1] - tbn), Arith<float>::root(s1));
+                if constexpr (DTW) {
+                    cn[2 * q] = Arith<float>::root(s0);
+                    cn[2 * q + 1] = Arith<float>::root(s1);
+                } else {
+                    cn[2 * q] = fmaf(pr.nu, fabsf(rt[2 * q] - tbn), Arith<float>::root(s0));
+                    cn[2 * q + 1] = fmaf(pr.nu, fabsf(rt[2 * q + 1] - tbn), Arith<float>::root(s1));
+                }
             }
         } else {
             float bv[DIM];
@@ -276,7 +286,8 @@ __device__ __forceinline__ bool run_strip_staged(const PairRef<float>& pr, int r
             for (int k = 0; k < DIM; ++k) bv[k] = recn[2 * k];
 #pragma unroll
             for (int r = 0; r < R; ++r)
-                cn[r] = fmaf(pr.nu, fabsf(rt[r] - tbn), dist<float, DIM, P>(ra[r], bv, DIM, pr.p));
+                cn[r] = DTW ? dist<float, DIM, P>(ra[r], bv, DIM, pr.p)
+                            : fmaf(pr.nu, fabsf(rt[r] - tbn), dist<float, DIM, P>(ra[r], bv, DIM, pr.p));
         }
     };
     prefetch_load(1 - lane);
@@ -346,11 +357,12 @@ __device__ __forceinline__ bool run_strip_staged(const PairRef<float>& pr, int r
         const float4 bnd = bndn;
         prefetch_load(j + 1);
         float upD = __shfl_up_sync(kFull, botD, 1);
-        float upC = __shfl_up_sync(kFull, botC, 1);
+        float upC = 0.f;
+        if constexpr (!DTW) upC = __shfl_up_sync(kFull, botC, 1);
         float upL = 0.f;
         if constexpr (KH) upL = __shfl_up_sync(kFull, botL, 1);
         upD = lane == 0 ? (first ? INF : bnd.x) : upD;  // D(r0-1, j)
-        upC = lane == 0 ? (first ? 0.f : bnd.z) : upC;  // c(r0-1, j)
+        if constexpr (!DTW) upC = lane == 0 ? (first ? 0.f : bnd.z) : upC;  // c(r0-1, j)
         if constexpr (KH) upL = lane == 0 ? (first ? 0.f : bnd.y) : upL;
         // a lane that has not reached column 1 sees an infinite row above: its
         // state then stays exactly at D(i, 0) = inf, so no branch is needed
@@ -392,6 +404,19 @@ __device__ __forceinline__ bool run_strip_staged(const PairRef<float>& pr, int r
                 Dlo[r] = ul;
                 cp[r] = cc[r];
             }
+        } else if constexpr (DTW) {
+            // min(left, up-left) first (both from the previous column), then
+            // the chain down the lane's rows: D = d + min(up, that)
+            float lm_[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) lm_[r] = fminf(Dl[r], r == 0 ? diagD : Dl[r - 1]);
+            float d_up = upD;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                d_up = cc[r] + fminf(d_up, lm_[r]);
+                Dl[r] = d_up;
+            }
+            (void)delb;
         } else {
             float tb_[R], tm_[R];
 #pragma unroll

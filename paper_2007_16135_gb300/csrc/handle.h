@@ -16,6 +16,11 @@ twed_status_t batch_f32_shaped(twed_handle_t h, const twed_set_f32_t* A, const t
                                float lambda, int p, float* d_out, void* stream, int order,
                                int rmax, int per_sm);
 int batch_f32_max_blocks_per_sm(int dim, int p);
+// DTW of explicit pairs on the staged FP32 engine (compiled point layouts:
+// twed::compiled_layout(dim, p)); timestamps may be NULL.
+twed_status_t dtw_batch_f32_staged(twed_handle_t h, const twed_set_f32_t* A, const twed_set_f32_t* B,
+                                   const int64_t* d_pairs, int64_t npairs, int dim, int p, float* d_out,
+                                   void* stream);
 int batch_f32_rmax_limit();
 // The handle's grow-only device workspace, at least `bytes` long (nullptr
 // and the handle's last error set on failure; a growth synchronizes the

@@ -26,15 +26,16 @@ __host__ __device__ constexpr int smem_per_warp() {
     else return 0;
 }
 
-template <typename T, int DIM, int P, int R, bool KH = false, int SB = kStepBlockPairs>
+template <typename T, int DIM, int P, int R, bool KH = false, int SB = kStepBlockPairs, bool DTW = false>
 __device__ __forceinline__ bool strip_call(const PairRef<T>& pr, int r0, int rows,
                                            const StripIO<T>& io, const SyncCtl& sc, T* o1, T* o2,
                                            unsigned char* wsmem) {
     if constexpr (kStaged<T, DIM>) {
         float* ring = reinterpret_cast<float*>(wsmem);
         void* bring = wsmem + kRingCols * Rec<float, DIM>::kLen * 4;
-        return run_strip_staged<DIM, P, R, KH, SB>(pr, r0, rows, io, sc, o1, o2, ring, bring);
+        return run_strip_staged<DIM, P, R, KH, SB, DTW>(pr, r0, rows, io, sc, o1, o2, ring, bring);
     } else {
+        static_assert(!DTW, "DTW runs on the staged FP32 engine only");
         (void)wsmem;
         return run_strip<T, DIM, P, R>(pr, r0, rows, io, sc, o1, o2);
     }
@@ -60,8 +61,9 @@ __global__ void __launch_bounds__(256) records_kernel(RecordsArgs<T> a) {
             }
             first = (__ldg(a.offs + lo) == g);
         }
-        const T t = a.ts[g];
-        const T tprev = first ? T(0) : a.ts[g - 1];
+        // a set without timestamps (DTW reads none) gives t = 0
+        const T t = a.ts ? a.ts[g] : T(0);
+        const T tprev = (first || !a.ts) ? T(0) : a.ts[g - 1];
         T d;
         T* out = a.rec + g * RL::kLen;
         if constexpr (DIM > 0) {
@@ -268,7 +270,7 @@ __host__ __device__ constexpr int pairs_smem_per_warp() {
     else return smem_per_warp<T, DIM>();
 }
 
-template <typename T, int DIM, int P, int R, int WD>
+template <typename T, int DIM, int P, int R, int WD, bool DTW>
 __device__ __forceinline__ void pairs_strip(const PairRef<T>& pr, int r0, int rows, const StripIO<T>& io,
                                             const SyncCtl& sc, T* o1, T* o2, unsigned char* wsmem) {
     if constexpr (WD > 0) {
@@ -277,13 +279,13 @@ __device__ __forceinline__ void pairs_strip(const PairRef<T>& pr, int r0, int ro
         float2* bring = reinterpret_cast<float2*>(wsmem + kWideRing * wide_rec_floats<WD>() * 4);
         run_strip_wide<WD, R>(pr, r0, rows, io, o1, o2, ring, bring);
     } else {
-        strip_call<T, DIM, P, R>(pr, r0, rows, io, sc, o1, o2, wsmem);
+        strip_call<T, DIM, P, R, false, kStepBlockPairs, DTW>(pr, r0, rows, io, sc, o1, o2, wsmem);
     }
 }
 
 // WD > 0: FP32 points of WD components, p = 2 (DIM = 0: the records hold
 // (t, delete cost) only and the points are read from the values).
-template <typename T, int DIM, int P, int RMAX, int WD = 0>
+template <typename T, int DIM, int P, int RMAX, int WD = 0, bool DTW = false>
 __global__ void __launch_bounds__(128, TWED_PAIRS_MIN_BLOCKS) pairs_kernel(PairsArgs<T> a) {
     using V2 = typename Pair2<T>::V;
     // packed row pairs need an even number of rows per lane
@@ -368,14 +370,14 @@ __global__ void __launch_bounds__(128, TWED_PAIRS_MIN_BLOCKS) pairs_kernel(Pairs
             StripIO<T> io = strip_io_global<T>(r0 == 1 ? nullptr : row, nullptr,
                                                last ? nullptr : row, nullptr, true);
             switch (R) {
-                case 1: if constexpr (!kEven) pairs_strip<T, DIM, P, 1, WD>(pr, r0, rows, io, a.sc, o1, o2, wsmem); break;
-                case 2: if constexpr (RMAX >= 2) pairs_strip<T, DIM, P, 2, WD>(pr, r0, rows, io, a.sc, o1, o2, wsmem); break;
-                case 3: if constexpr (RMAX >= 3 && !kEven) pairs_strip<T, DIM, P, 3, WD>(pr, r0, rows, io, a.sc, o1, o2, wsmem); break;
-                case 4: if constexpr (RMAX >= 4) pairs_strip<T, DIM, P, 4, WD>(pr, r0, rows, io, a.sc, o1, o2, wsmem); break;
-                case 5: if constexpr (RMAX >= 5 && !kEven) pairs_strip<T, DIM, P, 5, WD>(pr, r0, rows, io, a.sc, o1, o2, wsmem); break;
-                case 6: if constexpr (RMAX >= 6) pairs_strip<T, DIM, P, 6, WD>(pr, r0, rows, io, a.sc, o1, o2, wsmem); break;
-                case 7: if constexpr (RMAX >= 7 && !kEven) pairs_strip<T, DIM, P, 7, WD>(pr, r0, rows, io, a.sc, o1, o2, wsmem); break;
-                case 8: if constexpr (RMAX >= 8) pairs_strip<T, DIM, P, 8, WD>(pr, r0, rows, io, a.sc, o1, o2, wsmem); break;
+                case 1: if constexpr (!kEven) pairs_strip<T, DIM, P, 1, WD, DTW>(pr, r0, rows, io, a.sc, o1, o2, wsmem); break;
+                case 2: if constexpr (RMAX >= 2) pairs_strip<T, DIM, P, 2, WD, DTW>(pr, r0, rows, io, a.sc, o1, o2, wsmem); break;
+                case 3: if constexpr (RMAX >= 3 && !kEven) pairs_strip<T, DIM, P, 3, WD, DTW>(pr, r0, rows, io, a.sc, o1, o2, wsmem); break;
+                case 4: if constexpr (RMAX >= 4) pairs_strip<T, DIM, P, 4, WD, DTW>(pr, r0, rows, io, a.sc, o1, o2, wsmem); break;
+                case 5: if constexpr (RMAX >= 5 && !kEven) pairs_strip<T, DIM, P, 5, WD, DTW>(pr, r0, rows, io, a.sc, o1, o2, wsmem); break;
+                case 6: if constexpr (RMAX >= 6) pairs_strip<T, DIM, P, 6, WD, DTW>(pr, r0, rows, io, a.sc, o1, o2, wsmem); break;
+                case 7: if constexpr (RMAX >= 7 && !kEven) pairs_strip<T, DIM, P, 7, WD, DTW>(pr, r0, rows, io, a.sc, o1, o2, wsmem); break;
+                case 8: if constexpr (RMAX >= 8) pairs_strip<T, DIM, P, 8, WD, DTW>(pr, r0, rows, io, a.sc, o1, o2, wsmem); break;
                 default: break;
             }
             r0 += rows;
@@ -476,6 +478,17 @@ template <typename T, int RMAX_LIMIT>
 cudaError_t launch_pairs_t(const PairsArgs<T>& a, int blocks, int threads, cudaStream_t st) {
     if (a.npairs <= 0) return cudaSuccess;
     cudaError_t e = cudaSuccess;
+    if (a.dtw) {
+        // DTW: FP32 compiled point layouts on the staged engine only
+        if constexpr (sizeof(T) == 4) {
+            e = cudaErrorInvalidValue;
+            TWED_DISPATCH(a.dim, a.p, (e = DIM_ > 0 ? launch_with_smem(pairs_kernel<T, (DIM_ > 0 ? DIM_ : 1), (DIM_ > 0 ? P_ : 2), RMAX_LIMIT, 0, true>,
+                                                                      smem_per_warp<T, (DIM_ > 0 ? DIM_ : 1)>(), blocks, threads, st, a)
+                                                     : cudaErrorInvalidValue));
+            return e;
+        }
+        return cudaErrorInvalidValue;
+    }
     if constexpr (sizeof(T) == 4) {
         if (TWED_WIDE_DISPATCH(a.dim, a.p,
                                (e = launch_with_smem(pairs_kernel<T, 0, 2, wide_rmax<WD_>(), WD_>,

@@ -184,3 +184,22 @@ def test_dtw_one_pair_from_host(tw):
     a, b = np.cumsum(rng.normal(size=(400, 2)), 0), np.cumsum(rng.normal(size=(333, 2)), 0)
     assert tw.dtw(a, b, 2) == oracle.dtw(a, b, 2)
     assert tw.dtw(a, a, 1) == 0.0
+
+
+@pytest.mark.parametrize("dim,p", [(1, 2), (2, 1), (2, 2), (4, 2), (5, 2), (8, 1), (8, 2)])
+def test_dtw_batch_f32_staged_layouts(tw, dim, p):
+    # FP32 compiled layouts run DTW on the staged engine: lengths straddle its
+    # 256-row strips and 32-column staging chunks
+    import torch
+    rng = np.random.default_rng(900 + 10 * dim + p)
+    lens = [1, 2, 31, 32, 33, 255, 256, 257, 600] + [int(v) for v in rng.integers(1, 800, 7)]
+    S = walk_set(dim * 3 + p, lens, dim).astype(np.float32)
+    D = tw.DeviceSet.from_numpy(S.vals, S.ts, S.offs, torch.float32)
+    pairs = np.stack([rng.integers(0, S.n, 80), rng.integers(0, S.n, 80)], 1)
+    got = tw.dtw_batch(D, D, torch.as_tensor(pairs).cuda(), p).cpu().numpy().astype(np.float64)
+    tw.default_handle().sync_status()
+    S64 = S.astype(np.float64)
+    want = np.array([oracle.dtw(S64.series(x)[0], S64.series(y)[0], p) for x, y in pairs])
+    same = pairs[:, 0] == pairs[:, 1]
+    assert np.all(got[same] == 0.0)
+    assert np.max(np.abs(got[~same] - want[~same]) / want[~same]) <= 1e-5
