@@ -636,7 +636,7 @@ def _fp32_roof(cells, ms, opc, kernel, dev):
 def bench_dp(args, rank, world, dev, which=("path", "lcs", "dtw"), steps=5, warmup=3):
     """The dynamic programs beside TWED's value, one line each:
     path -- TWED with its optimal edit path (2 choice bits per cell, walk
-            back), FP32, 2048 seeded i<j pairs of the 4096-series dim-8 set;
+            back), FP32, 8192 seeded i<j pairs of the 4096-series dim-8 set;
     lcs  -- LCS lengths of 65,536 seeded i<j pairs of 4096 symbol sequences
             (alphabet 4, lengths U[64, 2048]), L2 flushed before every step;
     dtw  -- DTW (lp point distance, p = 2), FP32, 32,768 seeded i<j pairs of
@@ -665,7 +665,7 @@ def bench_dp(args, rank, world, dev, which=("path", "lcs", "dtw"), steps=5, warm
     if "path" in which:
         S, D = w3()
         nu, lam, p = 0.5, 0.5, 2
-        pairs = W.sample_upper_pairs(S.n, 2048, 3)
+        pairs = W.sample_upper_pairs(S.n, 8192, 3)
         pd = torch.as_tensor(pairs, device=dev)
         bufs = twed.path_batch_buffers(D, D, pd)
         L = S.lengths.astype(np.int64)
@@ -675,8 +675,8 @@ def bench_dp(args, rank, world, dev, which=("path", "lcs", "dtw"), steps=5, warm
         twed.default_handle().sync_status()
         res = {"value": cells * world / (ms / 1e3) / 1e9, "unit": "GCUPS", "ms_per_step": ms,
                "cells_per_step": cells, "dtype": "f32", "clocks": clk, "gpu_launches": 3 * steps,
-               "roofline": _fp32_roof(cells, ms, ops_per_cell(8, p), "path_pairs_kernel<float,8,2,4>", dev),
-               "config": {"workload": "TWED edit paths: 2048 seeded i<j pairs of 4096 dim-8 series, "
+               "roofline": _fp32_roof(cells, ms, ops_per_cell(8, p), "path_staged_kernel<8,2,8>", dev),
+               "config": {"workload": "TWED edit paths: 8192 seeded i<j pairs of 4096 dim-8 series, "
                                       "lengths U[64,2048], FP32, nu=lambda=0.5, p=2",
                           "pairs": len(pairs), "l2": "series records 208 MB > 126 MB L2",
                           "output": "distance + move string per pair (2-bit choices, walk back)"}}
@@ -783,7 +783,7 @@ def bench_dp(args, rank, world, dev, which=("path", "lcs", "dtw"), steps=5, warm
         twed.default_handle().sync_status()
         res = {"value": cells * world / (ms / 1e3) / 1e9, "unit": "GCUPS", "ms_per_step": ms,
                "cells_per_step": cells, "dtype": "f32", "clocks": clk, "gpu_launches": steps,
-               "roofline": _fp32_roof(cells, ms, 2 * 8 + 1, "dtw_pairs_kernel<float,8,2,4>", dev),
+               "roofline": _fp32_roof(cells, ms, 2 * 8 + 1, "pairs_kernel<float,8,2,8,0,true> (staged engine, DTW mode)", dev),
                "config": {"workload": "DTW: 32,768 seeded i<j pairs of 4096 dim-8 series, lengths U[64,2048], "
                                       "FP32, p=2", "pairs": len(pairs),
                           "l2": "series values 139 MB > 126 MB L2"}}

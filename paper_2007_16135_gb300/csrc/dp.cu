@@ -27,6 +27,7 @@
 #include "../../include/twed.h"
 #include "engine.cuh"
 #include "handle.h"
+#include "kernels.cuh"
 #include "launch.h"
 
 namespace twed {
@@ -528,6 +529,162 @@ __global__ void __launch_bounds__(128) path_pairs_kernel(PathArgs<T> a) {
     }
 }
 
+// ------------------------------------------------------------- FP32 paths, staged engine
+// Rows per lane of a strip with `left` rows to go: the rule of the
+// many-pairs kernel (at most RMAX, even when rows are packed in pairs).
+template <int DIM, int P, int RMAX>
+__device__ __forceinline__ int path_rows_per_lane(int left) {
+    constexpr bool kEven = P == 2 && DIM >= 2;
+    int R = left >= 32 * RMAX ? RMAX : (left + 31) / 32;
+    if (kEven) R = min((R + 1) & ~1, RMAX);
+    return R;
+}
+
+// TWED with one optimal edit path, FP32 with a compiled point layout: the
+// staged engine (column ring, packed rows) records the choices in words of
+// 16 steps (run_strip_staged's PATH layout: row i's choice at column j sits
+// at step s + 1 = j + L, L = the lane holding row i in its strip); lane 0
+// walks back from (n,m) and the warp moves the moves to the front.  Pairs
+// keep their orientation (the moves name a and b).
+template <int DIM, int P, int RMAX>
+__global__ void __launch_bounds__(128) path_staged_kernel(PathArgs<float> a) {
+    extern __shared__ __align__(16) unsigned char dyn_smem[];
+    unsigned char* wsmem = dyn_smem + (threadIdx.x >> 5) * smem_per_warp<float, DIM>();
+    const int lane = threadIdx.x & 31;
+    const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    float2* row = reinterpret_cast<float2*>(a.rows + gw * a.row_stride);
+    uint32_t* choice = a.choice + gw * a.choice_stride;
+    constexpr bool kEven = P == 2 && DIM >= 2;
+    while (true) {
+        unsigned long long w = 0;
+        if (lane == 0) w = atomicAdd(a.counter, 1ull);
+        w = __shfl_sync(kFull, w, 0);
+        if ((int64_t)w >= a.npairs) break;
+        int64_t fa = 0, fb = 0;
+        int n = a.n1, m = a.m1;
+        if (a.offs_a != nullptr) {
+            const int64_t x = a.pairs[2 * w], y = a.pairs[2 * w + 1];
+            if ((uint64_t)x >= (uint64_t)a.na || (uint64_t)y >= (uint64_t)a.nb) {
+                if (lane == 0) {
+                    a.dist[w] = __int_as_float(0x7fc00000);
+                    a.len[w] = -1;
+                    atomicCAS(a.sc.err, 0u, 1u);
+                    atomicCAS(a.sc.sticky, 0u, 1u);
+                }
+                continue;
+            }
+            fa = a.offs_a[x];
+            fb = a.offs_b[y];
+            n = (int)(a.offs_a[x + 1] - fa);
+            m = (int)(a.offs_b[y + 1] - fb);
+        }
+        PairRef<float> pr;
+        pr.rec_a = a.rec_a;
+        pr.rec_b = a.rec_b;
+        pr.vals_a = a.vals_a;
+        pr.vals_b = a.vals_b;
+        pr.a_first = fa;
+        pr.b_first = fb;
+        pr.n = n;
+        pr.m = m;
+        pr.dim = a.dim;
+        pr.p = a.p;
+        pr.nu = a.nu;
+        for (int r0 = 1; r0 <= n;) {
+            const int R = path_rows_per_lane<DIM, P, RMAX>(n - r0 + 1);
+            const int rows = min(n - r0 + 1, 32 * R);
+            const bool last = r0 + rows > n;
+            const StripIO<float> io =
+                strip_io_global<float>(r0 == 1 ? nullptr : row, nullptr, last ? nullptr : row, nullptr, true);
+            float* o1 = a.dist + w;
+            switch (R) {
+#define TWED_PATH_STRIP(RR)                                                                                  \
+    case RR:                                                                                                 \
+        if constexpr (RR <= RMAX && (!kEven || (RR % 2) == 0))                                               \
+            strip_call<float, DIM, P, RR, false, kStepBlockPairs, false, true>(pr, r0, rows, io, a.sc, o1,   \
+                                                                               nullptr, wsmem, choice, a.wpr); \
+        break;
+                TWED_PATH_STRIP(1)
+                TWED_PATH_STRIP(2)
+                TWED_PATH_STRIP(3)
+                TWED_PATH_STRIP(4)
+                TWED_PATH_STRIP(5)
+                TWED_PATH_STRIP(6)
+                TWED_PATH_STRIP(7)
+                TWED_PATH_STRIP(8)
+#undef TWED_PATH_STRIP
+                default: break;
+            }
+            r0 += rows;
+            __syncwarp();
+        }
+        __syncwarp();
+        __threadfence_block();
+        int8_t* mv = a.moves + (a.move_offs ? a.move_offs[w] : 0);
+        const int cap = n + m - 2;
+        // The walk back runs on the whole warp, in windows of 32 rows (lane k
+        // holds row i0 - k) by 32 columns (j0 - 31 .. j0): each lane loads
+        // the choice words of its row that cover the window (at most 3) in one
+        // round of loads; then every lane steps the walk in lockstep and the
+        // word of the current cell comes from the lane holding its row.
+        // Moves are written from the end of the buffer.
+        auto lane_in_strip = [&](int ri) -> int {
+            // every strip but the last holds 32 * RMAX rows (rows per lane
+            // RMAX); the last holds the rest
+            constexpr int kFullRows = 32 * RMAX;
+            const int nfull = n / kFullRows;
+            if (ri <= nfull * kFullRows) return ((ri - 1) % kFullRows) / RMAX;
+            const int r0 = nfull * kFullRows + 1;
+            return (ri - r0) / path_rows_per_lane<DIM, P, RMAX>(n - r0 + 1);
+        };
+        int i = n, j = m, len = 0;
+        while (i > 1 || j > 1) {
+            const int i0 = i, j0 = j;
+            const int ri = i0 - lane;
+            uint32_t wv0 = 0u, wv1 = 0u, wv2 = 0u;
+            int myL = 0, mybase = 0;
+            if (ri >= 1) {
+                myL = lane_in_strip(ri);
+                const uint32_t* rowp = choice + (int64_t)(ri - 1) * a.wpr;
+                mybase = (max(j0 - 31, 1) + myL) >> 4;
+                const int top = (j0 + myL) >> 4;
+                wv0 = __ldcg(rowp + mybase);
+                if (top > mybase) wv1 = __ldcg(rowp + mybase + 1);
+                if (top > mybase + 1) wv2 = __ldcg(rowp + mybase + 2);
+            }
+            while ((i > 1 || j > 1) && i > i0 - 32 && j > j0 - 32) {
+                const int t = j + myL;  // this lane's row at column j: step + 1
+                const int sel = (t >> 4) - mybase;
+                const uint32_t word = sel == 0 ? wv0 : (sel == 1 ? wv1 : wv2);
+                const uint32_t ch = __shfl_sync(kFull, (word >> (2 * (t & 15))) & 3u, i0 - i);
+                ++len;
+                if (lane == 0) mv[cap - len] = (int8_t)ch;
+                if (ch == 0u) {
+                    --i;
+                    --j;
+                } else if (ch == 1u) {
+                    --i;
+                } else {
+                    --j;
+                }
+            }
+        }
+        if (lane == 0) a.len[w] = len;
+        len = __shfl_sync(kFull, len, 0);
+        __syncwarp();
+        __threadfence_block();
+        if (len < cap) {
+            for (int k0 = 0; k0 < len; k0 += 32) {
+                int8_t v = 0;
+                if (k0 + lane < len) v = mv[cap - len + k0 + lane];
+                __syncwarp();
+                if (k0 + lane < len) mv[k0 + lane] = v;
+                __syncwarp();
+            }
+        }
+    }
+}
+
 }  // namespace dp
 
 // ------------------------------------------------------------- dispatch
@@ -706,6 +863,7 @@ twed_status_t dtw_host_impl(twed_handle_t h, const T* a, int64_t la, const T* b,
 // TWED edit paths: workspace = records, boundary rows and choice bits of the
 // warps in flight; the grid is cut so that the choice bits fit kPathBudget.
 constexpr size_t kPathBudget = (size_t)8 << 30;
+constexpr int kPathRStaged = 8;  // rows-per-lane cap of the staged path kernel
 
 template <typename T>
 twed_status_t path_launch(twed_handle_t h, twed::dp::PathArgs<T> pa, const T* vals_a, const T* ts_a,
@@ -713,19 +871,33 @@ twed_status_t path_launch(twed_handle_t h, twed::dp::PathArgs<T> pa, const T* va
                           const int64_t* offs_b, int64_t nb, int64_t totb, int64_t maxa, int64_t maxb, int dim,
                           T nu, T lambda, int p, cudaStream_t s) {
     const int rl = twed::rec_len<T>(dim, p);
-    const int64_t wpr = (maxb + 15) / 16;
+    // FP32 with a compiled point layout: the staged engine, whose choice
+    // words follow its steps (up to m + 31 of them per row)
+    const bool staged = sizeof(T) == 4 && twed::compiled_layout(dim, p);
+    const int64_t wpr = staged ? (maxb + 31) / 16 + 2 : (maxb + 15) / 16;
     const size_t per_choice = sizeof(uint32_t) * (size_t)maxa * (size_t)wpr;
     if (per_choice > kPathBudget)
         return err(h, TWED_ERR_UNSUPPORTED, "edit path: one pair's choice bits (n x m / 4 bytes) exceed 8 GiB");
     const int sms = twed::detail::handle_sms(h);
     int blocks = 0;
-    TWED_DP_DISPATCH(dim, p, (blocks = grid_for(twed::dp::path_pairs_kernel<T, DIM_, P_, kPathR>, pa.npairs, sms)));
+    int smem_warp = 0;
+    if constexpr (sizeof(T) == 4) {
+        if (staged) {
+            TWED_DISPATCH(dim, p, (smem_warp = twed::smem_per_warp<float, DIM_>(),
+                                   blocks = DIM_ > 0 ? twed::blocks_per_sm(twed::dp::path_staged_kernel<(DIM_ > 0 ? DIM_ : 1), (DIM_ > 0 ? P_ : 2), kPathRStaged>,
+                                                                           smem_warp, 128)
+                                                     : 0));
+            blocks = (int)std::min<int64_t>((int64_t)std::max(blocks, 1) * sms, (pa.npairs + 3) / 4);
+        }
+    }
+    if (!staged)
+        TWED_DP_DISPATCH(dim, p, (blocks = grid_for(twed::dp::path_pairs_kernel<T, DIM_, P_, kPathR>, pa.npairs, sms)));
     int64_t nwarps = (int64_t)blocks * 4;
     nwarps = std::max<int64_t>(1, std::min<int64_t>(nwarps, (int64_t)(kPathBudget / std::max<size_t>(per_choice, 1))));
     const int threads = nwarps >= 4 ? 128 : 32 * (int)nwarps;
     blocks = (int)((nwarps * 32 + threads - 1) / threads);
     nwarps = (int64_t)blocks * (threads / 32);
-    const int64_t stride = std::max(maxa, maxb) + 2;
+    const int64_t stride = (std::max(maxa, maxb) + 3) & ~(int64_t)1;  // >= longest + 2, even
     size_t off = align_up(64);
     const size_t o_ra = off;
     off = align_up(off + sizeof(T) * rl * (size_t)tota);
@@ -761,6 +933,14 @@ twed_status_t path_launch(twed_handle_t h, twed::dp::PathArgs<T> pa, const T* va
     pa.wpr = wpr;
     pa.sc = twed::SyncCtl{ctl, ctl + 1, 2000000000ull, -1, 0};
     (void)cudaGetLastError();
+    if constexpr (sizeof(T) == 4) {
+        if (staged) {
+            TWED_DISPATCH(dim, p, (e = DIM_ > 0 ? twed::launch_with_smem(twed::dp::path_staged_kernel<(DIM_ > 0 ? DIM_ : 1), (DIM_ > 0 ? P_ : 2), kPathRStaged>,
+                                                                         smem_warp, blocks, threads, s, pa)
+                                                : cudaErrorInvalidValue));
+            return e == cudaSuccess ? TWED_OK : cuda_err(h, e);
+        }
+    }
     TWED_DP_DISPATCH(dim, p, (twed::dp::path_pairs_kernel<T, DIM_, P_, kPathR><<<blocks, threads, 0, s>>>(pa)));
     e = cudaGetLastError();
     return e == cudaSuccess ? TWED_OK : cuda_err(h, e);

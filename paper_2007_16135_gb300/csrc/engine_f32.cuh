@@ -103,12 +103,34 @@ constexpr float kBig = 1.2676506e30f;  // 2^100
 // b_j) alone and D(i,j) = d + min(D(i-1,j), D(i,j-1), D(i-1,j-1)); times,
 // delete costs and the hand-off of c are not used (many-pairs schedule, no
 // compensation).
-template <int DIM, int P, int R, bool KH = false, int kStepBlock = kStepBlockPairs, bool DTW = false>
+//
+// PATH = true also records, per cell, which candidate gave D(i,j): the first
+// of match (0), delete in a (1), delete in b (2) equal to the minimum.  A
+// lane packs its rows' choices of 16 consecutive steps into one 32-bit word
+// per row: step s (lane L on column j = s - L + 1) goes to word (s + 1) / 16,
+// bits 2 ((s + 1) mod 16); words are stored at the block starts, row i's word
+// w at choice[(i - 1) * wpr + w] (rows past n are not stored).
+template <int DIM, int P, int R, bool KH = false, int kStepBlock = kStepBlockPairs, bool DTW = false,
+          bool PATH = false>
 __device__ __forceinline__ bool run_strip_staged(const PairRef<float>& pr, int r0, int rows,
                                                  const StripIO<float>& io, const SyncCtl& sc,
                                                  float* result_a, float* result_b, float* ring,
-                                                 void* bring_v) {
+                                                 void* bring_v, uint32_t* choice = nullptr, int64_t wpr = 0) {
     static_assert(DIM > 0, "staged engine needs a compile-time dimension");
+    static_assert(!PATH || (!KH && !DTW), "choice bits are recorded for plain TWED only");
+    uint32_t wbits[PATH ? R : 1];
+#pragma unroll
+    for (int r = 0; r < (PATH ? R : 1); ++r) wbits[r] = 0u;
+    auto flush_bits = [&](int w) {
+        if constexpr (PATH) {
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int i = r0 + (threadIdx.x & 31) * R + r;
+                if (i <= pr.n) choice[(int64_t)(i - 1) * wpr + w] = wbits[r];
+                wbits[r] = 0u;
+            }
+        }
+    };
     using RL = Rec<float, DIM>;
     constexpr int LEN = RL::kLen;
     constexpr bool PACK = (P == 2 && DIM >= 2 && (R % 2) == 0);
@@ -306,6 +328,9 @@ __device__ __forceinline__ bool run_strip_staged(const PairRef<float>& pr, int r
     // instruction cache when several strip heights run on one SM.
     auto boundary = [&](int s) -> bool {
         if (((s + 1) & 7) != 0) return true;
+        if constexpr (PATH) {
+            if (((s + 1) & 15) == 0) flush_bits(((s + 1) >> 4) - 1);  // steps s-16 .. s-1 are done
+        }
         const int jp = s - 31;  // lane 31 finished columns 1..jp
         if (io.publish && jp >= 1 && jp <= m && lane == 31) {
             if (io.down_flag != nullptr && (jp & 31) == 0) st_release(io.down_flag, (unsigned)jp);
@@ -430,7 +455,15 @@ __device__ __forceinline__ bool run_strip_staged(const PairRef<float>& pr, int r
             float d_up = upD;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                d_up = min3f(d_up + rdel[r], tb_[r], tm_[r]);
+                if constexpr (PATH) {
+                    const float da = d_up + rdel[r];
+                    const float v = min3f(da, tb_[r], tm_[r]);
+                    const uint32_t ch = tm_[r] == v ? 0u : (da == v ? 1u : 2u);
+                    wbits[r] |= ch << (2 * ((j + lane) & 15));  // j + lane = s + 1: warp-uniform
+                    d_up = v;
+                } else {
+                    d_up = min3f(d_up + rdel[r], tb_[r], tm_[r]);
+                }
                 Dl[r] = d_up;
                 cp[r] = cc[r];
             }
@@ -477,6 +510,9 @@ __device__ __forceinline__ bool run_strip_staged(const PairRef<float>& pr, int r
     if (!ok) {
         cp_async_wait_all();
         return false;
+    }
+    if constexpr (PATH) {
+        if (ok) flush_bits(steps >> 4);  // the word of the last step, s = steps - 1
     }
     // lane 31 ends on column m when all 32 lanes hold rows: publish it
     if (io.publish && lanes_used == 32 && lane == 31) {

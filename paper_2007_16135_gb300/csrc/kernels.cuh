@@ -26,16 +26,20 @@ __host__ __device__ constexpr int smem_per_warp() {
     else return 0;
 }
 
-template <typename T, int DIM, int P, int R, bool KH = false, int SB = kStepBlockPairs, bool DTW = false>
+template <typename T, int DIM, int P, int R, bool KH = false, int SB = kStepBlockPairs, bool DTW = false,
+          bool PATH = false>
 __device__ __forceinline__ bool strip_call(const PairRef<T>& pr, int r0, int rows,
                                            const StripIO<T>& io, const SyncCtl& sc, T* o1, T* o2,
-                                           unsigned char* wsmem) {
+                                           unsigned char* wsmem, uint32_t* choice = nullptr, int64_t wpr = 0) {
     if constexpr (kStaged<T, DIM>) {
         float* ring = reinterpret_cast<float*>(wsmem);
         void* bring = wsmem + kRingCols * Rec<float, DIM>::kLen * 4;
-        return run_strip_staged<DIM, P, R, KH, SB, DTW>(pr, r0, rows, io, sc, o1, o2, ring, bring);
+        return run_strip_staged<DIM, P, R, KH, SB, DTW, PATH>(pr, r0, rows, io, sc, o1, o2, ring, bring, choice,
+                                                              wpr);
     } else {
-        static_assert(!DTW, "DTW runs on the staged FP32 engine only");
+        static_assert(!DTW && !PATH, "DTW and choice bits run on the staged FP32 engine only");
+        (void)choice;
+        (void)wpr;
         (void)wsmem;
         return run_strip<T, DIM, P, R>(pr, r0, rows, io, sc, o1, o2);
     }

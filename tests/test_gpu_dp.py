@@ -203,3 +203,31 @@ def test_dtw_batch_f32_staged_layouts(tw, dim, p):
     same = pairs[:, 0] == pairs[:, 1]
     assert np.all(got[same] == 0.0)
     assert np.max(np.abs(got[~same] - want[~same]) / want[~same]) <= 1e-5
+
+
+@pytest.mark.parametrize("dim,p", [(1, 2), (2, 1), (3, 2), (4, 2), (8, 1), (8, 2)])
+def test_path_batch_f32_staged_layouts(tw, dim, p):
+    # FP32 compiled layouts record the choices on the staged engine (words of
+    # 16 steps, strips of up to 256 rows): every path is a valid monotone path
+    # whose cost, priced in FP64 on the same FP32-rounded inputs, is optimal
+    # within the 1e-5 bound, and the distance is within it too
+    import torch
+    from tests.test_oracle_path import path_cost
+    rng = np.random.default_rng(700 + 10 * dim + p)
+    lens = [1, 2, 15, 16, 17, 255, 256, 257, 513] + [int(v) for v in rng.integers(1, 700, 7)]
+    S = walk_set(40 + dim + p, lens, dim).astype(np.float32)
+    D = tw.DeviceSet.from_numpy(S.vals, S.ts, S.offs, torch.float32)
+    pairs = np.stack([rng.integers(0, S.n, 40), rng.integers(0, S.n, 40)], 1)
+    dist, moves, offs, lens_ = tw.twed_path_batch(D, D, torch.as_tensor(pairs).cuda(), 0.5, 0.75, p)
+    tw.default_handle().sync_status()
+    dist, moves, offs, lens_ = (x.cpu().numpy() for x in (dist, moves, offs, lens_))
+    S64 = S.astype(np.float64)
+    for k, (x, y) in enumerate(pairs):
+        (av, at), (bv, bt) = S64.series(x), S64.series(y)
+        want = oracle.twed(av, at, bv, bt, 0.5, 0.75, p)
+        got = "".join(tw.MOVE_CHARS[v] for v in moves[offs[k]:offs[k] + lens_[k]])
+        assert got.count("M") + got.count("A") == len(at) - 1, k
+        assert got.count("M") + got.count("B") == len(bt) - 1, k
+        tol = 1e-5 * max(want, 1e-30)
+        assert abs(float(dist[k]) - want) <= tol, k
+        assert abs(path_cost(got, av, at, bv, bt, 0.5, 0.75, p) - want) <= tol, k
