@@ -79,15 +79,19 @@ typedef struct {
     int xterm;          /* FP32 plans, dim 64, p = 2: TWED_XTERM_TF32 forms the
                            cross term a_i . b_j of |a_i - b_j|^2 on the tensor
                            cores (TF32 inputs, FP32 accumulation, FP32 norms);
-                           every cost then carries TF32 rounding (about 1e-4
-                           relative), so it is opt-in.  Needs every series of
-                           the plan to hold <= 1024 points, else
+                           TWED_XTERM_BF16 the same with the points rounded to
+                           BF16 (norms of the rounded points; the plan keeps a
+                           BF16 copy of the column set).  Every cost then
+                           carries the inputs' rounding (TF32 about 1e-4,
+                           BF16 about 1e-3 relative), so both are opt-in.
+                           Values must be 16-byte aligned, else
                            TWED_ERR_UNSUPPORTED. */
 } twed_opts_t;
 
 /* twed_opts_t.xterm values. */
 #define TWED_XTERM_OFF 0
 #define TWED_XTERM_TF32 1
+#define TWED_XTERM_BF16 2
 
 /* A packed set of series.  vals/ts/offs are device pointers; offs_host is a
  * host copy of offs (the library reads lengths from it to plan work). */

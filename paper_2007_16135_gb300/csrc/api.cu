@@ -590,6 +590,7 @@ struct twed_plan_s {
     unsigned* ctl = nullptr;  // plan's own [live err, sticky err]
     unsigned long long* counter = nullptr;
     bool xterm = false;  // tensor-core cross-term kernel (dim 64, FP32)
+    bool xbf16 = false;  // ... with BF16 inputs (TWED_XTERM_BF16)
     twed::XtermArgs xa{};                 // its argument block (out filled in at launch)
     alignas(64) unsigned char tmap[128];  // its TMA descriptor of the column set's values
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;  // around the pairs launch
@@ -638,7 +639,7 @@ RecordsArgs<double>& plan_rec<double>(twed_plan_t pl, int w) { return w ? pl->rd
 template <typename T>
 cudaError_t launch_plan_records(twed_plan_t pl, const RecordsArgs<T>& r, cudaStream_t st) {
     if constexpr (sizeof(T) == 4) {
-        if (pl->xterm) return twed::launch_xrecords(r, st);
+        if (pl->xterm) return twed::launch_xrecords(r, st, pl->xbf16);
     }
     return twed::launch_records(r, st);
 }
@@ -649,7 +650,7 @@ cudaError_t launch_plan_pairs(twed_plan_t pl, const PairsArgs<T>& pa, cudaStream
         if (pl->xterm) {
             twed::XtermArgs xa = pl->xa;
             xa.out = pa.out;
-            return twed::launch_xterm(pl->tmap, xa, pl->blocks, st);
+            return twed::launch_xterm(pl->tmap, xa, pl->blocks, st, pl->xbf16);
         }
     }
     return twed::launch_pairs(pa, pl->blocks, pl->threads, st);
@@ -898,8 +899,8 @@ twed_status_t plan_create(twed_handle_t h, const S* A, const S* B, int dim, T nu
     }
     pl->cells = cells;
 
-    const bool want_x = o && o->xterm == TWED_XTERM_TF32;
-    if (o && (o->xterm < TWED_XTERM_OFF || o->xterm > TWED_XTERM_TF32)) {
+    const bool want_x = o && (o->xterm == TWED_XTERM_TF32 || o->xterm == TWED_XTERM_BF16);
+    if (o && (o->xterm < TWED_XTERM_OFF || o->xterm > TWED_XTERM_BF16)) {
         delete pl;
         return fail(h, TWED_ERR_INVALID_ARG, "unknown xterm mode %d", o->xterm);
     }
@@ -912,6 +913,7 @@ twed_status_t plan_create(twed_handle_t h, const S* A, const S* B, int dim, T nu
         return fail(h, TWED_ERR_UNSUPPORTED, "tensor-core cross term: values must be 16-byte aligned");
     }
     pl->xterm = want_x;
+    pl->xbf16 = want_x && o->xterm == TWED_XTERM_BF16;
     const int rl = pl->xterm ? 4 : twed::rec_len<T>(dim, p);
     const int threads = pl->xterm ? twed::xterm_threads() : 128;
     const int per_sm_raw = pl->xterm ? twed::xterm_blocks_per_sm()
@@ -959,6 +961,8 @@ twed_status_t plan_create(twed_handle_t h, const S* A, const S* B, int dim, T nu
     const size_t o_xb = pl->xterm ? cv.take(sizeof(float) * 2 * (size_t)pl->blocks *
                                             (size_t)twed::xterm_warps_per_block() * (size_t)xbnd) : 0;
     const size_t o_cs = chunk_start.empty() ? 0 : cv.take(sizeof(int64_t) * chunk_start.size());
+    const int64_t xtot = sym ? tota : totb;  // points of the column set
+    const size_t o_bf = pl->xbf16 ? cv.take((size_t)2 * 64 * (size_t)xtot) : 0;  // its BF16 copy
     const size_t o_ctl = cv.take(64);
     pl->mem_bytes = cv.off;
     cudaError_t e = cudaMalloc(&pl->mem, pl->mem_bytes);
@@ -977,8 +981,13 @@ twed_status_t plan_create(twed_handle_t h, const S* A, const S* B, int dim, T nu
         e = cudaMemcpy(base + o_cs, chunk_start.data(), sizeof(int64_t) * chunk_start.size(),
                        cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(pl->ctl, 0, 64);
+    if (e == cudaSuccess && pl->xbf16) {
+        e = twed::launch_bf16_copy((const float*)(sym ? A->vals : B->vals), base + o_bf, 64 * xtot, nullptr);
+        if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    }
     if (e == cudaSuccess && pl->xterm)
-        e = twed::xterm_tensor_map(pl->tmap, (const float*)(sym ? A->vals : B->vals), sym ? tota : totb);
+        e = twed::xterm_tensor_map(pl->tmap, pl->xbf16 ? (const void*)(base + o_bf) : (const void*)(sym ? A->vals : B->vals),
+                                   xtot, pl->xbf16);
     if (e != cudaSuccess) {
         cudaGetLastError();
         cudaFree(pl->mem);

@@ -147,10 +147,14 @@ struct XtermArgs {
     unsigned long long* counter;  // work item counter, zero before the launch
     SyncCtl sc;
 };
-cudaError_t launch_xrecords(const RecordsArgs<float>& a, cudaStream_t st);
-// tmap: 128-byte CUtensorMap of the column set's values (xterm_tensor_map)
-cudaError_t xterm_tensor_map(void* tmap, const float* vals, int64_t total);
-cudaError_t launch_xterm(const void* tmap, const XtermArgs& a, int blocks, cudaStream_t st);
+// bf16: records hold the norms of the points rounded to BF16
+cudaError_t launch_xrecords(const RecordsArgs<float>& a, cudaStream_t st, bool bf16);
+// The points of a column set rounded to BF16 (nvals values, a multiple of 64).
+cudaError_t launch_bf16_copy(const float* src, void* dst, int64_t nvals, cudaStream_t st);
+// tmap: 128-byte CUtensorMap of the column set's values (xterm_tensor_map):
+// FP32, or with bf16 the set's BF16 copy
+cudaError_t xterm_tensor_map(void* tmap, const void* vals, int64_t total, bool bf16);
+cudaError_t launch_xterm(const void* tmap, const XtermArgs& a, int blocks, cudaStream_t st, bool bf16);
 int xterm_blocks_per_sm();
 int xterm_resident_blocks();
 void xterm_resources(char* buf, int len);

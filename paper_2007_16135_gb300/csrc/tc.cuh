@@ -42,6 +42,12 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
            ((uint32_t)(M >> 4) << 24);
 }
 
+// kind::f16 with BF16 inputs: c_format = 1 (F32), a_format = b_format = 1
+// (BF16), both K-major, same N / M fields.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
@@ -77,6 +83,23 @@ __device__ __forceinline__ void mma_tf32_tmem_a(uint32_t d_tmem, uint32_t a_tmem
         "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
         "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"((uint32_t)accumulate)
         : "memory");
+}
+// kind::f16 (BF16 A and B, FP32 accumulate), A from tensor memory: two BF16
+// values of K per 32-bit column (the lower one in the low half), so one MMA
+// (K = 16) reads 8 columns from a_tmem.
+__device__ __forceinline__ void mma_bf16_tmem_a(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc,
+                                                uint32_t idesc, bool accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"((uint32_t)accumulate)
+        : "memory");
+}
+// Two floats rounded to BF16 (nearest even) and packed: lo in bits 0-15.
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+    uint32_t d;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %2;" : "=r"(d) : "f"(hi), "f"(lo));
+    return d;
 }
 // Arrive once on the mbarrier when every MMA this thread issued has completed.
 __device__ __forceinline__ void mma_commit(uint64_t* mbar) {

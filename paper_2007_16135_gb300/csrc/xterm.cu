@@ -93,7 +93,10 @@ static_assert((OFF_SCHED % 8) == 0, "schedule alignment");
 }  // namespace x64
 
 // Point records for the tensor-core path: (t, delete cost, |x|^2, 0).
-__global__ void __launch_bounds__(256) xrecords_kernel(RecordsArgs<float> a) {
+// With bf16, the norm is that of the point rounded to BF16 (the values the
+// BF16 contraction multiplies), so that |a|^2 + |b|^2 - 2 a.b is exact for the
+// rounded points up to FP32 summation.
+__global__ void __launch_bounds__(256) xrecords_kernel(RecordsArgs<float> a, bool bf16) {
     using A = Arith<float>;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < a.total; g += stride) {
@@ -110,7 +113,8 @@ __global__ void __launch_bounds__(256) xrecords_kernel(RecordsArgs<float> a) {
             const float xk = x[k];
             const float d = first ? xk : xk - x[k - x64::D];
             s = fmaf(d, d, s);
-            nrm = fmaf(xk, xk, nrm);
+            const float xr = bf16 ? __uint_as_float(tc::pack_bf16x2(xk, 0.f) << 16) : xk;
+            nrm = fmaf(xr, xr, nrm);
         }
         const float t = a.ts[g];
         const float tprev = first ? 0.f : a.ts[g - 1];
@@ -120,6 +124,16 @@ __global__ void __launch_bounds__(256) xrecords_kernel(RecordsArgs<float> a) {
         r.z = nrm;
         r.w = 0.f;
         reinterpret_cast<float4*>(a.rec)[g] = r;
+    }
+}
+
+// Points of the column set rounded to BF16 for the B tiles of the BF16 mode,
+// two per 32-bit word (the lower index in the low half).
+__global__ void __launch_bounds__(256) bf16_copy_kernel(const float* src, uint32_t* dst, int64_t nwords) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; g < nwords; g += stride) {
+        const float2 v = reinterpret_cast<const float2*>(src)[g];
+        dst[g] = tc::pack_bf16x2(v.x, v.y);
     }
 }
 
@@ -285,6 +299,9 @@ __device__ __forceinline__ void st_shared_v4(float* p, float a, float b, float c
 
 }  // namespace
 
+// BF = false: TF32 inputs (the FP32 values as the tensor core reads them);
+// BF = true: BF16 inputs (A rounded by the consumers, B from a BF16 copy).
+template <bool BF>
 __global__ void __launch_bounds__(x64::THREADS, 2) xterm_sweep_kernel(const __grid_constant__ CUtensorMap tmap_b,
                                                                    XtermArgs a) {
     using namespace x64;
@@ -317,7 +334,13 @@ __global__ void __launch_bounds__(x64::THREADS, 2) xterm_sweep_kernel(const __gr
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = misc[0];
-    const uint32_t idesc = tc::idesc_tf32(128, NM);
+    const uint32_t idesc = BF ? tc::idesc_bf16(128, NM) : tc::idesc_tf32(128, NM);
+    // B tile: BOXES_T boxes of 16 bytes x NM points (4 TF32 or 8 BF16 values
+    // of K each); A: K along TMEM columns, one TF32 or two BF16 values each
+    constexpr int BOXES_T = BF ? BOXES / 2 : BOXES;
+    constexpr uint32_t TILE_BYTES_T = BF ? TILE_BYTES / 2 : TILE_BYTES;
+    constexpr int KSTEPS = BF ? D / 16 : D / 8;  // MMAs per row tile
+    constexpr int ACOLS = BF ? D / 2 : D;        // TMEM columns of one row tile of A
     // the TMA destinations need a 1024-byte aligned shared window
     const bool aligned = (tc::smem_u32(sm) & 1023u) == 0;
 
@@ -368,11 +391,11 @@ __global__ void __launch_bounds__(x64::THREADS, 2) xterm_sweep_kernel(const __gr
                     if (!__all_sync(kFull, w2)) { ok = false; break; }
                     const int t = (int)(idx % (uint32_t)ntilesM);
                     unsigned char* dst = sm + OFF_B + st * TILE_BYTES;
-                    if (lane == 0) tc::mbar_arrive_expect_tx(&b_full[st], TILE_BYTES);
+                    if (lane == 0) tc::mbar_arrive_expect_tx(&b_full[st], TILE_BYTES_T);
                     __syncwarp();
-                    if (lane < BOXES)
-                        tc::tma_load_2d(dst + lane * (NM * 16), &tmap_b, 4 * lane, (int)(it.yb + (int64_t)NM * t),
-                                        &b_full[st]);
+                    if (lane < BOXES_T)
+                        tc::tma_load_2d(dst + lane * (NM * 16), &tmap_b, (BF ? 8 : 4) * lane,
+                                        (int)(it.yb + (int64_t)NM * t), &b_full[st]);
                     __syncwarp();
                     ++Lp;
                 }
@@ -391,12 +414,14 @@ __global__ void __launch_bounds__(x64::THREADS, 2) xterm_sweep_kernel(const __gr
 #pragma unroll
                         for (int r = 0; r < RT; ++r) {
 #pragma unroll
-                            for (int ks = 0; ks < D / 8; ++ks) {
+                            for (int ks = 0; ks < KSTEPS; ++ks) {
                                 // K step ks covers k-groups 2ks, 2ks+1 (boxes NM * 16 bytes apart);
                                 // each further 8 points of the tile sit 128 bytes on
                                 const uint64_t bd = tc::smem_desc(bad + ks * 2 * (NM * 16), NM * 16, 128);
-                                tc::mma_tf32_tmem_a(tmem + (uint32_t)(ACC_COL + s * (RT * NM) + r * NM),
-                                                    tmem + (uint32_t)(r * D + ks * 8), bd, idesc, ks > 0);
+                                const uint32_t dt = tmem + (uint32_t)(ACC_COL + s * (RT * NM) + r * NM);
+                                const uint32_t at = tmem + (uint32_t)(r * ACOLS + ks * 8);
+                                if constexpr (BF) tc::mma_bf16_tmem_a(dt, at, bd, idesc, ks > 0);
+                                else tc::mma_tf32_tmem_a(dt, at, bd, idesc, ks > 0);
                             }
                         }
                         tc::mma_commit(&acc_full[s]);
@@ -457,18 +482,30 @@ __global__ void __launch_bounds__(x64::THREADS, 2) xterm_sweep_kernel(const __gr
 #pragma unroll
                     for (int r = 0; r < RT; ++r) {
                         const float4* src = a_src(S, r);
-#pragma unroll
-                        for (int h = 0; h < 2; ++h) {
+                        if constexpr (BF) {
+                            // 64 values rounded to BF16, two per column
                             float v[32];
 #pragma unroll
-                            for (int u = 0; u < 8; ++u) {
-                                const float4 f = __ldg(src + h * 8 + u);
-                                v[4 * u] = f.x;
-                                v[4 * u + 1] = f.y;
-                                v[4 * u + 2] = f.z;
-                                v[4 * u + 3] = f.w;
+                            for (int u = 0; u < 16; ++u) {
+                                const float4 f = __ldg(src + u);
+                                v[2 * u] = __uint_as_float(tc::pack_bf16x2(f.x, f.y));
+                                v[2 * u + 1] = __uint_as_float(tc::pack_bf16x2(f.z, f.w));
                             }
-                            tc::tmem_st32(tmem + tlane + (uint32_t)(r * D + 32 * h), v);
+                            tc::tmem_st32(tmem + tlane + (uint32_t)(r * ACOLS), v);
+                        } else {
+#pragma unroll
+                            for (int h = 0; h < 2; ++h) {
+                                float v[32];
+#pragma unroll
+                                for (int u = 0; u < 8; ++u) {
+                                    const float4 f = __ldg(src + h * 8 + u);
+                                    v[4 * u] = f.x;
+                                    v[4 * u + 1] = f.y;
+                                    v[4 * u + 2] = f.z;
+                                    v[4 * u + 3] = f.w;
+                                }
+                                tc::tmem_st32(tmem + tlane + (uint32_t)(r * D + 32 * h), v);
+                            }
                         }
                     }
                     tc::tmem_wait_st();
@@ -768,27 +805,45 @@ __global__ void __launch_bounds__(x64::THREADS, 2) xterm_sweep_kernel(const __gr
     if (warp == 0) tc::tmem_dealloc(tmem, TMEM_COLS);
 }
 
-cudaError_t launch_xrecords(const RecordsArgs<float>& a, cudaStream_t st) {
+cudaError_t launch_xrecords(const RecordsArgs<float>& a, cudaStream_t st, bool bf16) {
     if (a.total <= 0) return cudaSuccess;
     int64_t blocks = (a.total + 255) / 256;
     if (blocks > 65535) blocks = 65535;
     (void)cudaGetLastError();
-    xrecords_kernel<<<(int)blocks, 256, 0, st>>>(a);
+    xrecords_kernel<<<(int)blocks, 256, 0, st>>>(a, bf16);
     return cudaGetLastError();
 }
 
-static cudaError_t xterm_attributes() {
-    cudaError_t e = cudaFuncSetAttribute(xterm_sweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, x64::SMEM);
+cudaError_t launch_bf16_copy(const float* src, void* dst, int64_t nvals, cudaStream_t st) {
+    if (nvals <= 0) return cudaSuccess;
+    const int64_t nwords = nvals / 2;  // nvals is a multiple of 64
+    int64_t blocks = (nwords + 255) / 256;
+    if (blocks > 65535) blocks = 65535;
+    (void)cudaGetLastError();
+    bf16_copy_kernel<<<(int)blocks, 256, 0, st>>>(src, (uint32_t*)dst, nwords);
+    return cudaGetLastError();
+}
+
+template <bool BF>
+static cudaError_t xterm_attributes_t() {
+    cudaError_t e =
+        cudaFuncSetAttribute(xterm_sweep_kernel<BF>, cudaFuncAttributeMaxDynamicSharedMemorySize, x64::SMEM);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(xterm_sweep_kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+        e = cudaFuncSetAttribute(xterm_sweep_kernel<BF>, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  cudaSharedmemCarveoutMaxShared);
     return e;
+}
+static cudaError_t xterm_attributes() {
+    cudaError_t e = xterm_attributes_t<false>();
+    return e == cudaSuccess ? xterm_attributes_t<true>() : e;
 }
 
 // Tensor map of a set's 64-dimensional values for the B tiles: [total][64]
 // FP32, rows 256 bytes apart; a box is 4 values (16 bytes) of NM points, so
-// one tile is 16 boxes at x = 0, 4, .., 60.  Points past the end read 0.
-cudaError_t xterm_tensor_map(void* tmap, const float* vals, int64_t total) {
+// one tile is 16 boxes at x = 0, 4, .., 60.  With bf16, the values are the
+// set's BF16 copy, rows 128 bytes apart, a box 8 values (16 bytes), 8 boxes
+// per tile at x = 0, 8, .., 56.  Points past the end read 0.
+cudaError_t xterm_tensor_map(void* tmap, const void* vals, int64_t total, bool bf16) {
     static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
     if (!encode) {
         cudaDriverEntryPointQueryResult q;
@@ -800,22 +855,25 @@ cudaError_t xterm_tensor_map(void* tmap, const float* vals, int64_t total) {
         encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     }
     const cuuint64_t dims[2] = {(cuuint64_t)x64::D, (cuuint64_t)total};
-    const cuuint64_t strides[1] = {(cuuint64_t)x64::D * sizeof(float)};
-    const cuuint32_t box[2] = {4, (cuuint32_t)x64::NM};
+    const cuuint64_t strides[1] = {(cuuint64_t)x64::D * (bf16 ? 2 : 4)};
+    const cuuint32_t box[2] = {bf16 ? 8u : 4u, (cuuint32_t)x64::NM};
     const cuuint32_t estr[2] = {1, 1};
-    CUresult r = encode(reinterpret_cast<CUtensorMap*>(tmap), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
-                        const_cast<float*>(vals), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+    CUresult r = encode(reinterpret_cast<CUtensorMap*>(tmap),
+                        bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                        const_cast<void*>(vals), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                         CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-cudaError_t launch_xterm(const void* tmap, const XtermArgs& a, int blocks, cudaStream_t st) {
+cudaError_t launch_xterm(const void* tmap, const XtermArgs& a, int blocks, cudaStream_t st, bool bf16) {
     if (a.nitems <= 0) return cudaSuccess;
     cudaError_t e = xterm_attributes();
     if (e != cudaSuccess) return e;
     (void)cudaGetLastError();
-    xterm_sweep_kernel<<<blocks, x64::THREADS, x64::SMEM, st>>>(*reinterpret_cast<const CUtensorMap*>(tmap), a);
+    const CUtensorMap& tm = *reinterpret_cast<const CUtensorMap*>(tmap);
+    if (bf16) xterm_sweep_kernel<true><<<blocks, x64::THREADS, x64::SMEM, st>>>(tm, a);
+    else xterm_sweep_kernel<false><<<blocks, x64::THREADS, x64::SMEM, st>>>(tm, a);
     return cudaGetLastError();
 }
 
@@ -823,7 +881,7 @@ int xterm_blocks_per_sm() {
     cudaError_t e = xterm_attributes();
     int nb = 0;
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, xterm_sweep_kernel, x64::THREADS, x64::SMEM);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, xterm_sweep_kernel<false>, x64::THREADS, x64::SMEM);
     if (e != cudaSuccess) {
         (void)cudaGetLastError();
         return -(int)e;  // negative: the CUDA error code, for diagnostics
@@ -836,7 +894,7 @@ int xterm_blocks_per_sm() {
 int xterm_resident_blocks() {
     cudaFuncAttributes fa{};
     int dev = 0, smem_sm = 0, regs_sm = 0;
-    if (xterm_attributes() != cudaSuccess || cudaFuncGetAttributes(&fa, xterm_sweep_kernel) != cudaSuccess ||
+    if (xterm_attributes() != cudaSuccess || cudaFuncGetAttributes(&fa, xterm_sweep_kernel<false>) != cudaSuccess ||
         cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess) {
@@ -857,7 +915,7 @@ void xterm_resources(char* buf, int len) {
     cudaFuncAttributes fa{};
     int dev = 0, smem_sm = 0, smem_blk = 0;
     (void)xterm_attributes();
-    cudaFuncGetAttributes(&fa, xterm_sweep_kernel);
+    cudaFuncGetAttributes(&fa, xterm_sweep_kernel<false>);
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
     cudaDeviceGetAttribute(&smem_blk, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);

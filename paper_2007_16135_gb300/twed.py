@@ -57,7 +57,7 @@ class TwedError(RuntimeError):
         self.status = status
 
 
-XTERM_OFF, XTERM_TF32 = 0, 1
+XTERM_OFF, XTERM_TF32, XTERM_BF16 = 0, 1, 2
 
 
 class Opts(ctypes.Structure):

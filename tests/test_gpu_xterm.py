@@ -149,3 +149,30 @@ def test_tensor_core_reexecute_is_stable(tw):
     M2 = plan.execute().cpu().numpy()
     plan.status()
     assert np.array_equal(M1, M2)
+
+
+# BF16 inputs (TWED_XTERM_BF16): 8 significant bits, so a rounded point is
+# within 2^-9 of each component; d^2 of the rounded points (exact up to FP32
+# summation, the norms being those of the rounded points) differs from the
+# true d^2 by at most 2 |a - b| |da - db|, about 2^-7 d^2 when |a - b| is of the
+# order of |a| and |b| -- a cost within about 0.4%; the bound on the TWED is
+# 1e-2 relative.
+def test_bf16_block_matches_oracle(tw):
+    SA, SB = smoothed_set(1, LENGTHS_A), smoothed_set(2, LENGTHS_B)
+    ref = oracle_block(SA, SB)
+    Mb, desc = matrix(tw, SA, SB, tw.XTERM_BF16)
+    assert "tensor-core" in desc
+    rel = np.abs(Mb - ref) / ref
+    print(f"BF16 cross term: max rel err {rel.max():.3e}, mean {rel.mean():.3e}")
+    assert rel.max() <= 1e-2
+    Mt, _ = matrix(tw, SA, SB, tw.XTERM_TF32)
+    assert (np.abs(Mt - ref) / ref).max() <= 2e-3
+
+
+def test_bf16_symmetric_plan(tw):
+    S = smoothed_set(3, [40, 129, 1, 256, 17, 90, 300, 1100])
+    Mb, _ = matrix(tw, S, None, tw.XTERM_BF16)
+    ref = oracle_block(S, S)
+    iu = np.triu_indices(S.n, 1)
+    assert (np.abs(Mb[iu] - ref[iu]) / ref[iu]).max() <= 1e-2
+    assert np.array_equal(Mb, Mb.T) and np.all(np.diag(Mb) == 0)
