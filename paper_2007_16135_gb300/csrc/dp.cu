@@ -44,6 +44,7 @@ struct CellV {
 //   else max(L(i-1,j), L(i,j-1)).
 // Choice bits: bit 0 x_i == y_j (diagonal), bit 1 L(i-1,j) >= L(i,j-1) (up).
 struct Lcs {
+    static constexpr bool kAux = false;  // no second value per cell to hand over
     using V = int32_t;
     using Row = int32_t;
     using Col = int32_t;
@@ -72,6 +73,7 @@ struct Lcs {
 // zeros after the real ones); DIM = 0 reads the points from global memory.
 template <typename T, int DIM, int P>
 struct Dtw {
+    static constexpr bool kAux = false;
     using V = T;
     static constexpr int DV = DIM > 0 ? DIM : 1;
     struct Pt {
@@ -117,6 +119,7 @@ struct Dtw {
 // 2 delete in b.
 template <typename T, int DIM, int P>
 struct Twed {
+    static constexpr bool kAux = true;  // c(i,j), read by the diagonal successor
     using V = T;
     using RL = Rec<T, DIM>;
     static constexpr int DV = DIM > 0 ? DIM : 1;
@@ -212,7 +215,8 @@ __device__ __forceinline__ void strip(const Pol& pol, int r0, int rows, const Ce
     int j = 1 - lane;
     for (int s = 0; s < steps; ++s, ++j) {
         V upD = __shfl_up_sync(kFull, bot, 1);
-        V upC = __shfl_up_sync(kFull, botC, 1);
+        V upC = V(0);
+        if constexpr (Pol::kAux) upC = __shfl_up_sync(kFull, botC, 1);
         if (first) {
             if (lane == 0) {
                 upD = pol.top();
@@ -221,7 +225,8 @@ __device__ __forceinline__ void strip(const Pol& pol, int r0, int rows, const Ce
         } else {
             const int idx = s & 31;
             const V bD = __shfl_sync(kFull, chD, idx);
-            const V bC = __shfl_sync(kFull, chC, idx);
+            V bC = V(0);
+            if constexpr (Pol::kAux) bC = __shfl_sync(kFull, chC, idx);
             if (lane == 0) {
                 upD = bD;
                 upC = bC;
