@@ -200,9 +200,9 @@ twed_status_t twed_batch_f32_ex(twed_handle_t handle, const twed_set_f32_t* A,
 
 /* ---- explicit pairs without any allocation -------------------------------
  * The paper has no counterpart to this entry point.  It exists for callers
- * that must not allocate device memory: code that runs while another thread
- * captures a CUDA graph in global mode (cudaMalloc is illegal there), loops
- * where a cudaMalloc/cudaFree would synchronize the device, and plug-ins
+ * that must not allocate device memory: loops where a cudaMalloc/cudaFree
+ * would synchronize the device and stall the work queued behind it,
+ * latency-bound paths that must not wait on the allocator, and plug-ins
  * whose host framework hands them a fixed memory budget.  Everything above
  * allocates (twed_create, workspace growth, plans); this call does not.
  *
@@ -216,7 +216,7 @@ twed_status_t twed_batch_f32_ex(twed_handle_t handle, const twed_set_f32_t* A,
  * the array's device address (cudaGetSymbolAddress), reads the SM count, and
  * loads and sizes every kernel this call can launch (attribute and occupancy
  * queries), so that later calls on that device do no lazy kernel loading.
- * Make that first call before any stream capture.  The set-up belongs to the
+ * Make that first call during the caller's own set-up.  The set-up belongs to the
  * device's primary context: after cudaDeviceReset of that device this entry
  * point must not be called again in the process.
  *

@@ -1,8 +1,8 @@
 """The allocation-free entry point, twed_batch_f32_noalloc.
 
-Some callers cannot call cudaMalloc (code running during another thread's
-global-mode graph capture, device-synchronization-free loops, plug-ins with a
-fixed memory budget), so the library offers one batched call that works in
+Some callers cannot call cudaMalloc (loops that must not synchronize the
+device, latency-bound paths that must not wait on the allocator, plug-ins
+with a fixed memory budget), so the library offers one batched call that works in
 a static device array instead of allocated workspace.  Its results must
 equal those of twed_batch_f32, the allocating entry point, call after call,
 although every call reuses (and inherits the contents of) the same array;
