@@ -158,7 +158,7 @@ twed::SyncCtl make_sync(twed_handle_t h, const twed_opts_t* o) {
 // flight only lengthen the fill of the wavefront (each strip trails its
 // predecessor by about kCoopLag columns).
 constexpr int kCoopF64WarpsPerSm = 4;
-constexpr double kCoopLag = 110.0;
+constexpr double kCoopLag = 64.0;
 
 // Rows per lane for one long pair.  FP64: a cost model over R in {4, 2, 1}:
 // with W = min(strips, 4 x SMs) warps, the pair takes about

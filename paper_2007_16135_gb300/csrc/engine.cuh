@@ -374,14 +374,19 @@ __device__ __forceinline__ bool run_strip(const PairRef<T>& pr, int r0, int rows
     T diagC = T(0);
     T botD = INF, botC = T(0);  // this lane's bottom row at its last column
 
-    // ---- boundary row above the strip: 32 columns per chunk, one per lane
+    // ---- boundary row above the strip: 16 columns per chunk, lane L (and
+    // L + 16) holding column L of it; the chunk after the current one is read
+    // one chunk ahead, so a strip trails the one above by about 16 + 16 + 31
+    // columns (the read-ahead, the publication step of 16 and lane 31's skew)
+    constexpr int CK = 16;
+    const int cl = lane & (CK - 1);
     T chD = INF, chC = T(0), nxD = INF, nxC = T(0);
     bool ok = true;
     if (!first) {
-        const int c0 = 1 + lane;       // chunk 0: columns 1..32
-        const int c1 = 33 + lane;      // chunk 1: columns 33..64
+        const int c0 = 1 + cl;         // chunk 0: columns 1..16
+        const int c1 = 1 + CK + cl;    // chunk 1: columns 17..32
         if (io.up_flag) {
-            ok = wait_progress(io.up_flag, (unsigned)min(64, m), sc);
+            ok = wait_progress(io.up_flag, (unsigned)min(2 * CK, m), sc);
         }
         if (ok) {
             if (c0 <= m) {
@@ -421,22 +426,22 @@ __device__ __forceinline__ bool run_strip(const PairRef<T>& pr, int r0, int rows
                 upC = T(0);
             }
         } else {
-            const int idx = s & 31;
+            const int idx = s & (CK - 1);
             T bD = __shfl_sync(kFull, chD, idx);
             T bC = __shfl_sync(kFull, chC, idx);
             if (lane == 0) {
                 upD = bD;
                 upC = bC;
             }
-            if (idx == 31) {
+            if (idx == CK - 1) {
                 chD = nxD;
                 chC = nxC;
-                const int base = s + 34;  // first column of the chunk after next
+                const int base = s + 2 + CK;  // first column of the chunk after next
                 if (base <= m) {
                     bool w = true;
-                    if (io.up_flag) w = wait_progress(io.up_flag, (unsigned)min(base + 31, m), sc);
+                    if (io.up_flag) w = wait_progress(io.up_flag, (unsigned)min(base + CK - 1, m), sc);
                     if (__any_sync(kFull, !w)) return false;
-                    const int c = base + lane;
+                    const int c = base + cl;
                     if (c <= m) {
                         V2 v = __ldcg(io.up + (c - 1));
                         nxD = v.x;
@@ -476,7 +481,7 @@ __device__ __forceinline__ bool run_strip(const PairRef<T>& pr, int r0, int rows
                 o.x = botD;
                 o.y = botC;
                 __stcg(io.down + (j - 1), o);
-                if (io.down_flag != nullptr && io.publish && (((j & 31) == 0) || j == m)) {
+                if (io.down_flag != nullptr && io.publish && (((j & (CK - 1)) == 0) || j == m)) {
                     st_release(io.down_flag, (unsigned)j);
                 }
             }

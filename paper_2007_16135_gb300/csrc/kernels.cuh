@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(256) records_kernel(RecordsArgs<T> a) {
 // order from an atomic counter, so the strip a warp waits on was taken by a
 // warp that is already running: progress never depends on a warp that has
 // not started, whatever the residency.  A strip publishes its bottom row
-// every 32 columns into a ring slot (release store of the column count) and
+// every 16 columns into a ring slot (release store of the column count) and
 // its successor polls that count (acquire, bounded by %globaltimer).
 template <typename T, int DIM, int P, int R, bool KH>
 __global__ void __launch_bounds__(128) coop_kernel(CoopArgs<T> a) {
