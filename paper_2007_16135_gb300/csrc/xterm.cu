@@ -179,8 +179,9 @@ __device__ __forceinline__ bool xwait(uint64_t* bar, uint32_t parity, const Sync
 __device__ __forceinline__ bool xwait_prod(uint64_t* bar, uint32_t parity, const SyncCtl& sc) {
     if (tc::mbar_test_wait(bar, parity)) return true;
     const unsigned long long t0 = globaltimer();
+    uint32_t k = 0;
     while (!tc::mbar_try_wait_sleep(bar, parity, 50000u))
-        if (xwait_fail(sc, t0)) return false;
+        if ((++k & 7u) == 0 && xwait_fail(sc, t0)) return false;
     return true;
 }
 
@@ -409,16 +410,21 @@ __global__ void __launch_bounds__(x64::THREADS, 2) xterm_sweep_kernel(const __gr
                     if (w2 && Tp >= NS) w2 = xwait_prod(&acc_empty[s], ((Tp / NS) - 1) & 1, a.sc);
                     if (!__all_sync(kFull, w2)) { ok = false; break; }
                     tc::fence_after_sync();
+                    // the stage's B descriptor and the accumulator base, warp-uniform;
+                    // K step ks starts ks * 2 * NM * 16 bytes on (the descriptor's
+                    // address field counts 16-byte units and cannot carry: shared
+                    // addresses stay below 2^18)
+                    const uint64_t bd0 = tc::smem_desc(tc::smem_u32(sm + OFF_B + st * TILE_BYTES), NM * 16, 128);
+                    const uint32_t dt0 = tmem + (uint32_t)(ACC_COL + s * (RT * NM));
                     if (lane == 0) {
-                        const uint32_t bad = tc::smem_u32(sm + OFF_B + st * TILE_BYTES);
 #pragma unroll
                         for (int r = 0; r < RT; ++r) {
 #pragma unroll
                             for (int ks = 0; ks < KSTEPS; ++ks) {
                                 // K step ks covers k-groups 2ks, 2ks+1 (boxes NM * 16 bytes apart);
                                 // each further 8 points of the tile sit 128 bytes on
-                                const uint64_t bd = tc::smem_desc(bad + ks * 2 * (NM * 16), NM * 16, 128);
-                                const uint32_t dt = tmem + (uint32_t)(ACC_COL + s * (RT * NM) + r * NM);
+                                const uint64_t bd = bd0 + (uint64_t)((ks * 2 * NM * 16) >> 4);
+                                const uint32_t dt = dt0 + (uint32_t)(r * NM);
                                 const uint32_t at = tmem + (uint32_t)(r * ACOLS + ks * 8);
                                 if constexpr (BF) tc::mma_bf16_tmem_a(dt, at, bd, idesc, ks > 0);
                                 else tc::mma_tf32_tmem_a(dt, at, bd, idesc, ks > 0);
