@@ -885,7 +885,7 @@ def bench_mnist(args, rank, world, dev):
     res = {"value": plan.cells * world / (ms / 1e3) / 1e9, "unit": "GCUPS", "ms_per_step": ms,
            "cells_per_step": plan.cells, "dtype": "f64", "clocks": clk, "gpu_launches": 3 * 20,
            "result": {"seconds_per_query": ms / 1e3, "paper_seconds_per_query_other_gpu": 0.20},
-           "roofline": roof(plan.cells, ms, "f64", "pairs_kernel<double,0,0,R> (run-time dimension)"),
+           "roofline": roof(plan.cells, ms, "f64", "short_pairs_kernel<double,28> (cost tile, then wavefront)"),
            "config": {"workload": "u3 single query: 1 x 60,000 synthetic 28 x 28 stroke images, rows as 28 "
                                   "points in R^28 (the shape of the paper's digit-image query), t_i=i, "
                                   "nu=lambda=1, p=2, FP64", "pairs": plan.pairs,
@@ -918,8 +918,8 @@ def bench_mnist(args, rank, world, dev):
         full_cells = 60_000 * 59_999 // 2 * 784
         res = {"value": gcups, "unit": "GCUPS", "ms_per_step": ms, "cells_per_step": plan.cells, "dtype": dtype,
                "clocks": clk, "gpu_launches": 3 * steps,
-               "roofline": roof(plan.cells, ms, dtype, "pairs_kernel<double,0,0,R> (run-time dimension)"
-                                if dtype == "f64" else "pairs_kernel<float,0,2,4,28> (wide dim-28 strips)"),
+               "roofline": roof(plan.cells, ms, dtype, f"short_pairs_kernel<{'double' if dtype == 'f64' else 'float'},28> "
+                                                       "(cost tile, then wavefront)"),
                "result": {"extrapolated_all_pairs_seconds": full_cells / (gcups * 1e9),
                           "all_pairs_cells": full_cells, "paper_all_pairs_hours_other_gpu": "< 2.6"},
                "config": {"workload": f"u3 block: {nb} x {nb} images sampled from the 60,000 (seeded), 28 "

@@ -1022,6 +1022,7 @@ twed_status_t plan_create(twed_handle_t h, const S* A, const S* B, int dim, T nu
     pa.counter = pl->counter;
     pa.scratch = base + o_scr;
     pa.scratch_cols = scols;
+    pa.max_len = std::max(maxa, maxb);
     pa.sc.err = pl->ctl;
     pa.sc.sticky = pl->ctl + 1;
     pa.sc.timeout_ns = timeout_ns(o);
@@ -1345,6 +1346,7 @@ twed_status_t batch_impl(twed_handle_t h, const S* A, const S* B, const int64_t*
     pa.counter = counter;
     pa.scratch = base + o_scr;
     pa.scratch_cols = scols;
+    pa.max_len = std::max(maxa, maxb);
     pa.sc = make_sync(h, nullptr);
     pa.dtw = dtw ? 1 : 0;
     if (order) {

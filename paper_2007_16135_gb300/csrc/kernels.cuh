@@ -8,6 +8,8 @@
 #define TWED_PAIRS_MIN_BLOCKS 1
 #endif
 
+#include <algorithm>
+
 #include "engine.cuh"
 #include "engine_f32.cuh"
 #include "engine_wide.cuh"
@@ -266,6 +268,10 @@ __device__ __forceinline__ void triangle_pos(int64_t w, int64_t n, int64_t& p, i
     q = w - r * (2 * n - r - 1) / 2 + r + 1;
 }
 
+}  // namespace twed
+#include "engine_short.cuh"
+namespace twed {
+
 // Shared memory per warp of the many-pairs kernel (WD > 0: the wide-point
 // strips of engine_wide.cuh).
 template <typename T, int DIM, int WD>
@@ -478,9 +484,53 @@ int blocks_per_sm(K kernel, int smem_warp, int threads) {
      : ((p) == 2 && (dim) == 64) ? ([&] { constexpr int WD_ = 64; BODY; }(), true) \
                                  : false)
 
+// Short pairs (engine_short.cuh): every series of both sets at most
+// kShortMax points, p = 2, dims 16 and 28 (FP32 and FP64) or 64 (FP32),
+// values and records 16-byte aligned.
+template <typename T>
+bool short_pairs_fit(const PairsArgs<T>& a) {
+    if (a.dtw || a.p != 2 || a.max_len < 1 || a.max_len > kShortMax) return false;
+    if (a.cut_cells > 0 && a.cut_cells < (int64_t)kShortMax * kShortMax) return false;
+    if (((uintptr_t)a.vals_a | (uintptr_t)a.vals_b | (uintptr_t)a.rec_a | (uintptr_t)a.rec_b) & 15) return false;
+    return a.dim == 16 || a.dim == 28 || (sizeof(T) == 4 && a.dim == 64);
+}
+
+// The third case instantiates the FP64 kernel at dim 16 again (never taken).
+#define TWED_SHORT_DISPATCH(T, dim, BODY)                                                 \
+    ((dim) == 16   ? ([&] { constexpr int SD_ = 16; BODY; }(), true)                     \
+     : (dim) == 28 ? ([&] { constexpr int SD_ = 28; BODY; }(), true)                     \
+     : (dim) == 64 ? ([&] { constexpr int SD_ = sizeof(T) == 4 ? 64 : 16; BODY; }(), true) \
+                   : false)
+
+// Persistent grid: the resident blocks on every SM, no more than the pairs
+// need (kShortGrab pairs per warp).
+template <typename T, int SD>
+cudaError_t launch_short_dim(const PairsArgs<T>& a, int sms, cudaStream_t st) {
+    constexpr int threads = 32 * kShortWarps;
+    constexpr int warp_bytes = ShortSmem<T, SD>::kWarp;
+    static int nb = 0;  // resident blocks per SM (one query per process)
+    if (nb == 0) nb = blocks_per_sm(short_pairs_kernel<T, SD>, warp_bytes, threads);
+    const int64_t warps_needed = (a.npairs + kShortGrab - 1) / kShortGrab;
+    const int64_t blocks = std::min<int64_t>((int64_t)std::max(nb, 1) * sms,
+                                             (warps_needed + kShortWarps - 1) / kShortWarps);
+    return launch_with_smem(short_pairs_kernel<T, SD>, warp_bytes, (int)blocks, threads, st, a);
+}
+
+template <typename T>
+cudaError_t launch_short_pairs(const PairsArgs<T>& a, cudaStream_t st) {
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    e = cudaErrorInvalidValue;
+    TWED_SHORT_DISPATCH(T, a.dim, (e = launch_short_dim<T, SD_>(a, sms, st)));
+    return e;
+}
+
 template <typename T, int RMAX_LIMIT>
 cudaError_t launch_pairs_t(const PairsArgs<T>& a, int blocks, int threads, cudaStream_t st) {
     if (a.npairs <= 0) return cudaSuccess;
+    if (short_pairs_fit(a)) return launch_short_pairs(a, st);
     cudaError_t e = cudaSuccess;
     if (a.dtw) {
         // DTW: FP32 compiled point layouts on the staged engine only
@@ -493,8 +543,11 @@ cudaError_t launch_pairs_t(const PairsArgs<T>& a, int blocks, int threads, cudaS
         }
         return cudaErrorInvalidValue;
     }
+    // the wide strips copy points in 16-byte pieces: unaligned values run
+    // the run-time-dimension kernels
+    const bool vals16 = (((uintptr_t)a.vals_a | (uintptr_t)a.vals_b) & 15) == 0;
     if constexpr (sizeof(T) == 4) {
-        if (TWED_WIDE_DISPATCH(a.dim, a.p,
+        if (vals16 && TWED_WIDE_DISPATCH(a.dim, a.p,
                                (e = launch_with_smem(pairs_kernel<T, 0, 2, wide_rmax<WD_>(), WD_>,
                                                      wide_bytes_per_warp<WD_>(), blocks, threads, st, a))))
             return e;

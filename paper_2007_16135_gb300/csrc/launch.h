@@ -76,6 +76,7 @@ struct PairsArgs {
     int64_t cut_cells = 0;   // > 0: pairs with more cells are skipped (run elsewhere)
     const int64_t* order = nullptr;  // kExplicitPairs: run position -> pair index (nullptr: identity)
     int dtw = 0;             // FP32 compiled layouts only: DTW instead of TWED (nu, times, delete costs unused)
+    int64_t max_len = 0;     // longest series of either set; 1 .. 32 lets the short-pair kernel run (0: not known)
 };
 
 // Longest-first run order of an explicit pair list (order.cu): order[k] is
