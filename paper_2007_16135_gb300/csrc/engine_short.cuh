@@ -18,19 +18,20 @@
 //     shuffle, now one cost load and one delete-cost load per cell.
 //
 // Every lane is busy in phase 1 (lanes past the pair's rows repeat its last
-// row), so the fill and drain of phase 2 cost a few additions per step.  The
-// next pair's points and (t, delete cost) records are copied into the other
-// half of a double-buffered per-warp stage by cp.async while the current one
-// runs.  Warps take pairs from the launch's counter kShortGrab at a time.
+// row), so the fill and drain of phase 2 cost a few additions per step.
+// While a pair runs, the next pair's column points and (t', delete cost)
+// records are copied into the other half of a double-buffered per-warp
+// stage by cp.async, and each lane loads its next row point and record into
+// registers.  Warps take pairs from the launch's counter kShortGrab at a time.
 //
-// Cost tile layout: column j (0-based) of the pair is tile column j + 1,
-// rows are the lanes: tile[(j + 1) * 32 + i].  Tile column 0 (before the
-// first column) and column m + 1 (after the last) hold +inf costs with zero
-// delete costs: a lane before its first column then computes +inf, and a lane
-// past its last column keeps D(i, m) (its own value plus a zero delete cost
-// is the least candidate, since D(i, m) <= D(i-1, m) + dA(i) by the
-// recurrence).  The lanes of one load read one tile row each, so the bank of
-// a lane's address is its lane number and no load conflicts.
+// Cost tile layout: column j (0-based) of the pair at tile[j * 32 + i] for
+// row i.  At step s lane i reads entry (s - i, i) when 0 <= s - i < m and
+// otherwise takes cost +inf and delete cost 0: a lane before its first
+// column then computes +inf, and a lane past its last column keeps D(i, m)
+// (its own value plus a zero delete cost is the least candidate, since
+// D(i, m) <= D(i-1, m) + dA(i) by the recurrence).  The lanes of one load
+// read one tile row each, so the bank of a lane's address is its lane number
+// and no load conflicts.
 //
 // Arithmetic per cell follows the strip engines (engine.cuh): FP64 sums the
 // squared differences in component order with separately rounded products
@@ -43,93 +44,115 @@
 
 namespace twed {
 
-constexpr int kShortMax = 32;              // longest series this kernel takes
-constexpr int kShortWarps = 2;             // warps per block
-constexpr int kShortGrab = 8;              // pairs a warp takes from the counter at once
-constexpr int kShortCols = kShortMax + 2;  // cost-tile columns: two sentinels around 32
+constexpr int kShortMax = 32;   // longest series this kernel takes
+constexpr int kShortWarps = 2;  // warps per block
+constexpr int kShortGrab = 8;   // pairs a warp takes from the counter at once
 
-// Shared memory of one warp (bytes): two stages (points and records of both
-// series of a pair), the cost tile and its delete-cost row.
+// Shared memory of one warp (bytes): two stages (the column series' points
+// and records), the cost tile and its delete-cost row.
 template <typename T, int DIM>
 struct ShortSmem {
     static constexpr int kPts = kShortMax * DIM * (int)sizeof(T);  // one series' points
     static constexpr int kRecs = kShortMax * 16;                   // its 16-byte records
-    static constexpr int kStage = 2 * kPts + 2 * kRecs;
-    static constexpr int kCost = kShortCols * kShortMax * (int)sizeof(T);
-    static constexpr int kDelb = (kShortCols * (int)sizeof(T) + 15) / 16 * 16;
+    static constexpr int kStage = kPts + kRecs;
+    static constexpr int kCost = kShortMax * kShortMax * (int)sizeof(T);
+    static constexpr int kDelb = kShortMax * (int)sizeof(T);
     static constexpr int kWarp = 2 * kStage + kCost + kDelb;
 };
 
 __device__ __forceinline__ void cp_async_wait_one() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
-// Phase 1, FP32: costs of row `arow` against the m staged columns into
-// `col` (the lane's entry of tile column 1; columns 32 entries apart).
+// A lane's row point and its (t, delete cost) in registers.  FP32 keeps the
+// point as component pairs (a_2k, a_2k+1), the operands of f32x2 arithmetic.
+template <typename T, int DIM>
+struct ShortRow;
 template <int DIM>
-__device__ __forceinline__ void short_costs(const float* arow, const float* pb, const float* rb, float ti,
-                                            float nu, int m, float* col) {
+struct ShortRow<float, DIM> {
     static_assert(DIM % 4 == 0, "points come in 16-byte pieces");
-    constexpr int NQ = DIM / 4;
-    unsigned long long A2[2 * NQ];  // component pairs (a_2k, a_2k+1)
-    const ulonglong2* ap = reinterpret_cast<const ulonglong2*>(arow);
+    unsigned long long v[DIM / 2];
+    float t, del;
+    __device__ __forceinline__ void load(const float* pt, const float* rec) {
+        const ulonglong2* p = reinterpret_cast<const ulonglong2*>(pt);
 #pragma unroll
-    for (int q = 0; q < NQ; ++q) {
-        const ulonglong2 v = ap[q];
-        A2[2 * q] = v.x;
-        A2[2 * q + 1] = v.y;
+        for (int q = 0; q < DIM / 4; ++q) {
+            const ulonglong2 x = __ldg(p + q);
+            v[2 * q] = x.x;
+            v[2 * q + 1] = x.y;
+        }
+        const float2 r = __ldg(reinterpret_cast<const float2*>(rec));
+        t = r.x;
+        del = r.y;
     }
+};
+template <int DIM>
+struct ShortRow<double, DIM> {
+    static_assert(DIM % 2 == 0, "points come in 16-byte pieces");
+    double v[DIM];
+    double t, del;
+    __device__ __forceinline__ void load(const double* pt, const double* rec) {
+        const double2* p = reinterpret_cast<const double2*>(pt);
+#pragma unroll
+        for (int q = 0; q < DIM / 2; ++q) {
+            const double2 x = __ldg(p + q);
+            v[2 * q] = x.x;
+            v[2 * q + 1] = x.y;
+        }
+        const double2 r = __ldg(reinterpret_cast<const double2*>(rec));
+        t = r.x;
+        del = r.y;
+    }
+};
+
+// Phase 1, FP32: costs of the lane's row against the m staged columns into
+// `col` (the lane's entry of tile column 0; columns 32 entries apart).
+template <int DIM>
+__device__ __forceinline__ void short_costs(const ShortRow<float, DIM>& a, const float* pb, const float* rb,
+                                            float nu, int m, float* col) {
+    constexpr int NQ = DIM / 4;
 #pragma unroll 2
     for (int j = 0; j < m; ++j) {
         const ulonglong2* bp = reinterpret_cast<const ulonglong2*>(pb + j * DIM);
         // two running sums of pairs (components 4q, 4q+1 and 4q+2, 4q+3)
         ulonglong2 v = bp[0];
-        unsigned long long d0 = f2_sub(A2[0], v.x), d1 = f2_sub(A2[1], v.y);
+        unsigned long long d0 = f2_sub(a.v[0], v.x), d1 = f2_sub(a.v[1], v.y);
         unsigned long long s0 = f2_mul(d0, d0), s1 = f2_mul(d1, d1);
 #pragma unroll
         for (int q = 1; q < NQ; ++q) {
             v = bp[q];
-            d0 = f2_sub(A2[2 * q], v.x);
-            d1 = f2_sub(A2[2 * q + 1], v.y);
+            d0 = f2_sub(a.v[2 * q], v.x);
+            d1 = f2_sub(a.v[2 * q + 1], v.y);
             s0 = f2_fma(d0, d0, s0);
             s1 = f2_fma(d1, d1, s1);
         }
         float lo, hi;
         f2_unpack(f2_add(s0, s1), lo, hi);
-        col[32 * j] = Arith<float>::wcost(Arith<float>::root(lo + hi), nu, ti, rb[4 * j]);
+        col[32 * j] = Arith<float>::wcost(Arith<float>::root(lo + hi), nu, a.t, rb[4 * j]);
     }
 }
 
 // Phase 1, FP64: the oracle's order (d_k = a_k - b_k, s = d_0^2, then
 // s = s + d_k^2), every operation correctly rounded.
 template <int DIM>
-__device__ __forceinline__ void short_costs(const double* arow, const double* pb, const double* rb, double ti,
+__device__ __forceinline__ void short_costs(const ShortRow<double, DIM>& a, const double* pb, const double* rb,
                                             double nu, int m, double* col) {
-    static_assert(DIM % 2 == 0, "points come in 16-byte pieces");
     using A = Arith<double>;
-    double av[DIM];
-    const double2* ap = reinterpret_cast<const double2*>(arow);
-#pragma unroll
-    for (int q = 0; q < DIM / 2; ++q) {
-        const double2 v = ap[q];
-        av[2 * q] = v.x;
-        av[2 * q + 1] = v.y;
-    }
 #pragma unroll 2
     for (int j = 0; j < m; ++j) {
         const double2* bp = reinterpret_cast<const double2*>(pb + j * DIM);
         double2 v = bp[0];
-        double d = A::sub(av[0], v.x);
+        double d = A::sub(a.v[0], v.x);
         double s = A::mul(d, d);
-        d = A::sub(av[1], v.y);
+        d = A::sub(a.v[1], v.y);
         s = A::sq_acc(s, d);
 #pragma unroll
         for (int q = 1; q < DIM / 2; ++q) {
             v = bp[q];
-            d = A::sub(av[2 * q], v.x);
+            d = A::sub(a.v[2 * q], v.x);
             s = A::sq_acc(s, d);
-            d = A::sub(av[2 * q + 1], v.y);
+            d = A::sub(a.v[2 * q + 1], v.y);
             s = A::sq_acc(s, d);
         }
-        col[32 * j] = A::wcost(A::root(s), nu, ti, rb[2 * j]);
+        col[32 * j] = A::wcost(A::root(s), nu, a.t, rb[2 * j]);
     }
 }
 
@@ -157,8 +180,6 @@ __global__ void __launch_bounds__(32 * kShortWarps) short_pairs_kernel(PairsArgs
     T* delb = reinterpret_cast<T*>(ws + 2 * SM::kStage + SM::kCost);
     const int lane = threadIdx.x & 31;
     const T INF = A::inf();
-    cost[lane] = INF;  // tile column 0: never written again
-    if (lane == 0) delb[0] = T(0);
 
     struct Job {
         int64_t xa, yb;
@@ -223,48 +244,53 @@ __global__ void __launch_bounds__(32 * kShortWarps) short_pairs_kernel(PairsArgs
             return true;
         }
     };
-    // points and records of a pair into stage `buf` (16-byte pieces)
+    // the column series' points and records into stage `buf` (16-byte pieces)
     auto stage = [&](const Job& J, int buf) {
         unsigned char* sb = ws + buf * SM::kStage;
         constexpr int PP = DIM * (int)sizeof(T) / 16;  // pieces per point
-        const unsigned char* ga = reinterpret_cast<const unsigned char*>(a.vals_a + J.xa * DIM);
         const unsigned char* gb = reinterpret_cast<const unsigned char*>(a.vals_b + J.yb * DIM);
-        for (int c = lane; c < J.n * PP; c += 32) cp_async16(sb + 16 * c, ga + 16 * c);
-        for (int c = lane; c < J.m * PP; c += 32) cp_async16(sb + SM::kPts + 16 * c, gb + 16 * c);
-        if (lane < J.n) cp_async16(sb + 2 * SM::kPts + 16 * lane, a.rec_a + (J.xa + lane) * RL);
-        if (lane < J.m) cp_async16(sb + 2 * SM::kPts + SM::kRecs + 16 * lane, a.rec_b + (J.yb + lane) * RL);
+        for (int c = lane; c < J.m * PP; c += 32) cp_async16(sb + 16 * c, gb + 16 * c);
+        if (lane < J.m) cp_async16(sb + SM::kPts + 16 * lane, a.rec_b + (J.yb + lane) * RL);
     };
-    auto compute = [&](const Job& J, int buf) {
+    // the lane's row (lanes past the last row repeat it; their results are never read)
+    auto load_row = [&](const Job& J, ShortRow<T, DIM>& r) {
+        const int64_t i = J.xa + min(lane, J.n - 1);
+        r.load(a.vals_a + i * DIM, a.rec_a + i * RL);
+    };
+    auto compute = [&](const Job& J, int buf, const ShortRow<T, DIM>& row) {
         const unsigned char* sb = ws + buf * SM::kStage;
-        const T* pa = reinterpret_cast<const T*>(sb);
-        const T* pb = reinterpret_cast<const T*>(sb + SM::kPts);
-        const T* ra = reinterpret_cast<const T*>(sb + 2 * SM::kPts);
-        const T* rb = reinterpret_cast<const T*>(sb + 2 * SM::kPts + SM::kRecs);
+        const T* pb = reinterpret_cast<const T*>(sb);
+        const T* rb = reinterpret_cast<const T*>(sb + SM::kPts);
         const int n = J.n, m = J.m;
-        const int i = min(lane, n - 1);  // lanes past the last row repeat it; never read
-        const T ti = ra[RL * i], dA = ra[RL * i + 1];
-        if (lane < m) delb[lane + 1] = rb[RL * lane + 1];
-        if (lane == 0) delb[m + 1] = T(0);
-        cost[32 * (m + 1) + lane] = INF;
-        short_costs<DIM>(pa + i * DIM, pb, rb, ti, a.nu, m, cost + 32 + lane);
+        if (lane < m) delb[lane] = rb[RL * lane + 1];
+        short_costs<DIM>(row, pb, rb, a.nu, m, cost + lane);
         __syncwarp();
         // the wavefront: lane i (row i+1) on column s - i at step s
-        T Dl = INF, cl = T(0);                    // D and c of the lane's row at its last column
+        T Dl = INF, cl = T(0);                           // D and c of the lane's row at its last column
         T diagD = lane == 0 ? T(0) : INF, diagC = T(0);  // D(0, 0) = 0, c(0, 0) = 0
-        const T* crow = cost + lane;
-#pragma unroll 4
-        for (int s = 0; s < n + m - 1; ++s) {
-            T upD = __shfl_up_sync(kFull, Dl, 1);
-            const T upC = __shfl_up_sync(kFull, cl, 1);
-            upD = lane == 0 ? INF : upD;  // D(0, j) = +inf for j >= 1
-            const int jj = min(max(s - lane, -1), m) + 1;
-            const T c = crow[32 * jj];
-            const T tb = A::add(Dl, delb[jj]);
-            const T tm = A::add(A::add(diagD, c), diagC);
-            Dl = short_min3(A::add(upD, dA), tb, tm);
-            cl = c;
-            diagD = upD;
-            diagC = upC;
+        const T dA = row.del;
+        // step s: tile entry (s - lane, lane) is cb[32 s], its delete cost db[s]
+        // (read only for 0 <= s - lane < m)
+        const T* cb = cost + lane - 32 * lane;
+        const T* db = delb - lane;
+        // steps past n + m - 2 leave every row's value unchanged
+        for (int s0 = 0; s0 < n + m - 1; s0 += 4) {
+            const int r0 = s0 - lane;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                T upD = __shfl_up_sync(kFull, Dl, 1);
+                const T upC = __shfl_up_sync(kFull, cl, 1);
+                upD = lane == 0 ? INF : upD;  // D(0, j) = +inf for j >= 1
+                const bool in = (unsigned)(r0 + u) < (unsigned)m;
+                const T c = in ? cb[32 * (s0 + u)] : INF;
+                const T dbv = in ? db[s0 + u] : T(0);
+                const T tb = A::add(Dl, dbv);
+                const T tm = A::add(A::add(diagD, c), diagC);
+                Dl = short_min3(A::add(upD, dA), tb, tm);
+                cl = c;
+                diagD = upD;
+                diagC = upC;
+            }
         }
         if (lane == n - 1) {
             *J.o1 = Dl;
@@ -273,19 +299,27 @@ __global__ void __launch_bounds__(32 * kShortWarps) short_pairs_kernel(PairsArgs
     };
 
     Job cur{}, nxt{};
+    ShortRow<T, DIM> row, nrow;
     bool live = fetch(cur);
-    if (live) stage(cur, 0);
+    if (live) {
+        stage(cur, 0);
+        load_row(cur, row);
+    }
     cp_async_commit();
     int buf = 0;
     while (live) {
         const bool more = fetch(nxt);
-        if (more) stage(nxt, buf ^ 1);
+        if (more) {
+            stage(nxt, buf ^ 1);
+            load_row(nxt, nrow);
+        }
         cp_async_commit();
         cp_async_wait_one();  // this lane's copies of the current pair have landed
         __syncwarp();         // and every lane's
-        compute(cur, buf);
+        compute(cur, buf, row);
         __syncwarp();  // the stage and the cost tile are free again
         cur = nxt;
+        row = nrow;
         live = more;
         buf ^= 1;
     }
