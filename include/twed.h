@@ -94,7 +94,13 @@ typedef struct {
 #define TWED_XTERM_BF16 2
 
 /* A packed set of series.  vals/ts/offs are device pointers; offs_host is a
- * host copy of offs (the library reads lengths from it to plan work). */
+ * host copy of offs (the library reads lengths from it to plan work).
+ * vals needs only the alignment of its element type.  When it is 16-byte
+ * aligned, p = 2 sets at dims 16, 28 and 64 (FP32) take kernels that copy
+ * points in 16-byte pieces, and sets whose series all have at most 32
+ * points (dims 16 and 28, also FP64) take the short-pair kernel; the device
+ * lengths must then match offs_host (a longer pair found on the device is
+ * reported as TWED_ERR_INVALID_ARG with NaN as its value). */
 typedef struct {
     const double* vals;
     const double* ts;
