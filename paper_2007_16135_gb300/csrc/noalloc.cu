@@ -27,20 +27,27 @@ constexpr int kMaxDevices = 64;
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 // Every (dim, p) the many-pairs dispatch can pick: dim 1 (any p); dims 2,
-// 3, 4 and 8 (5-7 use the dim-8 layout) with p = 1 or 2; everything else on
-// the run-time-dimension kernels.
-constexpr int kVariants = 10;
+// 3, 4 and 8 (5-7 use the dim-8 layout) with p = 1 or 2; the wide strips of
+// dims 16, 28 and 64 at p = 2; everything else on the run-time-dimension
+// kernels (which also serve the wide dims when the values are not 16-byte
+// aligned).  The short-pair kernel is never chosen here: this entry point
+// leaves PairsArgs::max_len at 0.
+constexpr int kVariants = 13;
+constexpr int kRuntimeDim = 9;  // variant index of the run-time-dimension kernels
 int variant_of(int dim, int p) {
     if (dim == 1) return 0;
+    if (p == 2 && (dim == 16 || dim == 28 || dim == 64)) return dim == 16 ? 10 : (dim == 28 ? 11 : 12);
     const int d = dim <= 4 ? dim : (dim <= 8 ? 8 : 0);
-    if (d == 0 || (p != 1 && p != 2)) return kVariants - 1;
+    if (d == 0 || (p != 1 && p != 2)) return kRuntimeDim;
     const int di = d == 2 ? 0 : d == 3 ? 1 : d == 4 ? 2 : 3;
     return 1 + 2 * di + (p - 1);
 }
 void variant_rep(int v, int* dim, int* p) {
     static const int dims[4] = {2, 3, 4, 8};
+    static const int wide[3] = {16, 28, 64};
     if (v == 0) { *dim = 1; *p = 2; }
-    else if (v == kVariants - 1) { *dim = 9; *p = 2; }
+    else if (v == kRuntimeDim) { *dim = 9; *p = 2; }
+    else if (v > kRuntimeDim) { *dim = wide[v - kRuntimeDim - 1]; *p = 2; }
     else { *dim = dims[(v - 1) / 2]; *p = (v - 1) % 2 + 1; }
 }
 

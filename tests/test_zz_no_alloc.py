@@ -144,3 +144,29 @@ def test_noalloc_size_limit_is_the_documented_one(tw):
             assert out.item() == 0.0  # TWED(a, a) = 0
         else:
             assert st == tw.TWED_ERR_UNSUPPORTED
+
+
+def test_noalloc_wide_dim_two_calls(tw):
+    # dim 28 at p = 2 runs the wide strips here (their kernel loaded at the
+    # first call's set-up), series of up to 300 points; the second call
+    # allocates nothing and both match the oracle
+    import torch
+    stream = torch.cuda.current_stream()
+    SA, SB = _set(11, 12, 1, 300, 28), _set(12, 9, 1, 260, 28)
+    A = tw.DeviceSet.from_numpy(SA.vals, SA.ts, SA.offs, torch.float32)
+    B = tw.DeviceSet.from_numpy(SB.vals, SB.ts, SB.offs, torch.float32)
+    rng = np.random.default_rng(13)
+    pairs = np.stack([rng.integers(0, SA.n, 90), rng.integers(0, SB.n, 90)], 1)
+    d_pairs = torch.as_tensor(pairs, dtype=torch.int64).cuda()
+    ref = oracle.twed_pairs(SA.astype(np.float64).as_tuple(), SB.astype(np.float64).as_tuple(), pairs, 1.0, 1.0, 2)
+    out = torch.full((len(pairs),), float("nan"), dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    for call in range(2):
+        free0 = _free_bytes()
+        assert _call_noalloc(tw, A, B, d_pairs, out, 1.0, 1.0, 2, stream) == tw.TWED_OK
+        torch.cuda.synchronize()
+        if call > 0:
+            assert _free_bytes() == free0
+        got = out.cpu().numpy().astype(np.float64)
+        assert (np.abs(got - ref) / np.maximum(np.abs(ref), 1e-300)).max() <= 1e-5
+        out.fill_(float("nan"))
