@@ -39,8 +39,8 @@ UNIT = "GCUPS"
 FALLBACK_SM_MAX_MHZ = 2070.0
 FP32_LANES_PER_SM = 128  # FADD/FMUL/FFMA lanes per SM per clock
 FP64_LANES_PER_SM = 2    # DFMA lanes per SM per clock on GB300
-KERNEL_SOURCES = ["engine.cuh", "engine_f32.cuh", "kernels.cuh", "kernels_f32.cu", "kernels_f64.cu",
-                  "launch.h"]
+KERNEL_SOURCES = ["engine.cuh", "engine_f32.cuh", "engine_wide.cuh", "engine_short.cuh", "kernels.cuh",
+                  "kernels_f32.cu", "kernels_f64.cu", "launch.h"]
 
 
 def parse():
