@@ -41,6 +41,7 @@ FP32_LANES_PER_SM = 128  # FADD/FMUL/FFMA lanes per SM per clock
 FP64_LANES_PER_SM = 2    # DFMA lanes per SM per clock on GB300
 KERNEL_SOURCES = ["engine.cuh", "engine_f32.cuh", "engine_wide.cuh", "engine_short.cuh", "kernels.cuh",
                   "kernels_f32.cu", "kernels_f64.cu", "launch.h"]
+XTERM_SOURCES = ["xterm.cu", "tc.cuh", "launch.h"]
 
 
 def parse():
@@ -79,9 +80,9 @@ def parse():
 
 
 # ---------------------------------------------------------------- helpers
-def kernel_src_hash() -> str:
+def kernel_src_hash(sources=None) -> str:
     h = hashlib.sha256()
-    for f in KERNEL_SOURCES:
+    for f in sources or KERNEL_SOURCES:
         with open(os.path.join(ROOT, "paper_2007_16135_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -300,12 +301,16 @@ def bench_plan(args, rank, world, dev, workload):
         if dtype == "f64":
             peak_ops = props.multi_processor_count * FP64_LANES_PER_SM * sm_max * 1e6
     achieved = cells * opc / kern_s
+    # ncu's DRAM bytes of one launch of the dominant kernel, stored with a hash
+    # of its sources: null once the kernel has changed since the capture
     traffic = None
-    tp = os.path.join(ROOT, "profiles", f"pairs_kernel_{workload}_traffic.json")
+    tname = (f"xterm_sweep_kernel_{workload}_{args.xterm}" if xterm else f"pairs_kernel_{workload}") + (
+        f"_{args.nseries}" if args.nseries else "")
+    tp = os.path.join(ROOT, "profiles", f"{tname}_traffic.json")
     if os.path.exists(tp):
         with open(tp) as f:
             tj = json.load(f)
-        if tj.get("src_hash") == kernel_src_hash():
+        if tj.get("src_hash") == kernel_src_hash(XTERM_SOURCES if xterm else None):
             traffic = tj.get("dram_bytes_per_launch")
     kname = "xterm_sweep_kernel (tcgen05 tf32)" if xterm else f"pairs_kernel<float,{dim if dim in (1,2,3,4,8) else 0},2,8>"
     lanes = FP64_LANES_PER_SM if dtype == "f64" else FP32_LANES_PER_SM
