@@ -1351,7 +1351,7 @@ twed_status_t batch_impl(twed_handle_t h, const S* A, const S* B, const int64_t*
     pa.dtw = dtw ? 1 : 0;
     if (order) {
         int64_t* ord = (int64_t*)(base + o_ord);
-        TWED_CUDA(h, twed::launch_order_pairs(d_pairs, npairs, A->offs, B->offs, ord,
+        TWED_CUDA(h, twed::launch_order_pairs(d_pairs, npairs, A->offs, A->n, B->offs, B->n, ord,
                                               (unsigned long long*)(base + o_bins), h->sms, st));
         pa.order = ord;
     }

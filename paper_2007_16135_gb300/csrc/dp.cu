@@ -447,6 +447,7 @@ struct PathArgs {
     int64_t choice_stride;
     int64_t wpr;            // words per choice row (>= ceil(longest / 16))
     SyncCtl sc;
+    const int64_t* order = nullptr;  // run position -> pair index (nullptr: list order)
 };
 
 // TWED of each pair with one optimal edit path: the forward pass records the
@@ -465,6 +466,7 @@ __global__ void __launch_bounds__(128) path_pairs_kernel(PathArgs<T> a) {
         if (lane == 0) w = atomicAdd(a.counter, 1ull);
         w = __shfl_sync(kFull, w, 0);
         if ((int64_t)w >= a.npairs) break;
+        if (a.order != nullptr) w = (unsigned long long)a.order[w];  // longest first
         int64_t fa = 0, fb = 0;
         int n = a.n1, m = a.m1;
         if (a.offs_a != nullptr) {
@@ -565,6 +567,7 @@ __global__ void __launch_bounds__(128) path_staged_kernel(PathArgs<float> a) {
         if (lane == 0) w = atomicAdd(a.counter, 1ull);
         w = __shfl_sync(kFull, w, 0);
         if ((int64_t)w >= a.npairs) break;
+        if (a.order != nullptr) w = (unsigned long long)a.order[w];  // longest first
         int64_t fa = 0, fb = 0;
         int n = a.n1, m = a.m1;
         if (a.offs_a != nullptr) {
@@ -912,6 +915,12 @@ twed_status_t path_launch(twed_handle_t h, twed::dp::PathArgs<T> pa, const T* va
     off = align_up(off + sizeof(CellV<T>) * (size_t)nwarps * (size_t)stride);
     const size_t o_ch = off;
     off = align_up(off + per_choice * (size_t)nwarps);
+    // a pair list runs longest first, so that no large pair starts last
+    const bool ordered = offs_a != nullptr && pa.pairs != nullptr && pa.npairs > 1;
+    const size_t o_ord = off;
+    if (ordered) off = align_up(off + sizeof(int64_t) * (size_t)pa.npairs);
+    const size_t o_bins = off;
+    if (ordered) off = align_up(off + sizeof(unsigned long long) * twed::kOrderBins);
     twed_status_t st;
     char* base = (char*)twed::detail::handle_workspace(h, off, &st);
     if (!base) return st;
@@ -923,6 +932,12 @@ twed_status_t path_launch(twed_handle_t h, twed::dp::PathArgs<T> pa, const T* va
     twed::RecordsArgs<T> rb{vals_b, ts_b, offs_b, nb, totb, dim, p, nu, lambda, (T*)(base + o_rb)};
     if ((e = twed::launch_records(ra, s)) != cudaSuccess) return cuda_err(h, e);
     if ((e = twed::launch_records(rb, s)) != cudaSuccess) return cuda_err(h, e);
+    if (ordered) {
+        if ((e = twed::launch_order_pairs(pa.pairs, pa.npairs, offs_a, na, offs_b, nb, (int64_t*)(base + o_ord),
+                                          (unsigned long long*)(base + o_bins), sms, s)) != cudaSuccess)
+            return cuda_err(h, e);
+        pa.order = (const int64_t*)(base + o_ord);
+    }
     pa.rec_a = (const T*)(base + o_ra);
     pa.rec_b = (const T*)(base + o_rb);
     pa.vals_a = vals_a;

@@ -81,10 +81,11 @@ struct PairsArgs {
 
 // Longest-first run order of an explicit pair list (order.cu): order[k] is
 // the index of the pair to run k-th, by decreasing len_a * len_b in
-// quarter-octave classes.  bins: kOrderBins device words of scratch.
+// quarter-octave classes.  bins: kOrderBins device words of scratch.  A pair
+// with an index outside [0, na) x [0, nb) sorts last and is not dereferenced.
 constexpr int kOrderBins = 256;
-cudaError_t launch_order_pairs(const int64_t* pairs, int64_t npairs, const int64_t* offs_a,
-                               const int64_t* offs_b, int64_t* order, unsigned long long* bins,
+cudaError_t launch_order_pairs(const int64_t* pairs, int64_t npairs, const int64_t* offs_a, int64_t na,
+                               const int64_t* offs_b, int64_t nb, int64_t* order, unsigned long long* bins,
                                int sms, cudaStream_t st);
 
 // Elements per point record for (dim, p) (16-byte multiple; see Rec<>).

@@ -21,12 +21,15 @@ struct OrderKey {
     const int64_t* pairs;
     const int64_t* oa;
     const int64_t* ob;
+    int64_t na, nb;  // series in each set: indices outside are never dereferenced
 };
 
 // Class of a pair: 0 for the largest cell counts, kOrderBins - 1 for the
 // smallest (4 * floor(log2 c) + the two bits after c's leading one).
 __device__ __forceinline__ int cell_class(const OrderKey& k, int64_t w) {
     const int64_t x = k.pairs[2 * w], y = k.pairs[2 * w + 1];
+    // a pair outside the sets runs last; the pairs kernel reports it
+    if ((uint64_t)x >= (uint64_t)k.na || (uint64_t)y >= (uint64_t)k.nb) return kOrderBins - 1;
     const int64_t* oa = k.oa;
     const int64_t* ob = k.ob;
     const unsigned long long c =
@@ -101,11 +104,11 @@ __global__ void __launch_bounds__(256) order_scatter_kernel(OrderKey key, int64_
 
 }  // namespace
 
-cudaError_t launch_order_pairs(const int64_t* pairs, int64_t npairs, const int64_t* offs_a,
-                               const int64_t* offs_b, int64_t* order, unsigned long long* bins,
+cudaError_t launch_order_pairs(const int64_t* pairs, int64_t npairs, const int64_t* offs_a, int64_t na,
+                               const int64_t* offs_b, int64_t nb, int64_t* order, unsigned long long* bins,
                                int sms, cudaStream_t st) {
     if (npairs <= 0) return cudaSuccess;
-    const OrderKey key{pairs, offs_a, offs_b};
+    const OrderKey key{pairs, offs_a, offs_b, na, nb};
     const int threads = 256;
     const int64_t hist_blocks = std::min<int64_t>((int64_t)sms * 4, (npairs + threads - 1) / threads);
     const int64_t chunk = (int64_t)threads * kItems;
